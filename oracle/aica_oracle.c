@@ -1,0 +1,527 @@
+/*
+ * CPU oracle for the AICA pair-force path.  TEST INFRASTRUCTURE ONLY.
+ *
+ * Plain, slow FP64 reference code written from the paper (Macpherson & Reese,
+ * "Molecular dynamics in arbitrary geometries: parallel evaluation of pair
+ * forces", arXiv cs/0702131).  Only the test suite, the package smoke check
+ * and the CPU-baseline leg of the benchmark may load this library.  It shares
+ * no code, header or table with the CUDA path.  Built with -ffp-contract=off
+ * so every FP64 operation rounds exactly as written.
+ *
+ * Contents
+ *   oracle_lj            all-pairs minimum-image Lennard-Jones sum (the plain
+ *                        definition the method reaches, see §2.3)
+ *   oracle_cell_pairs    brute-force cell-cell minimum distance between
+ *                        triangulated polyhedra, all periodic images (§2.2,
+ *                        App. A.1, with the exact-distance criterion)
+ *   oracle_locate        point location by ray parity with a symbolic
+ *                        perturbation tie-break, FP64 with an error filter;
+ *                        uncertain cases are flagged for exact resolution
+ *   oracle_aica_loop     the real-real and real-referred loops of §2.3 over
+ *                        the oracle's own lists and binning
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------ LJ pair */
+/* The paper names Lennard-Jones molecules (§3) but prints no formula; the
+ * 12-6 form, plain truncation at r < rc and Lorentz-Berthelot mixing are the
+ * reading used throughout.  f is the force on the first molecule of the pair,
+ * d = x_first - x_second. */
+static void lj_pair(double r2, double eps_ab, double sig_ab, double *fscal, double *u)
+{
+    double s = (sig_ab * sig_ab) / r2;
+    double s3 = s * s * s;
+    double s6 = s3 * s3;
+    *fscal = 24.0 * eps_ab * (2.0 * s6 - s3) / r2;
+    *u = 4.0 * eps_ab * (s6 - s3);
+}
+
+static double min_image(double d, double L, int periodic)
+{
+    if (periodic) d -= L * nearbyint(d / L);
+    return d;
+}
+
+/* Forces F[k] = sum_{l != k, r_kl < rc} f_kl for every k in idx (or all k when
+ * idx is NULL), with Fabs[k] = sum_l |f_kl|.  ev7 gets U and the virial
+ * W_ab = sum_pairs d_a f_b (xx, yy, zz, xy, xz, yz), each pair counted once
+ * (half from each of its two molecules).  count gets the number of (k, l)
+ * ordered pairs within rc, i.e. twice the pair count when idx is NULL. */
+void oracle_lj(int64_t n, const double *pos, const int32_t *species, int S,
+               const double *eps, const double *sigma, double rc, const double *L,
+               const int32_t *periodic, int shift, const int64_t *idx, int64_t nidx,
+               double *F, double *Fabs, double *ev7, int64_t *count)
+{
+    double rc2 = rc * rc;
+    double U = 0, wxx = 0, wyy = 0, wzz = 0, wxy = 0, wxz = 0, wyz = 0;
+    int64_t cnt = 0;
+    int64_t m = idx ? nidx : n;
+    (void)S;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : U, wxx, wyy, wzz, wxy, wxz, wyz, cnt)
+    for (int64_t t = 0; t < m; ++t) {
+        int64_t k = idx ? idx[t] : t;
+        double fx = 0, fy = 0, fz = 0, fa = 0;
+        int a = species[k];
+        for (int64_t l = 0; l < n; ++l) {
+            if (l == k) continue;
+            double dx = min_image(pos[3 * k + 0] - pos[3 * l + 0], L[0], periodic[0]);
+            double dy = min_image(pos[3 * k + 1] - pos[3 * l + 1], L[1], periodic[1]);
+            double dz = min_image(pos[3 * k + 2] - pos[3 * l + 2], L[2], periodic[2]);
+            double r2 = (dx * dx + dy * dy) + dz * dz;
+            if (!(r2 < rc2)) continue;
+            int b = species[l];
+            double eab = sqrt(eps[a] * eps[b]);
+            double sab = 0.5 * (sigma[a] + sigma[b]);
+            double fs, u;
+            lj_pair(r2, eab, sab, &fs, &u);
+            if (shift) {
+                double fc, uc;
+                lj_pair(rc2, eab, sab, &fc, &uc);
+                u -= uc;
+            }
+            fx += fs * dx;
+            fy += fs * dy;
+            fz += fs * dz;
+            fa += fabs(fs) * sqrt(r2);
+            U += 0.5 * u;
+            wxx += 0.5 * dx * (fs * dx);
+            wyy += 0.5 * dy * (fs * dy);
+            wzz += 0.5 * dz * (fs * dz);
+            wxy += 0.5 * dx * (fs * dy);
+            wxz += 0.5 * dx * (fs * dz);
+            wyz += 0.5 * dy * (fs * dz);
+            cnt += 1;
+        }
+        F[3 * t + 0] = fx;
+        F[3 * t + 1] = fy;
+        F[3 * t + 2] = fz;
+        Fabs[t] = fa;
+    }
+    ev7[0] = U;
+    ev7[1] = wxx; ev7[2] = wyy; ev7[3] = wzz;
+    ev7[4] = wxy; ev7[5] = wxz; ev7[6] = wyz;
+    *count = cnt;
+}
+
+/* ------------------------------------------------- cell-cell min distance */
+typedef struct { double x, y, z; } v3;
+
+static v3 ld(const double *p) { v3 r = {p[0], p[1], p[2]}; return r; }
+static v3 ldsh(const double *p, v3 s) { v3 r = {p[0] + s.x, p[1] + s.y, p[2] + s.z}; return r; }
+static v3 sub(v3 a, v3 b) { v3 r = {a.x - b.x, a.y - b.y, a.z - b.z}; return r; }
+static v3 add(v3 a, v3 b) { v3 r = {a.x + b.x, a.y + b.y, a.z + b.z}; return r; }
+static v3 scl(v3 a, double s) { v3 r = {a.x * s, a.y * s, a.z * s}; return r; }
+static double dot(v3 a, v3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+static v3 cross(v3 a, v3 b)
+{
+    v3 r = {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+    return r;
+}
+
+/* squared distance from p to the closed segment [a, b] */
+static double d2_point_seg(v3 p, v3 a, v3 b)
+{
+    v3 ab = sub(b, a);
+    double t = dot(sub(p, a), ab) / dot(ab, ab);
+    if (t < 0) t = 0;
+    if (t > 1) t = 1;
+    v3 q = add(a, scl(ab, t));
+    v3 d = sub(p, q);
+    return dot(d, d);
+}
+
+/* squared distance from p to the closed triangle abc: the orthogonal
+ * projection when it falls inside, otherwise the nearest edge */
+static double d2_point_tri(v3 p, v3 a, v3 b, v3 c)
+{
+    v3 nrm = cross(sub(b, a), sub(c, a));
+    double s0 = dot(cross(sub(b, a), sub(p, a)), nrm);
+    double s1 = dot(cross(sub(c, b), sub(p, b)), nrm);
+    double s2 = dot(cross(sub(a, c), sub(p, c)), nrm);
+    if (s0 >= 0 && s1 >= 0 && s2 >= 0) {
+        double h = dot(sub(p, a), nrm);
+        return h * h / dot(nrm, nrm);
+    }
+    double d = d2_point_seg(p, a, b);
+    double e = d2_point_seg(p, b, c);
+    double f = d2_point_seg(p, c, a);
+    if (e < d) d = e;
+    if (f < d) d = f;
+    return d;
+}
+
+/* squared distance between closed segments [p0,p1] and [q0,q1]: either an
+ * endpoint is involved, or both closest points are interior and then they are
+ * the feet of the common perpendicular of the two lines */
+static double d2_seg_seg(v3 p0, v3 p1, v3 q0, v3 q1)
+{
+    double best = d2_point_seg(p0, q0, q1);
+    double t;
+    if ((t = d2_point_seg(p1, q0, q1)) < best) best = t;
+    if ((t = d2_point_seg(q0, p0, p1)) < best) best = t;
+    if ((t = d2_point_seg(q1, p0, p1)) < best) best = t;
+    v3 u = sub(p1, p0), v = sub(q1, q0), w = sub(p0, q0);
+    double a = dot(u, u), b = dot(u, v), c = dot(v, v), d = dot(u, w), e = dot(v, w);
+    double D = a * c - b * b;
+    if (D > 1e-14 * a * c) {
+        double s = (b * e - c * d) / D;
+        double r = (a * e - b * d) / D;
+        if (s > 0 && s < 1 && r > 0 && r < 1) {
+            v3 g = sub(add(w, scl(u, s)), scl(v, r));
+            double gg = dot(g, g);
+            if (gg < best) best = gg;
+        }
+    }
+    return best;
+}
+
+/* Geometry of cell c: triangles tri[tri_off[c]..tri_off[c+1]) (9 doubles each),
+ * vertices vtx[...] (3 doubles), edges edg[...] (6 doubles). */
+typedef struct {
+    const int64_t *tri_off, *vtx_off, *edg_off;
+    const double *tri, *vtx, *edg;
+} cellgeo;
+
+/* min squared distance between cell A and cell B translated by sB */
+static double cell_d2(const cellgeo *g, int64_t A, int64_t B, v3 sB)
+{
+    v3 z = {0, 0, 0};
+    double best = INFINITY, t;
+    for (int64_t i = g->vtx_off[A]; i < g->vtx_off[A + 1]; ++i) {
+        v3 p = ld(g->vtx + 3 * i);
+        for (int64_t j = g->tri_off[B]; j < g->tri_off[B + 1]; ++j) {
+            const double *T = g->tri + 9 * j;
+            if ((t = d2_point_tri(p, ldsh(T, sB), ldsh(T + 3, sB), ldsh(T + 6, sB))) < best) best = t;
+        }
+    }
+    for (int64_t i = g->vtx_off[B]; i < g->vtx_off[B + 1]; ++i) {
+        v3 p = ldsh(g->vtx + 3 * i, sB);
+        for (int64_t j = g->tri_off[A]; j < g->tri_off[A + 1]; ++j) {
+            const double *T = g->tri + 9 * j;
+            if ((t = d2_point_tri(p, ldsh(T, z), ldsh(T + 3, z), ldsh(T + 6, z))) < best) best = t;
+        }
+    }
+    for (int64_t i = g->edg_off[A]; i < g->edg_off[A + 1]; ++i) {
+        const double *E = g->edg + 6 * i;
+        v3 p0 = ld(E), p1 = ld(E + 3);
+        for (int64_t j = g->edg_off[B]; j < g->edg_off[B + 1]; ++j) {
+            const double *Q = g->edg + 6 * j;
+            if ((t = d2_seg_seg(p0, p1, ldsh(Q, sB), ldsh(Q + 3, sB))) < best) best = t;
+        }
+    }
+    return best;
+}
+
+/* For every query cell A = query[q]: every (B, n) with B a real cell, n an
+ * integer image vector (|n_k| <= m[k]; n_k = 0 on non-periodic axes), (B, n)
+ * != (A, 0), and min_dist^2(A, B + n.L) < thr^2.  Results per query are in
+ * image-major (n lexicographic), then ascending B order, at most cap entries
+ * per query (count[q] = -1 if the capacity is exceeded).
+ *
+ * When use_bound is set a pair is skipped without the exact test if
+ * |ctr_A - ctr_B - n.L| - rad_A - rad_B > thr (1 + 1e-9) + 1e-9, where rad_c
+ * bounds the distance from ctr_c to every vertex of c; every point of a cell
+ * lies in the convex hull of its vertices, so this bound never drops a pair.
+ * ties[q] counts decisions with |d^2 - thr^2| <= 1e-9 thr^2. */
+void oracle_cell_pairs(const int64_t *tri_off, const double *tri, const int64_t *vtx_off,
+                       const double *vtx, const int64_t *edg_off, const double *edg,
+                       const double *ctr, const double *rad, int64_t n_cells,
+                       const int64_t *query, int64_t nq, double thr, const int32_t *m,
+                       const double *L, int use_bound, int64_t cap, int64_t *count,
+                       int32_t *outB, int32_t *outN, double *outD2, int64_t *ties)
+{
+    cellgeo g = {tri_off, vtx_off, edg_off, tri, vtx, edg};
+    double thr2 = thr * thr;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t q = 0; q < nq; ++q) {
+        int64_t A = query[q];
+        int64_t c = 0, nt = 0;
+        for (int nx = -m[0]; nx <= m[0]; ++nx)
+            for (int ny = -m[1]; ny <= m[1]; ++ny)
+                for (int nz = -m[2]; nz <= m[2]; ++nz) {
+                    v3 s = {nx * L[0], ny * L[1], nz * L[2]};
+                    for (int64_t B = 0; B < n_cells; ++B) {
+                        if (B == A && nx == 0 && ny == 0 && nz == 0) continue;
+                        if (use_bound) {
+                            v3 dc = {ctr[3 * A] - ctr[3 * B] - s.x, ctr[3 * A + 1] - ctr[3 * B + 1] - s.y,
+                                     ctr[3 * A + 2] - ctr[3 * B + 2] - s.z};
+                            double lb = sqrt(dot(dc, dc)) - rad[A] - rad[B];
+                            if (lb > thr * (1 + 1e-9) + 1e-9) continue;
+                        }
+                        double d2 = cell_d2(&g, A, B, s);
+                        if (fabs(d2 - thr2) <= 1e-9 * thr2) nt++;
+                        if (d2 < thr2) {
+                            if (c < cap) {
+                                int64_t o = q * cap + c;
+                                outB[o] = (int32_t)B;
+                                outN[3 * o + 0] = nx;
+                                outN[3 * o + 1] = ny;
+                                outN[3 * o + 2] = nz;
+                                outD2[o] = d2;
+                            }
+                            c++;
+                        }
+                    }
+                }
+        count[q] = c > cap ? -1 : c;
+        ties[q] = nt;
+    }
+}
+
+/* -------------------------------------------------------- point location */
+/* Signs of orientation determinants for a point perturbed to
+ * p_eps = p + (eps, eps^2, eps^3), eps -> 0+.  Each sign is computed in FP64
+ * and accepted only when the value clears a bound (>= 30x the worst rounding
+ * error); otherwise the caller reports the molecule as uncertain. */
+#define UNCERTAIN 2
+
+/* sign of (b_y - a_y)(p_z - a_z) - (b_z - a_z)(p_y - a_y) for p perturbed by
+ * (eps^2, eps^3) in (y, z) */
+static int orient2_yz_eps(v3 a, v3 b, v3 p)
+{
+    double t1 = (b.y - a.y) * (p.z - a.z), t2 = (b.z - a.z) * (p.y - a.y);
+    double v = t1 - t2, bound = 1e-14 * (fabs(t1) + fabs(t2));
+    if (v > bound) return 1;
+    if (v < -bound) return -1;
+    if (v != 0 || bound != 0) return UNCERTAIN;
+    double cy = -(b.z - a.z), cz = (b.y - a.y);
+    if (cy != 0) return cy > 0 ? 1 : -1;
+    if (cz != 0) return cz > 0 ? 1 : -1;
+    return 0;
+}
+
+/* sign of N_x with N = (b - a) x (c - a): the triangle's yz-projected area */
+static int orient2_yz(v3 a, v3 b, v3 c)
+{
+    double t1 = (b.y - a.y) * (c.z - a.z), t2 = (b.z - a.z) * (c.y - a.y);
+    double v = t1 - t2, bound = 1e-14 * (fabs(t1) + fabs(t2));
+    if (v > bound) return 1;
+    if (v < -bound) return -1;
+    if (v == 0 && bound == 0) return 0;
+    return UNCERTAIN;
+}
+
+/* sign of N . (p - a): the plane value of p (exact zero -> 0) */
+static int orient3(v3 a, v3 b, v3 c, v3 p)
+{
+    v3 u = sub(b, a), w = sub(c, a), d = sub(p, a);
+    double n1 = u.y * w.z, n2 = u.z * w.y, n3 = u.z * w.x, n4 = u.x * w.z, n5 = u.x * w.y, n6 = u.y * w.x;
+    double Nx = n1 - n2, Ny = n3 - n4, Nz = n5 - n6;
+    double v = (Nx * d.x + Ny * d.y) + Nz * d.z;
+    double perm = (fabs(n1) + fabs(n2)) * fabs(d.x) + (fabs(n3) + fabs(n4)) * fabs(d.y) +
+                  (fabs(n5) + fabs(n6)) * fabs(d.z);
+    double bound = 1e-13 * perm;
+    if (v > bound) return 1;
+    if (v < -bound) return -1;
+    if (v == 0 && perm == 0) return 0;
+    return UNCERTAIN;
+}
+
+/* Parity of crossings of the ray p_eps + s x^, s > 0, with the closed
+ * triangulated surface of a cell.  Returns 1 inside, 0 outside, UNCERTAIN. */
+static int inside_ray(const double *tri, int64_t t0, int64_t t1, v3 p)
+{
+    int parity = 0;
+    for (int64_t t = t0; t < t1; ++t) {
+        v3 a = ld(tri + 9 * t), b = ld(tri + 9 * t + 3), c = ld(tri + 9 * t + 6);
+        int nx = orient2_yz(a, b, c);
+        if (nx == UNCERTAIN) return UNCERTAIN;
+        if (nx == 0) continue; /* edge-on in the yz projection: never crossed */
+        int e0 = orient2_yz_eps(a, b, p), e1 = orient2_yz_eps(b, c, p), e2 = orient2_yz_eps(c, a, p);
+        if (e0 == UNCERTAIN || e1 == UNCERTAIN || e2 == UNCERTAIN) return UNCERTAIN;
+        if (!(e0 == nx && e1 == nx && e2 == nx)) continue;
+        int o = orient3(a, b, c, p);
+        if (o == UNCERTAIN) return UNCERTAIN;
+        if (o == 0) o = nx; /* on the plane: p_eps sits on the +N_x side */
+        if (o == -nx) parity ^= 1;
+    }
+    return parity;
+}
+
+static double wrap_coord(double x, double L)
+{
+    if (x >= 0 && x < L) return x;
+    x = x - L * floor(x / L);
+    if (x >= L) x -= L;
+    return x;
+}
+
+/* For each molecule: wrap periodic coordinates into [0, L), then test every
+ * cell whose closed bounding box holds the point (the box test is exact and
+ * only skips cells that cannot hold it).  cell[k] = the containing cell,
+ * -1 if none, -2 if some decision was uncertain or two cells claimed it.
+ * Candidate cells come from a uniform grid over the mesh bounding box. */
+void oracle_locate(const int64_t *tri_off, const double *tri, const double *lo, const double *hi,
+                   int64_t n_cells, const double *pos, int64_t n, const double *L,
+                   const int32_t *periodic, int32_t *cell, double *wrapped)
+{
+    double glo[3] = {INFINITY, INFINITY, INFINITY}, ghi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t c = 0; c < n_cells; ++c)
+        for (int d = 0; d < 3; ++d) {
+            if (lo[3 * c + d] < glo[d]) glo[d] = lo[3 * c + d];
+            if (hi[3 * c + d] > ghi[d]) ghi[d] = hi[3 * c + d];
+        }
+    int G[3];
+    double h[3];
+    double per = cbrt((double)n_cells);
+    for (int d = 0; d < 3; ++d) {
+        G[d] = (int)per + 1;
+        h[d] = (ghi[d] - glo[d]) / G[d];
+    }
+    size_t nb = (size_t)G[0] * (size_t)G[1] * (size_t)G[2];
+    int64_t *boff = calloc(nb + 1, sizeof(int64_t));
+    for (int pass = 0; pass < 2; ++pass) {
+        int64_t *fill = pass ? calloc(nb, sizeof(int64_t)) : NULL;
+        int64_t *lst = pass ? malloc(sizeof(int64_t) * (boff[nb] ? boff[nb] : 1)) : NULL;
+        for (int64_t c = 0; c < n_cells; ++c) {
+            int i0[3], i1[3];
+            for (int d = 0; d < 3; ++d) {
+                i0[d] = (int)floor((lo[3 * c + d] - glo[d]) / h[d]) - 1;
+                i1[d] = (int)floor((hi[3 * c + d] - glo[d]) / h[d]) + 1;
+                if (i0[d] < 0) i0[d] = 0;
+                if (i1[d] > G[d] - 1) i1[d] = G[d] - 1;
+            }
+            for (int x = i0[0]; x <= i1[0]; ++x)
+                for (int y = i0[1]; y <= i1[1]; ++y)
+                    for (int z = i0[2]; z <= i1[2]; ++z) {
+                        int64_t b = ((int64_t)x * G[1] + y) * G[2] + z;
+                        if (!pass) boff[b + 1]++;
+                        else lst[boff[b] + fill[b]++] = c;
+                    }
+        }
+        if (!pass) {
+            for (size_t b = 0; b < nb; ++b) boff[b + 1] += boff[b];
+        } else {
+#pragma omp parallel for schedule(dynamic, 256)
+            for (int64_t k = 0; k < n; ++k) {
+                v3 p = ld(pos + 3 * k);
+                double *pp = &p.x;
+                for (int d = 0; d < 3; ++d)
+                    if (periodic[d]) pp[d] = wrap_coord(pp[d], L[d]);
+                wrapped[3 * k] = p.x;
+                wrapped[3 * k + 1] = p.y;
+                wrapped[3 * k + 2] = p.z;
+                int ib[3], ok = 1;
+                for (int d = 0; d < 3; ++d) {
+                    ib[d] = (int)floor((pp[d] - glo[d]) / h[d]);
+                    if (ib[d] < 0) ib[d] = 0;
+                    if (ib[d] > G[d] - 1) ib[d] = G[d] - 1;
+                    if (pp[d] < glo[d] || pp[d] > ghi[d]) ok = 0;
+                }
+                int32_t found = -1;
+                if (ok) {
+                    int64_t b = ((int64_t)ib[0] * G[1] + ib[1]) * G[2] + ib[2];
+                    for (int64_t i = boff[b]; i < boff[b + 1]; ++i) {
+                        int64_t c = lst[i];
+                        if (p.x < lo[3 * c] || p.x > hi[3 * c] || p.y < lo[3 * c + 1] || p.y > hi[3 * c + 1] ||
+                            p.z < lo[3 * c + 2] || p.z > hi[3 * c + 2])
+                            continue;
+                        int r = inside_ray(tri, tri_off[c], tri_off[c + 1], p);
+                        if (r == UNCERTAIN) { found = -2; break; }
+                        if (r == 1) {
+                            if (found >= 0) { found = -2; break; }
+                            found = (int32_t)c;
+                        }
+                    }
+                }
+                cell[k] = found;
+            }
+            free(fill);
+            free(lst);
+        }
+    }
+    free(boff);
+}
+
+/* ------------------------------------------------------------- AICA loops */
+/* The force loops of §2.3 over the oracle's lists and binning, literally:
+ * real-real (DIL cells with Newton's third law, then same-cell pairs with
+ * sorted index k' > k) and real-referred (force on the real molecule only).
+ * Molecules are in binned order: cell c holds xs[cell_off[c] .. cell_off[c+1]).
+ * A referred molecule q of referred cell (src, n) sits at xs[q] + n.L.
+ * counts: evaluated {same, dil, referred}, within rc {same, dil, referred}.
+ * ev7: U and virial, real-referred pairs weighted 1/2 (each physical pair is
+ * evaluated from both of its sides). */
+static void pair_eval(const double *xp, const double *xq, const int32_t *n, const double *L, int a, int b,
+                      const double *eps, const double *sigma, double rc2, int shift, double *fp, double *fq,
+                      double w, double *ev, int64_t *within)
+{
+    double dx = (xp[0] - xq[0]) - L[0] * n[0];
+    double dy = (xp[1] - xq[1]) - L[1] * n[1];
+    double dz = (xp[2] - xq[2]) - L[2] * n[2];
+    double r2 = (dx * dx + dy * dy) + dz * dz;
+    if (!(r2 < rc2)) return;
+    double eab = sqrt(eps[a] * eps[b]), sab = 0.5 * (sigma[a] + sigma[b]), fs, u;
+    lj_pair(r2, eab, sab, &fs, &u);
+    if (shift) {
+        double fc, uc;
+        lj_pair(rc2, eab, sab, &fc, &uc);
+        u -= uc;
+    }
+    fp[0] += fs * dx; fp[1] += fs * dy; fp[2] += fs * dz;
+    if (fq) { fq[0] -= fs * dx; fq[1] -= fs * dy; fq[2] -= fs * dz; }
+    ev[0] += w * u;
+    ev[1] += w * dx * (fs * dx); ev[2] += w * dy * (fs * dy); ev[3] += w * dz * (fs * dz);
+    ev[4] += w * dx * (fs * dy); ev[5] += w * dx * (fs * dz); ev[6] += w * dy * (fs * dz);
+    (*within)++;
+}
+
+void oracle_aica_loop(int64_t n_cells, const int64_t *cell_off, const double *xs, const int32_t *sp,
+                      const double *eps, const double *sigma, double rc, const double *L, int shift,
+                      const int64_t *dil_off, const int32_t *dil_ids, int64_t n_ref, const int32_t *ref_src,
+                      const int32_t *ref_n, const int64_t *ref_off, const int32_t *ref_ids, double *F,
+                      double *ev7, int64_t *counts)
+{
+    double rc2 = rc * rc;
+    int32_t zero[3] = {0, 0, 0};
+    memset(ev7, 0, 7 * sizeof(double));
+    memset(counts, 0, 6 * sizeof(int64_t));
+    /* real-real */
+    for (int64_t I = 0; I < n_cells; ++I) {
+        for (int64_t k = cell_off[I]; k < cell_off[I + 1]; ++k) {
+            for (int64_t e = dil_off[I]; e < dil_off[I + 1]; ++e) {
+                int64_t J = dil_ids[e];
+                for (int64_t l = cell_off[J]; l < cell_off[J + 1]; ++l) {
+                    counts[1]++;
+                    pair_eval(xs + 3 * k, xs + 3 * l, zero, L, sp[k], sp[l], eps, sigma, rc2, shift, F + 3 * k,
+                              F + 3 * l, 1.0, ev7, &counts[4]);
+                }
+            }
+            for (int64_t k2 = cell_off[I]; k2 < cell_off[I + 1]; ++k2) {
+                if (!(k2 > k)) continue;
+                counts[0]++;
+                pair_eval(xs + 3 * k, xs + 3 * k2, zero, L, sp[k], sp[k2], eps, sigma, rc2, shift, F + 3 * k,
+                          F + 3 * k2, 1.0, ev7, &counts[3]);
+            }
+        }
+    }
+    /* real-referred */
+    for (int64_t M = 0; M < n_ref; ++M) {
+        int64_t c = ref_src[M];
+        for (int64_t q = cell_off[c]; q < cell_off[c + 1]; ++q) {
+            for (int64_t e = ref_off[M]; e < ref_off[M + 1]; ++e) {
+                int64_t N = ref_ids[e];
+                for (int64_t p = cell_off[N]; p < cell_off[N + 1]; ++p) {
+                    counts[2]++;
+                    pair_eval(xs + 3 * p, xs + 3 * q, ref_n + 3 * M, L, sp[p], sp[q], eps, sigma, rc2, shift,
+                              F + 3 * p, NULL, 0.5, ev7, &counts[5]);
+                }
+            }
+        }
+    }
+}
+
+int oracle_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
