@@ -1,0 +1,192 @@
+/*
+ * aica.h -- C ABI of the GB300 (sm_103a) AICA pair-force library.
+ *
+ * AICA, the Arbitrary Interacting Cells Algorithm (Macpherson & Reese,
+ * arXiv cs/0702131), evaluates short-range pair forces between molecules
+ * binned into the cells of an arbitrary polyhedral mesh: each cell carries a
+ * direct interaction list (DIL) of the cells it must interact with (§2.2),
+ * built once because the mesh is static, and periodic boundaries are handled
+ * by "referred" copies of cells and molecules (§2.2.1).  On one GPU only
+ * periodic referral exists.  Every compute step runs in hand-written CUDA
+ * kernels; there is no CPU fallback.
+ *
+ * Conventions
+ *   - All functions return an aica_status; on failure aica_last_error() gives
+ *     a thread-local message.  No exception crosses this boundary.
+ *   - "host" pointers are read during the call and may be freed afterwards.
+ *     "device" pointers are CUDA global memory owned by the caller; the
+ *     library reads inputs and writes outputs on `stream` (a cudaStream_t, or
+ *     NULL for the legacy default stream) and returns before the work ends
+ *     unless stated otherwise.
+ *   - The library owns the mesh, the interaction lists, the binned molecule
+ *     state and its workspaces (device memory allocated on the device that is
+ *     current at aica_mesh_create).  A mesh handle is not thread-safe.
+ *   - Reduced LJ units; rc and skin are absolute lengths.
+ */
+#ifndef AICA_H
+#define AICA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct aica_mesh aica_mesh; /* opaque, library-owned */
+
+typedef enum {
+    AICA_OK = 0,
+    AICA_ERR_INVALID_ARG = 1,  /* NULL pointer, negative size, unsupported option   */
+    AICA_ERR_BAD_MESH = 2,     /* open cell, inverted or non-star cell, bad index     */
+    AICA_ERR_OUTSIDE_MESH = 3, /* a molecule lies in no cell (see aica_bin_molecules) */
+    AICA_ERR_NOT_BUILT = 4,    /* forces requested before lists or binning            */
+    AICA_ERR_CAPACITY = 5,     /* a fixed per-cell limit of the kernels is exceeded   */
+    AICA_ERR_CUDA = 6,         /* a CUDA runtime call failed                          */
+    AICA_ERR_OOM = 7           /* device allocation failed                            */
+} aica_status;
+
+typedef enum { AICA_FP32 = 0, AICA_FP64 = 1 } aica_precision;
+
+/* Translational periodicity of the domain: an axis with periodic[k] != 0
+ * repeats with period L[k]; the mesh must fill [0, L[k]] along it. */
+typedef struct {
+    double L[3];
+    int32_t periodic[3];
+} aica_box;
+
+/* Lennard-Jones 12-6 parameters.  The paper names LJ molecules (§3) without
+ * printing the potential; this library uses u(r) = 4 eps ((s/r)^12 - (s/r)^6)
+ * truncated at r < rc, with Lorentz-Berthelot mixing eps_ab = sqrt(eps_a
+ * eps_b), sigma_ab = (sigma_a + sigma_b) / 2 and one absolute rc for every
+ * pair (the largest cut-off builds the lists, App. A). */
+typedef struct {
+    int32_t n_species;   /* S: 1..8 forward, 1..4 backward                 */
+    const double *eps;   /* host [S]                                       */
+    const double *sigma; /* host [S]                                       */
+    int32_t shift;       /* nonzero: subtract u(rc) from each pair's energy */
+} aica_lj;
+
+typedef struct {
+    int64_t n_cells;
+    int64_t n_dil;      /* entries of all direct interaction lists         */
+    int64_t n_ref;      /* referred cells                                  */
+    int64_t n_ref_ids;  /* entries of all referred-cell real-cell lists    */
+    int64_t n_ties;     /* cell-pair decisions within 1e-9 (rc+skin)^2     */
+    double rc, skin;
+} aica_list_info;
+
+/* Create a mesh from a face-based description (OpenFOAM style).  Defines the
+ * cells whose DILs §2.2 builds; the cell numbering is the caller's and is
+ * what "j > i" in App. A.1 refers to.
+ *   points        host [n_points*3] FP64 vertex coordinates
+ *   face_offsets  host [n_faces+1]; face f has vertices
+ *                 face_vertices[face_offsets[f] .. face_offsets[f+1])
+ *   owner         host [n_faces] cell on the side the right-handed normal
+ *                 leaves; neighbour host [n_faces] the other cell or -1
+ *   box           host; periodic axes of the domain
+ * Faces are split into fans from their lowest vertex id, so both cells of a
+ * face see the same triangles.  Each cell must be closed and star-shaped
+ * about the mean of its vertices (every tetrahedron from that point to a
+ * face triangle has positive volume), else AICA_ERR_BAD_MESH.  At most 32
+ * triangles, 24 vertices and 48 edges per cell (AICA_ERR_CAPACITY).
+ * Synchronous; allocates device memory on the current device. */
+aica_status aica_mesh_create(const double *points, int64_t n_points, const int64_t *face_offsets,
+                             const int64_t *face_vertices, int64_t n_faces, const int64_t *owner,
+                             const int64_t *neighbour, int64_t n_cells, const aica_box *box,
+                             aica_mesh **out);
+
+/* Free every library allocation of the mesh.  NULL is ignored. */
+void aica_mesh_destroy(aica_mesh *mesh);
+
+/* Build the interaction lists (§2.2, App. A): for cells i < j, j joins DIL(i)
+ * iff the minimum distance between the two closed triangulated polyhedra is
+ * below rc + skin (vertex-triangle and edge-edge distances, decided in FP64;
+ * this replaces the paper's vertex-vertex search and so has no twisted-mesh
+ * error).  Periodic referred cells (§2.2.1) are every (c, n), n a nonzero
+ * integer image vector, with at least one real cell J within rc + skin of
+ * c + n.L; each keeps the ascending list of such J.  Requires rc > 0,
+ * skin >= 0 and rc + skin < L/2 on periodic axes.  Runs on `stream` and
+ * synchronizes it before returning (the list sizes are needed on the host). */
+aica_status aica_build_interaction_list(aica_mesh *mesh, double rc, double skin, void *stream);
+
+/* Sizes of the current lists (host struct).  AICA_ERR_NOT_BUILT before a build. */
+aica_status aica_get_list_info(const aica_mesh *mesh, aica_list_info *info);
+
+/* Copy the lists to host buffers sized from aica_get_list_info:
+ *   dil_off [n_cells+1], dil_ids [n_dil]      DIL(i) = dil_ids[dil_off[i]..dil_off[i+1]), ascending
+ *   ref_src [n_ref], ref_n [n_ref*3]          referred cell m = source cell and image vector n
+ *   ref_off [n_ref+1], ref_ids [n_ref_ids]    its real cells, ascending
+ * Referred cells are sorted by (source, n) with n lexicographic.  Any
+ * pointer may be NULL to skip that array.  Synchronous. */
+aica_status aica_get_lists(const aica_mesh *mesh, int64_t *dil_off, int32_t *dil_ids, int32_t *ref_src,
+                           int32_t *ref_n, int64_t *ref_off, int32_t *ref_ids);
+
+/* Bin molecules into cells (§2.2: a molecule's cell must always be known).
+ *   pos      device [n*3] FP64 positions; periodic coordinates are wrapped
+ *            into [0, L) first
+ *   species  device [n] int32 in [0, S) (checked by aica_forces)
+ *   cell_of  device [n] out, optional: containing cell, -1 if none
+ *   order    device [n] out, optional: order[s] = original index of binned
+ *            slot s (stable counting sort by cell, then original index)
+ *   cell_off device [n_cells+1] out, optional: cell c holds slots
+ *            cell_off[c] .. cell_off[c+1])
+ * The containing cell is the unique cell that holds p + (e, e^2, e^3) for
+ * infinitesimal e > 0, so points on faces, edges and vertices have exactly
+ * one cell.  The binned state stays in the mesh for the force calls.  A
+ * molecule in no cell gets cell -1, no slot and zero force; the call then
+ * returns AICA_ERR_OUTSIDE_MESH (after synchronizing the stream) unless
+ * deferred checking is on (aica_set_deferred_checks). */
+aica_status aica_bin_molecules(aica_mesh *mesh, const double *pos, const int32_t *species, int64_t n,
+                               int32_t *cell_of, int32_t *order, int32_t *cell_off, void *stream);
+
+/* Forces, potential energy and virial over the AICA pair set (§2.3):
+ * same-cell pairs, DIL pairs with Newton's third law, and real-referred pairs
+ * acting on the real molecule only, for the last binned molecules.
+ *   prec   AICA_FP32: FP32 pair arithmetic on cell-local coordinates, FP64
+ *          energy/virial sums, and r^2 < rc^2 decided in FP64 whenever the
+ *          FP32 value lies within 1e-5 rc^2 of the cut-off;
+ *          AICA_FP64: all FP64.
+ *   force_out  device [n*3], float (FP32) or double (FP64), original order;
+ *              overwritten
+ *   ev_out     device double [7], optional: U, Wxx, Wyy, Wzz, Wxy, Wxz, Wyz
+ *              with W_ab = sum over pairs of r_a f_b, each physical pair once
+ *   counts_out device int64 [6], optional: evaluated pairs {same-cell, DIL,
+ *              real-referred}, then pairs within rc in the same order; each
+ *              real-referred pair is evaluated once from each side.
+ * AICA_ERR_NOT_BUILT without lists and binning. */
+aica_status aica_forces(aica_mesh *mesh, const aica_lj *lj, aica_precision prec, void *force_out,
+                        double *ev_out, int64_t *counts_out, void *stream);
+
+/* Adjoint of aica_forces for a loss L(F): given grad_force = dL/dF (device
+ * [n*3], prec's type, original order) compute
+ *   grad_pos   device [n*3] prec's type: dL/dx, a Hessian-vector product
+ *   grad_eps   device double [S], optional: dL/d eps_s
+ *   grad_sigma device double [S], optional: dL/d sigma_s
+ * Pair terms are recomputed over the same pair set (nothing is stored by the
+ * forward call).  A real-referred pair moves the real molecule's force, so
+ * its position gradient also reaches the source molecule of the referred
+ * copy.  The cut-off is not differentiated. */
+aica_status aica_forces_backward(aica_mesh *mesh, const aica_lj *lj, aica_precision prec,
+                                 const void *grad_force, void *grad_pos, double *grad_eps,
+                                 double *grad_sigma, void *stream);
+
+/* With deferred != 0, aica_bin_molecules and aica_forces do not synchronize
+ * to check device-side error flags; errors are reported by
+ * aica_check_status (which synchronizes `stream`). */
+aica_status aica_set_deferred_checks(aica_mesh *mesh, int deferred);
+aica_status aica_check_status(aica_mesh *mesh, void *stream);
+
+/* Number of kernels the last call on this mesh launched (for accounting). */
+int64_t aica_last_launch_count(const aica_mesh *mesh);
+
+/* Thread-local message of the last failure in this thread ("" if none). */
+const char *aica_last_error(void);
+
+/* Name of a status code. */
+const char *aica_status_string(aica_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AICA_H */

@@ -60,7 +60,7 @@ def lib():
         L = ctypes.CDLL(_SO)
         vp = ctypes.c_void_p
         L.oracle_lj.argtypes = [ctypes.c_int64, _f64, _i32, ctypes.c_int, _f64, _f64, ctypes.c_double, _f64,
-                                _i32, ctypes.c_int, vp, ctypes.c_int64, _f64, _f64, _f64, _i64]
+                                _i32, ctypes.c_int, vp, ctypes.c_int64, _f64, _f64, _f64, _f64, _i64]
         L.oracle_cell_pairs.argtypes = [_i64, _f64, _i64, _f64, _i64, _f64, _f64, _f64, ctypes.c_int64, _i64,
                                         ctypes.c_int64, ctypes.c_double, _i32, _f64, ctypes.c_int,
                                         ctypes.c_int64, _i64, _i32, _i32, _f64, _i64]
@@ -87,7 +87,8 @@ def lj(pos, species, eps, sigma, rc, box, shift=False, idx=None):
     """All-pairs minimum-image LJ forces (the plain definition).
 
     Returns dict(F [m,3], Fabs [m] = sum_l |f_kl|, U, W [6] (xx,yy,zz,xy,xz,yz),
-    pairs = number of unordered pairs within rc (only when idx is None)).
+    Uabs = sum |u|, Wabs = sum |r . f| over pairs, pairs = number of unordered
+    pairs within rc (only when idx is None)).
     Requires rc < L/2 on periodic axes, where the minimum image is unique.
     """
     pos = _c(pos, np.float64)
@@ -97,11 +98,12 @@ def lj(pos, species, eps, sigma, rc, box, shift=False, idx=None):
     F = np.zeros((m, 3))
     Fabs = np.zeros(m)
     ev = np.zeros(7)
+    ab = np.zeros(2)
     cnt = np.zeros(1, np.int64)
     lib().oracle_lj(n, pos, _c(species, np.int32), len(eps), _c(eps, np.float64), _c(sigma, np.float64),
                     float(rc), _c(box["L"], np.float64), _c(box["periodic"], np.int32), int(bool(shift)),
-                    None if idx_arr is None else idx_arr.ctypes.data, m, F, Fabs, ev, cnt)
-    out = dict(F=F, Fabs=Fabs, U=ev[0], W=ev[1:].copy())
+                    None if idx_arr is None else idx_arr.ctypes.data, m, F, Fabs, ev, ab, cnt)
+    out = dict(F=F, Fabs=Fabs, U=ev[0], W=ev[1:].copy(), Uabs=ab[0], Wabs=ab[1])
     if idx is None:
         out["pairs"] = int(cnt[0]) // 2
     return out

@@ -51,19 +51,20 @@ static double min_image(double d, double L, int periodic)
 /* Forces F[k] = sum_{l != k, r_kl < rc} f_kl for every k in idx (or all k when
  * idx is NULL), with Fabs[k] = sum_l |f_kl|.  ev7 gets U and the virial
  * W_ab = sum_pairs d_a f_b (xx, yy, zz, xy, xz, yz), each pair counted once
- * (half from each of its two molecules).  count gets the number of (k, l)
+ * (half from each of its two molecules); abs2 gets sum_pairs |u| and
+ * sum_pairs |r . f|, the scales of those sums.  count gets the number of (k, l)
  * ordered pairs within rc, i.e. twice the pair count when idx is NULL. */
 void oracle_lj(int64_t n, const double *pos, const int32_t *species, int S,
                const double *eps, const double *sigma, double rc, const double *L,
                const int32_t *periodic, int shift, const int64_t *idx, int64_t nidx,
-               double *F, double *Fabs, double *ev7, int64_t *count)
+               double *F, double *Fabs, double *ev7, double *abs2, int64_t *count)
 {
     double rc2 = rc * rc;
-    double U = 0, wxx = 0, wyy = 0, wzz = 0, wxy = 0, wxz = 0, wyz = 0;
+    double U = 0, wxx = 0, wyy = 0, wzz = 0, wxy = 0, wxz = 0, wyz = 0, Ua = 0, Va = 0;
     int64_t cnt = 0;
     int64_t m = idx ? nidx : n;
     (void)S;
-#pragma omp parallel for schedule(dynamic, 16) reduction(+ : U, wxx, wyy, wzz, wxy, wxz, wyz, cnt)
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : U, wxx, wyy, wzz, wxy, wxz, wyz, Ua, Va, cnt)
     for (int64_t t = 0; t < m; ++t) {
         int64_t k = idx ? idx[t] : t;
         double fx = 0, fy = 0, fz = 0, fa = 0;
@@ -90,6 +91,8 @@ void oracle_lj(int64_t n, const double *pos, const int32_t *species, int S,
             fz += fs * dz;
             fa += fabs(fs) * sqrt(r2);
             U += 0.5 * u;
+            Ua += 0.5 * fabs(u);
+            Va += 0.5 * fabs(fs) * r2;
             wxx += 0.5 * dx * (fs * dx);
             wyy += 0.5 * dy * (fs * dy);
             wzz += 0.5 * dz * (fs * dz);
@@ -106,6 +109,8 @@ void oracle_lj(int64_t n, const double *pos, const int32_t *species, int S,
     ev7[0] = U;
     ev7[1] = wxx; ev7[2] = wyy; ev7[3] = wzz;
     ev7[4] = wxy; ev7[5] = wxz; ev7[6] = wyz;
+    abs2[0] = Ua;
+    abs2[1] = Va;
     *count = cnt;
 }
 

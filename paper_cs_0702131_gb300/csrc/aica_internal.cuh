@@ -1,0 +1,119 @@
+// Internal state and helpers of the AICA library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/aica.h"
+
+namespace aica {
+
+// Per-cell limits of the list builder and binning kernels.
+constexpr int kMaxTri = 32;
+constexpr int kMaxVtx = 24;
+constexpr int kMaxEdg = 48;
+constexpr int kMaxSpecies = 8;
+constexpr int kMaxSpeciesBwd = 4;
+
+// Device-side error flags (bitwise OR into mesh->d_flags[0]).
+enum : unsigned {
+    kFlagOutside = 1u,   // a molecule lies in no cell
+    kFlagSpecies = 2u,   // a species index is out of range
+    kFlagCapacity = 4u,  // a per-cell capacity of a kernel was exceeded
+};
+
+// Thread-local last error message.
+void set_error(const char *fmt, ...);
+aica_status cuda_fail(cudaError_t e, const char *what);
+
+#define AICA_CUDA(call)                                        \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return aica::cuda_fail(e_, #call); \
+    } while (0)
+
+// A device buffer that only grows.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    cudaError_t reserve(size_t n) {
+        if (n <= bytes) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        cudaError_t e = cudaMalloc(&p, n);
+        if (e == cudaSuccess) bytes = n;
+        return e;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// One work entry of the pair schedule: real cell I interacts with the
+// molecules of cell j, translated by the image vector n.
+struct WorkEntry {
+    int32_t j;      // partner cell
+    int32_t n;      // image vector, 3 x int8 packed (x in bits 0-7, y 8-15, z 16-23)
+};
+
+__host__ __device__ inline int32_t pack_n(int nx, int ny, int nz) {
+    return (int32_t)(((unsigned)(nx & 0xff)) | ((unsigned)(ny & 0xff) << 8) | ((unsigned)(nz & 0xff) << 16));
+}
+__host__ __device__ inline int unpack_n(int32_t p, int axis) {
+    return (int)(signed char)((p >> (8 * axis)) & 0xff);
+}
+
+}  // namespace aica
+
+struct aica_mesh {
+    int device = 0;
+    int64_t n_cells = 0, n_points = 0;
+    aica_box box{};
+    int max_tri = 0, max_vtx = 0, max_edg = 0;
+
+    // Geometry (device, FP64).  Triangles are oriented out of their cell.
+    aica::DevBuf tri_off, tri, vtx_off, vtx, edg_off, edg;  // int32 offsets, double coords
+    aica::DevBuf ctr, rad, lo, hi, org;                      // [C*3] vertex mean, [C] radius, AABB, origin
+    aica::DevBuf ntri;                                       // [C] int32 triangle counts
+    // FP32 copies local to each cell's dyadic origin org_c = orgk_c * 2^-10.
+    aica::DevBuf orgk;                                       // [C*3] int32
+    aica::DevBuf tri32, vtx32, edg32, ctr32;                 // float, minus org_c
+    aica::DevBuf rad32;                                      // [C] float, rad rounded up
+    double max_local = 0;                                    // largest |local coordinate|
+    // Point-location grid: cells whose bounding box meets a bucket.
+    int G[3] = {1, 1, 1};
+    double glo[3] = {0, 0, 0}, gh[3] = {1, 1, 1};
+    aica::DevBuf bkt_off, bkt_cells;
+    // Host copies kept for the list builder's bucket grid.
+    std::vector<double> h_ctr, h_rad;
+
+    // Interaction lists (device), valid when built.
+    bool built = false;
+    double rc = 0, skin = 0;
+    int64_t n_dil = 0, n_ref = 0, n_ref_ids = 0, n_ties = 0, n_work = 0;
+    aica::DevBuf dil_off, dil_ids, ref_src, ref_n, ref_off, ref_ids;   // int32 (ref_n: 3 int32)
+    aica::DevBuf work_off, work, work_d32;   // [C+1] int32 (index of first DIL entry), WorkEntry, float4 shift
+    aica::DevBuf work_split;                 // [C] int32: first referred entry of each cell
+    aica::DevBuf proc_order;                 // [C] int32: cell processing order (spatially local)
+
+    // Binned molecules (device), valid when binned.
+    bool binned = false;
+    int64_t n_mol = 0, cap_mol = 0;
+    aica::DevBuf cell_of, order, cell_off, fill, xloc, xs64, scratch_i32, inv;
+    int max_species = -1;                    // from the last checked binning, -1 if unknown
+    aica::DevBuf facc, vsorted;              // force / gradient accumulators in binned order
+    aica::DevBuf acc;                        // double[16] sums + uint64 counters
+    aica::DevBuf flags;                      // unsigned[4] device error flags
+    aica::DevBuf params;                     // per-call parameter block
+    aica::DevBuf tmp;                        // general scratch
+
+    bool deferred = false;
+    int64_t launches = 0;
+};

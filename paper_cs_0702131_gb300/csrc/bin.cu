@@ -1,0 +1,282 @@
+// Molecule-to-cell binning (step a4; §2.2 requires each molecule's cell to be
+// known at every step).
+//
+// Kernels
+//   bin_locate   thread per molecule: wrap periodic coordinates, look up the
+//                point-location bucket, test candidate cells until one holds
+//                p + (e, e^2, e^3): tetrahedra by their four face planes,
+//                other (star-shaped) cells by the cone from the vertex mean
+//                through each face triangle.  FP32 filter on cell-local
+//                coordinates, FP64 and exact slow paths (predicates.cuh).
+//   bin_count    warp-aggregated histogram of cells (match_any + one atomic)
+//   (scan)       cell offsets
+//   bin_scatter  warp-aggregated slot claims
+//   bin_fixup    per-cell insertion sort by original index: the binned order
+//                is the stable counting sort by (cell, original index)
+//   bin_gather   sorted FP64 positions and float4 cell-local coordinates with
+//                the species in .w (the pair kernels' input layout)
+#include <math.h>
+
+#include <algorithm>
+
+#include "aica_internal.cuh"
+#include "predicates.cuh"
+#include "scan.cuh"
+
+namespace aica {
+namespace {
+
+struct BinArgs {
+    int64_t n;
+    const double *pos;
+    const int *species;
+    double L[3];
+    int per[3];
+    int G[3];
+    double glo[3], gh[3], ghi[3];
+    const int *bkt_off, *bkt_cells;
+    const int *tri_off, *ntri, *orgk;
+    const float *tri32, *ctr32;
+    const double *tri, *ctr;
+    float max_local;
+    int *cell_of;
+    unsigned *flags;
+};
+
+__device__ __forceinline__ double wrap_coord(double x, double L) {
+    if (x >= 0.0 && x < L) return x;
+    x = __dsub_rn(x, __dmul_rn(L, floor(__ddiv_rn(x, L))));
+    if (x >= L) x = __dsub_rn(x, L);
+    return x;
+}
+
+__device__ __forceinline__ float3 ld3f(const float *p) { return make_float3(p[0], p[1], p[2]); }
+
+// sign of O(a, b, c, p + (e, e^2, e^3)); FP32 filter then exact slow path
+__device__ __forceinline__ int orient(float3 a, float3 b, float3 c, float3 q, float scale, const double *a64,
+                                      const double *b64, const double *c64, const double *p64) {
+    int s = orient_f32(a, b, c, q, scale);
+    if (s) return s;
+    return orient_sos_slow(a64, b64, c64, p64);
+}
+
+__device__ bool cell_contains(const BinArgs &a, int c, float3 q, const double *p64) {
+    int t0 = a.tri_off[c], nt = a.ntri[c];
+    float scale = fmaxf(a.max_local, fmaxf(fabsf(q.x), fmaxf(fabsf(q.y), fabsf(q.z))));
+    if (nt == 4) {   // tetrahedron: convex, inside iff behind all four faces
+        for (int t = t0; t < t0 + 4; ++t) {
+            const float *T = a.tri32 + 9 * t;
+            const double *D = a.tri + 9 * t;
+            if (orient(ld3f(T), ld3f(T + 3), ld3f(T + 6), q, scale, D, D + 3, D + 6, p64) > 0) return false;
+        }
+        return true;
+    }
+    float3 C = ld3f(a.ctr32 + 3 * c);
+    const double *C64 = a.ctr + 3 * c;
+    for (int t = t0; t < t0 + nt; ++t) {
+        const float *T = a.tri32 + 9 * t;
+        const double *D = a.tri + 9 * t;
+        float3 x0 = ld3f(T), x1 = ld3f(T + 3), x2 = ld3f(T + 6);
+        // p in the cone from C through triangle (x0, x1, x2)?
+        if (orient(C, x0, x1, q, scale, C64, D, D + 3, p64) < 0) continue;
+        if (orient(C, x1, x2, q, scale, C64, D + 3, D + 6, p64) < 0) continue;
+        if (orient(C, x2, x0, q, scale, C64, D + 6, D, p64) < 0) continue;
+        return orient(x0, x1, x2, q, scale, D, D + 3, D + 6, p64) < 0;
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(256) bin_locate(BinArgs a) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= a.n) return;
+    double p[3];
+    bool ok = true;
+    int ib[3];
+    for (int d = 0; d < 3; ++d) {
+        p[d] = a.pos[3 * k + d];
+        if (a.per[d]) p[d] = wrap_coord(p[d], a.L[d]);
+        if (!(p[d] >= a.glo[d] && p[d] <= a.ghi[d])) ok = false;
+        ib[d] = min(max((int)floor((p[d] - a.glo[d]) / a.gh[d]), 0), a.G[d] - 1);
+    }
+    int found = -1;
+    if (ok) {
+        int b = (ib[0] * a.G[1] + ib[1]) * a.G[2] + ib[2];
+        // dyadic bucket origin: p relative to it is one rounding from exact
+        int kb[3];
+        float3 pb;
+        for (int d = 0; d < 3; ++d) kb[d] = (int)rint((a.glo[d] + (ib[d] + 0.5) * a.gh[d]) * 1024.0);
+        pb.x = (float)(p[0] - kb[0] * (1.0 / 1024.0));
+        pb.y = (float)(p[1] - kb[1] * (1.0 / 1024.0));
+        pb.z = (float)(p[2] - kb[2] * (1.0 / 1024.0));
+        for (int i = a.bkt_off[b]; i < a.bkt_off[b + 1]; ++i) {
+            int c = a.bkt_cells[i];
+            float3 q = make_float3(pb.x - (float)(a.orgk[3 * c] - kb[0]) * (1.0f / 1024.0f),
+                                   pb.y - (float)(a.orgk[3 * c + 1] - kb[1]) * (1.0f / 1024.0f),
+                                   pb.z - (float)(a.orgk[3 * c + 2] - kb[2]) * (1.0f / 1024.0f));
+            if (cell_contains(a, c, q, p)) {
+                found = c;
+                break;
+            }
+        }
+    }
+    a.cell_of[k] = found;
+    if (found < 0) atomicOr(a.flags, kFlagOutside);
+}
+
+__global__ void __launch_bounds__(256) bin_count(const int *cell_of, int64_t n, int *cnt) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int c = k < n ? cell_of[k] : -1;
+    unsigned same = __match_any_sync(0xffffffffu, c);
+    int lane = threadIdx.x & 31;
+    if (c >= 0 && lane == __ffs(same) - 1) atomicAdd(cnt + c, __popc(same));
+}
+
+__global__ void __launch_bounds__(256) bin_scatter(const int *cell_of, int64_t n, const int *cell_off, int *fill,
+                                                   int *order) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int c = k < n ? cell_of[k] : -1;
+    unsigned same = __match_any_sync(0xffffffffu, c);
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(same) - 1;
+    int base = 0;
+    if (c >= 0 && lane == leader) base = atomicAdd(fill + c, __popc(same));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (c >= 0) order[cell_off[c] + base + __popc(same & ((1u << lane) - 1u))] = (int)k;
+}
+
+__global__ void __launch_bounds__(256) bin_fixup(const int *cell_off, int C, int *order) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    int s = cell_off[c], e = cell_off[c + 1];
+    for (int i = s + 1; i < e; ++i) {
+        int v = order[i], j = i - 1;
+        while (j >= s && order[j] > v) {
+            order[j + 1] = order[j];
+            --j;
+        }
+        order[j + 1] = v;
+    }
+}
+
+__global__ void __launch_bounds__(256) bin_gather(BinArgs a, const int *order, const int *cell_off, int C,
+                                                  double *xs64, float4 *xloc, int *inv) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int sp = 0;
+    if (s < cell_off[C]) {
+        int k = order[s];
+        inv[k] = (int)s;
+        sp = a.species[k];
+    int c = a.cell_of[k];
+    double p[3];
+    for (int d = 0; d < 3; ++d) {
+        p[d] = a.pos[3 * (int64_t)k + d];
+        if (a.per[d]) p[d] = wrap_coord(p[d], a.L[d]);
+        xs64[3 * s + d] = p[d];
+    }
+    xloc[s] = make_float4((float)(p[0] - a.orgk[3 * c] * (1.0 / 1024.0)), (float)(p[1] - a.orgk[3 * c + 1] * (1.0 / 1024.0)),
+                          (float)(p[2] - a.orgk[3 * c + 2] * (1.0 / 1024.0)), __int_as_float(sp & (kMaxSpecies - 1)));
+    }
+    // largest species index (flags[1]) and out-of-range species (flags[0])
+    unsigned bad = (unsigned)sp >= (unsigned)kMaxSpecies;
+    int mx = __reduce_max_sync(0xffffffffu, sp < 0 ? kMaxSpecies : sp);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(a.flags, kFlagSpecies);
+    if ((threadIdx.x & 31) == 0) atomicMax((int *)a.flags + 1, mx);
+}
+
+}  // namespace
+}  // namespace aica
+
+using namespace aica;
+
+extern "C" aica_status aica_bin_molecules(aica_mesh *m, const double *pos, const int32_t *species, int64_t n,
+                                          int32_t *cell_of, int32_t *order, int32_t *cell_off, void *stream) {
+    if (!m) { set_error("aica_bin_molecules: mesh is NULL"); return AICA_ERR_INVALID_ARG; }
+    if (n < 0 || n > (int64_t)INT32_MAX / 2 || (n > 0 && (!pos || !species))) {
+        set_error("aica_bin_molecules: bad molecule arrays (n = %lld)", (long long)n);
+        return AICA_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int C = (int)m->n_cells;
+    m->launches = 0;
+    m->binned = false;
+    if (n > m->cap_mol) {
+        int64_t cap = std::max<int64_t>(n, 1024);
+        AICA_CUDA(m->cell_of.reserve(sizeof(int) * cap));
+        AICA_CUDA(m->order.reserve(sizeof(int) * cap));
+        AICA_CUDA(m->xloc.reserve(sizeof(float4) * cap));
+        AICA_CUDA(m->inv.reserve(sizeof(int) * cap));
+        AICA_CUDA(m->xs64.reserve(sizeof(double) * 3 * cap));
+        AICA_CUDA(m->facc.reserve(sizeof(double) * 4 * cap));
+        AICA_CUDA(m->vsorted.reserve(sizeof(double) * 4 * cap));
+        m->cap_mol = cap;
+    }
+    AICA_CUDA(m->cell_off.reserve(sizeof(int) * (C + 1)));
+    AICA_CUDA(m->fill.reserve(sizeof(int) * (C + 1)));
+    AICA_CUDA(m->scratch_i32.reserve(sizeof(int) * (scan_work_items(C) + 8)));
+    m->n_mol = n;
+    BinArgs a{};
+    a.n = n;
+    a.pos = pos;
+    a.species = species;
+    for (int d = 0; d < 3; ++d) {
+        a.L[d] = m->box.L[d];
+        a.per[d] = m->box.periodic[d] ? 1 : 0;
+        a.G[d] = m->G[d];
+        a.glo[d] = m->glo[d];
+        a.gh[d] = m->gh[d];
+        a.ghi[d] = m->glo[d] + m->G[d] * m->gh[d];
+    }
+    a.bkt_off = m->bkt_off.as<int>();
+    a.bkt_cells = m->bkt_cells.as<int>();
+    a.tri_off = m->tri_off.as<int>();
+    a.ntri = m->ntri.as<int>();
+    a.orgk = m->orgk.as<int>();
+    a.tri32 = m->tri32.as<float>();
+    a.ctr32 = m->ctr32.as<float>();
+    a.tri = m->tri.as<double>();
+    a.ctr = m->ctr.as<double>();
+    a.max_local = (float)(m->max_local * (1 + 1e-6));
+    a.cell_of = m->cell_of.as<int>();
+    a.flags = m->flags.as<unsigned>();
+    int *cnt = m->fill.as<int>();
+    int *off = m->cell_off.as<int>();
+    AICA_CUDA(cudaMemsetAsync(m->flags.p, 0, 16, st));
+    AICA_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (C + 1), st));
+    unsigned nb = (unsigned)((n + 255) / 256);
+    if (n > 0) {
+        bin_locate<<<nb, 256, 0, st>>>(a);
+        bin_count<<<nb, 256, 0, st>>>(a.cell_of, n, cnt);
+        m->launches += 2;
+    }
+    m->launches += exclusive_scan<int, int>(cnt, C, off, m->scratch_i32.as<int>(), st);
+    AICA_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (C + 1), st));
+    if (n > 0) {
+        bin_scatter<<<nb, 256, 0, st>>>(a.cell_of, n, off, cnt, m->order.as<int>());
+        bin_fixup<<<(C + 255) / 256, 256, 0, st>>>(off, C, m->order.as<int>());
+        AICA_CUDA(cudaMemsetAsync(m->inv.p, 0xff, sizeof(int) * n, st));
+        bin_gather<<<nb, 256, 0, st>>>(a, m->order.as<int>(), off, C, m->xs64.as<double>(), m->xloc.as<float4>(),
+                                       m->inv.as<int>());
+        m->launches += 3;
+    }
+    AICA_CUDA(cudaGetLastError());
+    if (cell_of && n) AICA_CUDA(cudaMemcpyAsync(cell_of, a.cell_of, sizeof(int) * n, cudaMemcpyDeviceToDevice, st));
+    if (order && n) AICA_CUDA(cudaMemcpyAsync(order, m->order.p, sizeof(int) * n, cudaMemcpyDeviceToDevice, st));
+    if (cell_off) AICA_CUDA(cudaMemcpyAsync(cell_off, off, sizeof(int) * (C + 1), cudaMemcpyDeviceToDevice, st));
+    m->binned = true;
+    m->max_species = -1;
+    if (!m->deferred) {
+        unsigned flags[2] = {0, 0};
+        AICA_CUDA(cudaMemcpyAsync(flags, m->flags.p, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        AICA_CUDA(cudaStreamSynchronize(st));
+        m->max_species = (int)flags[1];
+        if (flags[0] & kFlagSpecies) {
+            set_error("aica_bin_molecules: species index outside [0, %d)", kMaxSpecies);
+            return AICA_ERR_INVALID_ARG;
+        }
+        if (flags[0] & kFlagOutside) {
+            set_error("aica_bin_molecules: some molecules lie in no cell (cell_of = -1)");
+            return AICA_ERR_OUTSIDE_MESH;
+        }
+    }
+    return AICA_OK;
+}

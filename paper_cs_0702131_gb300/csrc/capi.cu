@@ -1,0 +1,60 @@
+// C-ABI glue: thread-local error messages, status names, deferred checks.
+#include <stdarg.h>
+#include <stdio.h>
+
+#include "aica_internal.cuh"
+
+namespace aica {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+aica_status cuda_fail(cudaError_t e, const char *what) {
+    set_error("CUDA error %d (%s) in %s", (int)e, cudaGetErrorString(e), what);
+    return e == cudaErrorMemoryAllocation ? AICA_ERR_OOM : AICA_ERR_CUDA;
+}
+
+}  // namespace aica
+
+extern "C" const char *aica_last_error(void) { return aica::g_err; }
+
+extern "C" const char *aica_status_string(aica_status s) {
+    switch (s) {
+        case AICA_OK: return "AICA_OK";
+        case AICA_ERR_INVALID_ARG: return "AICA_ERR_INVALID_ARG";
+        case AICA_ERR_BAD_MESH: return "AICA_ERR_BAD_MESH";
+        case AICA_ERR_OUTSIDE_MESH: return "AICA_ERR_OUTSIDE_MESH";
+        case AICA_ERR_NOT_BUILT: return "AICA_ERR_NOT_BUILT";
+        case AICA_ERR_CAPACITY: return "AICA_ERR_CAPACITY";
+        case AICA_ERR_CUDA: return "AICA_ERR_CUDA";
+        case AICA_ERR_OOM: return "AICA_ERR_OOM";
+    }
+    return "AICA_UNKNOWN_STATUS";
+}
+
+extern "C" aica_status aica_set_deferred_checks(aica_mesh *m, int deferred) {
+    if (!m) { aica::set_error("aica_set_deferred_checks: mesh is NULL"); return AICA_ERR_INVALID_ARG; }
+    m->deferred = deferred != 0;
+    return AICA_OK;
+}
+
+extern "C" aica_status aica_check_status(aica_mesh *m, void *stream) {
+    if (!m) { aica::set_error("aica_check_status: mesh is NULL"); return AICA_ERR_INVALID_ARG; }
+    unsigned flags[2] = {0, 0};
+    cudaStream_t st = (cudaStream_t)stream;
+    AICA_CUDA(cudaMemcpyAsync(flags, m->flags.p, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    AICA_CUDA(cudaStreamSynchronize(st));
+    AICA_CUDA(cudaGetLastError());
+    if (flags[0] & aica::kFlagSpecies) { aica::set_error("species index out of range"); return AICA_ERR_INVALID_ARG; }
+    if (flags[0] & aica::kFlagOutside) { aica::set_error("some molecules lie in no cell"); return AICA_ERR_OUTSIDE_MESH; }
+    if (flags[0] & aica::kFlagCapacity) { aica::set_error("a kernel capacity was exceeded"); return AICA_ERR_CAPACITY; }
+    return AICA_OK;
+}
+
+extern "C" int64_t aica_last_launch_count(const aica_mesh *m) { return m ? m->launches : 0; }

@@ -1,0 +1,578 @@
+// Interaction-list builder (steps a2, a3): direct interaction lists (§2.2,
+// App. A.1) and periodic referred cells with their real-cell lists (§2.2.1,
+// App. A.2), plus the per-cell pair schedule the force kernels walk.
+//
+// The paper builds DILs by a vertex-vertex search and notes it can miss
+// slivers of twisted cells (§2.2); here a cell pair is listed iff the exact
+// minimum distance between the two closed triangulated polyhedra is below
+// rc + skin.  The paper's iterated referral across patch segments (App. A.2)
+// reduces, for a translation-periodic box on one device, to enumerating
+// image vectors n directly: the result does not depend on evaluation order.
+//
+// Kernels
+//   lst_query<0/1>  warp per query cell A: candidates (B, n) from a centroid
+//                   bucket grid, FP32 sphere / vertex / bounding-box filters,
+//                   FP32 min distance with early exit, FP64 recomputation when
+//                   the FP32 value is within 1e-3 (rc+skin)^2 of the cut;
+//                   pass 0 counts, pass 1 writes keys (image, B)
+//   lst_sort        per-segment bitonic sort of the keys
+//   lst_classify    per-cell counts of DIL entries, referred cells, entries
+//   lst_fill        CSR outputs and the pair schedule
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "aica_internal.cuh"
+#include "geom.cuh"
+#include "scan.cuh"
+
+namespace aica {
+namespace {
+
+constexpr int kQWarps = 4;
+constexpr int kSortMax = 4096;
+
+struct QArgs {
+    int C;
+    double thr2;
+    float thr, thr2_lo, thr2_hi;
+    double L[3];
+    float Lf[3];
+    int per[3];
+    int G[3];
+    double g0[3], gh[3];
+    const int *bkt_off, *bkt_cells;
+    float rad_max;
+    const int *tri_off, *vtx_off, *edg_off, *orgk;
+    const float *tri32, *vtx32, *edg32, *ctr32, *rad32;
+    const double *tri, *vtx, *edg, *ctr;
+    int *count;
+    const long long *seg_off;
+    unsigned long long *keys;
+    unsigned long long *ties;
+};
+
+__device__ __forceinline__ V3<float> ldf(const float *p) { return {p[0], p[1], p[2]}; }
+__device__ __forceinline__ V3<double> ldd(const double *p) { return {p[0], p[1], p[2]}; }
+
+__device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+// FP64 minimum squared distance between cell A and cell B shifted by s.
+__device__ __noinline__ double min_d2_f64(const QArgs &a, int A, int B, V3<double> s) {
+    double m = INFINITY;
+    for (int i = a.vtx_off[A]; i < a.vtx_off[A + 1]; ++i) {
+        V3<double> p = ldd(a.vtx + 3 * i);
+        for (int t = a.tri_off[B]; t < a.tri_off[B + 1]; ++t) {
+            const double *T = a.tri + 9 * t;
+            m = fmin(m, d2_point_triangle(p, ldd(T) + s, ldd(T + 3) + s, ldd(T + 6) + s));
+        }
+    }
+    for (int i = a.vtx_off[B]; i < a.vtx_off[B + 1]; ++i) {
+        V3<double> p = ldd(a.vtx + 3 * i) + s;
+        for (int t = a.tri_off[A]; t < a.tri_off[A + 1]; ++t) {
+            const double *T = a.tri + 9 * t;
+            m = fmin(m, d2_point_triangle(p, ldd(T), ldd(T + 3), ldd(T + 6)));
+        }
+    }
+    for (int i = a.edg_off[A]; i < a.edg_off[A + 1]; ++i) {
+        V3<double> p0 = ldd(a.edg + 6 * i), p1 = ldd(a.edg + 6 * i + 3);
+        for (int j = a.edg_off[B]; j < a.edg_off[B + 1]; ++j)
+            m = fmin(m, d2_segment_segment(p0, p1, ldd(a.edg + 6 * j) + s, ldd(a.edg + 6 * j + 3) + s));
+    }
+    return m;
+}
+
+struct WarpA {
+    const float *T, *V, *E;   // shared: A's triangles, vertices, edges in A's frame
+    int nt, nv, ne;
+    V3<float> lo, hi, c;
+    float rad;
+    int ok[3];
+};
+
+// Decide whether cell B shifted by image n is within rc + skin of cell A:
+// bit 0 = listed, bit 1 = an FP64 decision within 1e-9 (rc+skin)^2 of the cut.
+// One out-of-line function serves both passes, so both make the same choices.
+__device__ __noinline__ int decide(const QArgs &a, const WarpA &w, int A, int B, int nx, int ny, int nz) {
+    // B's frame relative to A's: integer origin difference (exact) plus n.L
+    V3<float> D = {(float)(a.orgk[3 * B] - a.orgk[3 * A]) * (1.0f / 1024.0f) + (float)nx * a.Lf[0],
+                   (float)(a.orgk[3 * B + 1] - a.orgk[3 * A + 1]) * (1.0f / 1024.0f) + (float)ny * a.Lf[1],
+                   (float)(a.orgk[3 * B + 2] - a.orgk[3 * A + 2]) * (1.0f / 1024.0f) + (float)nz * a.Lf[2]};
+    V3<float> cB = ldf(a.ctr32 + 3 * B) + D - w.c;
+    float R = a.thr + w.rad + a.rad32[B];
+    float dc2 = dot3(cB, cB);
+    if (dc2 > R * R * 1.0001f + 1e-4f) return 0;
+    // vertex-vertex distances (an upper bound on the minimum) and B's box
+    float m = INFINITY;
+    V3<float> blo = {INFINITY, INFINITY, INFINITY}, bhi = {-INFINITY, -INFINITY, -INFINITY};
+    int v0 = a.vtx_off[B], v1 = a.vtx_off[B + 1];
+    for (int i = v0; i < v1; ++i) {
+        V3<float> q = ldf(a.vtx32 + 3 * i) + D;
+        blo = {fminf(blo.x, q.x), fminf(blo.y, q.y), fminf(blo.z, q.z)};
+        bhi = {fmaxf(bhi.x, q.x), fmaxf(bhi.y, q.y), fmaxf(bhi.z, q.z)};
+        for (int k = 0; k < w.nv; ++k) {
+            V3<float> d = q - ldf(w.V + 3 * k);
+            m = fminf(m, dot3(d, d));
+        }
+    }
+    if (m < a.thr2_lo) return 1;
+    float gx = fmaxf(0.f, fmaxf(blo.x - w.hi.x, w.lo.x - bhi.x));
+    float gy = fmaxf(0.f, fmaxf(blo.y - w.hi.y, w.lo.y - bhi.y));
+    float gz = fmaxf(0.f, fmaxf(blo.z - w.hi.z, w.lo.z - bhi.z));
+    if (gx * gx + gy * gy + gz * gz > a.thr2_hi) return 0;
+    // FP32 minimum distance with early acceptance
+    for (int t = a.tri_off[B]; t < a.tri_off[B + 1]; ++t) {
+        const float *T = a.tri32 + 9 * t;
+        V3<float> p0 = ldf(T) + D, p1 = ldf(T + 3) + D, p2 = ldf(T + 6) + D;
+        for (int k = 0; k < w.nv; ++k) m = fminf(m, d2_point_triangle(ldf(w.V + 3 * k), p0, p1, p2));
+        if (m < a.thr2_lo) return 1;
+    }
+    for (int i = v0; i < v1; ++i) {
+        V3<float> q = ldf(a.vtx32 + 3 * i) + D;
+        for (int t = 0; t < w.nt; ++t)
+            m = fminf(m, d2_point_triangle(q, ldf(w.T + 9 * t), ldf(w.T + 9 * t + 3), ldf(w.T + 9 * t + 6)));
+        if (m < a.thr2_lo) return 1;
+    }
+    for (int j = a.edg_off[B]; j < a.edg_off[B + 1]; ++j) {
+        V3<float> q0 = ldf(a.edg32 + 6 * j) + D, q1 = ldf(a.edg32 + 6 * j + 3) + D;
+        for (int k = 0; k < w.ne; ++k)
+            m = fminf(m, d2_segment_segment(ldf(w.E + 6 * k), ldf(w.E + 6 * k + 3), q0, q1));
+        if (m < a.thr2_lo) return 1;
+    }
+    if (m > a.thr2_hi) return 0;
+    // close to the cut: decide in FP64 on the original coordinates
+    V3<double> s = {nx * a.L[0], ny * a.L[1], nz * a.L[2]};
+    double d2 = min_d2_f64(a, A, B, s);
+    return (d2 < a.thr2 ? 1 : 0) | (fabs(d2 - a.thr2) <= 1e-9 * a.thr2 ? 2 : 0);
+}
+
+__device__ __forceinline__ unsigned long long make_key(int B, int nx, int ny, int nz) {
+    // sort key: image n' = -n lexicographic, then B
+    unsigned nk = ((unsigned)(-nx + 128) << 16) | ((unsigned)(-ny + 128) << 8) | (unsigned)(-nz + 128);
+    return ((unsigned long long)nk << 32) | (unsigned)B;
+}
+
+template <int PASS>
+__global__ void __launch_bounds__(32 * kQWarps) lst_query(QArgs a) {
+    __shared__ float sh[kQWarps][kMaxTri * 9 + kMaxVtx * 3 + kMaxEdg * 6];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpA w;
+    w.T = sh[wid];
+    w.V = w.T + kMaxTri * 9;
+    w.E = w.V + kMaxVtx * 3;
+    float *T = sh[wid], *V = T + kMaxTri * 9, *E = V + kMaxVtx * 3;
+    for (int A = blockIdx.x * kQWarps + wid; A < a.C; A += gridDim.x * kQWarps) {
+        int t0 = a.tri_off[A], v0 = a.vtx_off[A], e0 = a.edg_off[A];
+        w.nt = a.tri_off[A + 1] - t0;
+        w.nv = a.vtx_off[A + 1] - v0;
+        w.ne = a.edg_off[A + 1] - e0;
+        __syncwarp();
+        for (int i = lane; i < 9 * w.nt; i += 32) T[i] = a.tri32[9 * t0 + i];
+        for (int i = lane; i < 3 * w.nv; i += 32) V[i] = a.vtx32[3 * v0 + i];
+        for (int i = lane; i < 6 * w.ne; i += 32) E[i] = a.edg32[6 * e0 + i];
+        __syncwarp();
+        w.lo = {INFINITY, INFINITY, INFINITY};
+        w.hi = {-INFINITY, -INFINITY, -INFINITY};
+        for (int k = 0; k < w.nv; ++k) {
+            V3<float> q = ldf(V + 3 * k);
+            w.lo = {fminf(w.lo.x, q.x), fminf(w.lo.y, q.y), fminf(w.lo.z, q.z)};
+            w.hi = {fmaxf(w.hi.x, q.x), fmaxf(w.hi.y, q.y), fmaxf(w.hi.z, q.z)};
+        }
+        w.c = ldf(a.ctr32 + 3 * A);
+        w.rad = a.rad32[A];
+        // bucket range of the query sphere around A's vertex mean
+        int b0[3], b1[3];
+        double Rq = (double)a.thr + (double)w.rad + (double)a.rad_max;
+        for (int d = 0; d < 3; ++d) {
+            double cA = a.ctr[3 * A + d];
+            b0[d] = (int)floor((cA - Rq - a.g0[d]) / a.gh[d]);
+            b1[d] = (int)floor((cA + Rq - a.g0[d]) / a.gh[d]);
+            if (!a.per[d]) {
+                b0[d] = max(b0[d], 0);
+                b1[d] = min(b1[d], a.G[d] - 1);
+            }
+        }
+        int cnt = 0;
+        long long wbase = PASS ? a.seg_off[A] : 0;
+        for (int bx = b0[0]; bx <= b1[0]; ++bx) {
+            int wx = bx - floordiv(bx, a.G[0]) * a.G[0], nx = a.per[0] ? floordiv(bx, a.G[0]) : 0;
+            for (int by = b0[1]; by <= b1[1]; ++by) {
+                int wy = by - floordiv(by, a.G[1]) * a.G[1], ny = a.per[1] ? floordiv(by, a.G[1]) : 0;
+                for (int bz = b0[2]; bz <= b1[2]; ++bz) {
+                    int wz = bz - floordiv(bz, a.G[2]) * a.G[2], nz = a.per[2] ? floordiv(bz, a.G[2]) : 0;
+                    int b = (wx * a.G[1] + wy) * a.G[2] + wz;
+                    int s = a.bkt_off[b], e = a.bkt_off[b + 1];
+                    for (int base = s; base < e; base += 32) {
+                        int i = base + lane;
+                        int dec = 0;
+                        int B = -1;
+                        if (i < e) {
+                            B = a.bkt_cells[i];
+                            if (!(B == A && nx == 0 && ny == 0 && nz == 0)) dec = decide(a, w, A, B, nx, ny, nz);
+                        }
+                        bool acc = dec & 1;
+                        unsigned bal = __ballot_sync(0xffffffffu, acc);
+                        if (PASS == 0 && (dec & 2)) atomicAdd(a.ties, 1ull);
+                        if (PASS == 1 && acc) {
+                            long long slot = wbase + cnt + __popc(bal & ((1u << lane) - 1u));
+                            if (slot < a.seg_off[A + 1]) a.keys[slot] = make_key(B, nx, ny, nz);
+                        }
+                        cnt += __popc(bal);
+                    }
+                }
+            }
+        }
+        if (PASS == 0 && lane == 0) a.count[A] = cnt;
+        __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(256) lst_sort(const long long *seg_off, unsigned long long *keys, int C,
+                                                unsigned *flags) {
+    __shared__ unsigned long long s[kSortMax];
+    for (int A = blockIdx.x; A < C; A += gridDim.x) {
+        long long s0 = seg_off[A];
+        int len = (int)(seg_off[A + 1] - s0);
+        if (len <= 1) continue;
+        if (len > kSortMax) {
+            if (threadIdx.x == 0) atomicOr(flags, kFlagCapacity);
+            continue;
+        }
+        int P = 1;
+        while (P < len) P <<= 1;
+        for (int i = threadIdx.x; i < P; i += blockDim.x) s[i] = i < len ? keys[s0 + i] : ~0ull;
+        __syncthreads();
+        for (int k = 2; k <= P; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                    int l = i ^ j;
+                    if (l > i) {
+                        unsigned long long x = s[i], y = s[l];
+                        bool up = (i & k) == 0;
+                        if ((x > y) == up) {
+                            s[i] = y;
+                            s[l] = x;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        for (int i = threadIdx.x; i < len; i += blockDim.x) keys[s0 + i] = s[i];
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ void key_fields(unsigned long long k, int &B, int &npx, int &npy, int &npz) {
+    B = (int)(k & 0xffffffffu);
+    unsigned nk = (unsigned)(k >> 32);
+    npx = (int)((nk >> 16) & 0xff) - 128;
+    npy = (int)((nk >> 8) & 0xff) - 128;
+    npz = (int)(nk & 0xff) - 128;
+}
+
+__global__ void lst_classify(const long long *seg_off, const unsigned long long *keys, int C, int *c_dil, int *c_re,
+                             int *c_rc) {
+    int A = blockIdx.x * blockDim.x + threadIdx.x;
+    if (A >= C) return;
+    int nd = 0, nr = 0, ng = 0;
+    int px = 1000, py = 0, pz = 0;
+    for (long long i = seg_off[A]; i < seg_off[A + 1]; ++i) {
+        int B, x, y, z;
+        key_fields(keys[i], B, x, y, z);
+        if (x == 0 && y == 0 && z == 0) {
+            nd += B > A;
+        } else {
+            nr++;
+            if (x != px || y != py || z != pz) ng++;
+            px = x; py = y; pz = z;
+        }
+    }
+    c_dil[A] = nd;
+    c_re[A] = nr;
+    c_rc[A] = ng;
+}
+
+struct FillArgs {
+    int C;
+    const long long *seg_off;
+    const unsigned long long *keys;
+    const int *o_dil, *o_re, *o_rc;
+    const int *orgk;
+    double L[3];
+    int *dil_ids, *ref_src, *ref_n, *ref_off, *ref_ids;
+    int *work_off, *work_split;
+    WorkEntry *work;
+    float4 *work_d32;
+};
+
+__global__ void lst_fill(FillArgs f) {
+    int A = blockIdx.x * blockDim.x + threadIdx.x;
+    if (A > f.C) return;
+    if (A == f.C) {
+        f.work_off[f.C] = f.o_dil[f.C] + f.o_re[f.C];
+        f.ref_off[f.o_rc[f.C]] = f.o_re[f.C];
+        return;
+    }
+    int wd = f.o_dil[A], wr = f.o_re[A], g = f.o_rc[A];
+    int nd = f.o_dil[A + 1] - wd;
+    int w0 = wd + wr;
+    f.work_off[A] = w0;
+    f.work_split[A] = w0 + nd;
+    int id = 0, ir = 0;
+    int px = 1000, py = 0, pz = 0;
+    for (long long i = f.seg_off[A]; i < f.seg_off[A + 1]; ++i) {
+        int B, x, y, z;
+        key_fields(f.keys[i], B, x, y, z);
+        int slot;
+        if (x == 0 && y == 0 && z == 0) {
+            if (B <= A) continue;
+            f.dil_ids[wd + id] = B;
+            slot = w0 + id;
+            id++;
+        } else {
+            if (x != px || y != py || z != pz) {
+                f.ref_src[g] = A;
+                f.ref_n[3 * g] = x;
+                f.ref_n[3 * g + 1] = y;
+                f.ref_n[3 * g + 2] = z;
+                f.ref_off[g] = wr + ir;
+                g++;
+                px = x; py = y; pz = z;
+            }
+            f.ref_ids[wr + ir] = B;
+            slot = w0 + nd + ir;
+            ir++;
+        }
+        // partner B seen from A: its molecules shifted by n = -n'
+        int nx = -x, ny = -y, nz = -z;
+        f.work[slot] = WorkEntry{B, pack_n(nx, ny, nz)};
+        double dx = (double)(f.orgk[3 * B] - f.orgk[3 * A]) * (1.0 / 1024.0) + nx * f.L[0];
+        double dy = (double)(f.orgk[3 * B + 1] - f.orgk[3 * A + 1]) * (1.0 / 1024.0) + ny * f.L[1];
+        double dz = (double)(f.orgk[3 * B + 2] - f.orgk[3 * A + 2]) * (1.0 / 1024.0) + nz * f.L[2];
+        f.work_d32[slot] = make_float4((float)dx, (float)dy, (float)dz, 0.f);
+    }
+}
+
+}  // namespace
+}  // namespace aica
+
+using namespace aica;
+
+extern "C" aica_status aica_build_interaction_list(aica_mesh *m, double rc, double skin, void *stream) {
+    if (!m) { set_error("aica_build_interaction_list: mesh is NULL"); return AICA_ERR_INVALID_ARG; }
+    if (!(rc > 0) || !(skin >= 0) || !isfinite(rc + skin)) {
+        set_error("aica_build_interaction_list: need rc > 0 and skin >= 0");
+        return AICA_ERR_INVALID_ARG;
+    }
+    double thr = rc + skin;
+    for (int d = 0; d < 3; ++d)
+        if (m->box.periodic[d] && !(thr < 0.5 * m->box.L[d])) {
+            set_error("aica_build_interaction_list: rc + skin must be below L/2 on periodic axis %d", d);
+            return AICA_ERR_INVALID_ARG;
+        }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int C = (int)m->n_cells;
+    m->launches = 0;
+    m->built = false;
+
+    // ---- centroid bucket grid (host): about one cell per bucket
+    QArgs a{};
+    double lo[3], hi[3], vol = 1;
+    for (int d = 0; d < 3; ++d) {
+        if (m->box.periodic[d]) {
+            lo[d] = 0;
+            hi[d] = m->box.L[d];
+        } else {
+            lo[d] = INFINITY;
+            hi[d] = -INFINITY;
+            for (int c = 0; c < C; ++c) {
+                lo[d] = std::min(lo[d], m->h_ctr[3 * c + d]);
+                hi[d] = std::max(hi[d], m->h_ctr[3 * c + d]);
+            }
+            hi[d] = std::max(hi[d], lo[d] + 1e-9);
+        }
+        vol *= hi[d] - lo[d];
+    }
+    double h0 = cbrt(vol / C);
+    int64_t nb = 1;
+    for (int d = 0; d < 3; ++d) {
+        a.G[d] = std::max(1, std::min(2048, (int)floor((hi[d] - lo[d]) / h0)));
+        a.g0[d] = lo[d];
+        a.gh[d] = (hi[d] - lo[d]) / a.G[d];
+        nb *= a.G[d];
+    }
+    std::vector<int> boff(nb + 1, 0), bcell(C), bidx(C);
+    for (int c = 0; c < C; ++c) {
+        int ix[3];
+        for (int d = 0; d < 3; ++d)
+            ix[d] = std::min(a.G[d] - 1, std::max(0, (int)floor((m->h_ctr[3 * c + d] - a.g0[d]) / a.gh[d])));
+        bidx[c] = (ix[0] * a.G[1] + ix[1]) * a.G[2] + ix[2];
+        boff[bidx[c] + 1]++;
+    }
+    for (int64_t b = 0; b < nb; ++b) boff[b + 1] += boff[b];
+    {
+        std::vector<int> fl(boff.begin(), boff.end() - 1);
+        for (int c = 0; c < C; ++c) bcell[fl[bidx[c]]++] = c;
+    }
+    float rad_max = 0;
+    for (int c = 0; c < C; ++c) rad_max = std::max(rad_max, (float)m->h_rad[c]);
+
+    DevBuf d_boff, d_bcell, d_cnt, d_seg, d_keys, d_scan, d_ties;
+    auto fail = [&](cudaError_t e, const char *w) {
+        d_boff.release(); d_bcell.release(); d_cnt.release(); d_seg.release(); d_keys.release();
+        d_scan.release(); d_ties.release();
+        return cuda_fail(e, w);
+    };
+#define CK(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) return fail(e_, #x); } while (0)
+    CK(d_boff.reserve(sizeof(int) * (nb + 1)));
+    CK(d_bcell.reserve(sizeof(int) * C));
+    CK(cudaMemcpyAsync(d_boff.p, boff.data(), sizeof(int) * (nb + 1), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_bcell.p, bcell.data(), sizeof(int) * C, cudaMemcpyHostToDevice, st));
+    CK(d_cnt.reserve(sizeof(int) * 3 * (C + 1)));
+    CK(d_seg.reserve(sizeof(long long) * (C + 1)));
+    CK(d_scan.reserve(sizeof(long long) * (scan_work_items(C) + 8)));
+    CK(d_ties.reserve(sizeof(unsigned long long)));
+    CK(cudaMemsetAsync(d_ties.p, 0, sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(m->flags.p, 0, 16, st));
+
+    a.C = C;
+    a.thr = (float)thr;
+    a.thr2 = thr * thr;
+    a.thr2_lo = (float)(a.thr2 * (1 - 1e-3));
+    a.thr2_hi = (float)(a.thr2 * (1 + 1e-3));
+    for (int d = 0; d < 3; ++d) {
+        a.L[d] = m->box.periodic[d] ? m->box.L[d] : 0.0;
+        a.Lf[d] = (float)a.L[d];
+        a.per[d] = m->box.periodic[d] ? 1 : 0;
+    }
+    a.bkt_off = d_boff.as<int>();
+    a.bkt_cells = d_bcell.as<int>();
+    a.rad_max = rad_max;
+    a.tri_off = m->tri_off.as<int>(); a.vtx_off = m->vtx_off.as<int>(); a.edg_off = m->edg_off.as<int>();
+    a.orgk = m->orgk.as<int>();
+    a.tri32 = m->tri32.as<float>(); a.vtx32 = m->vtx32.as<float>(); a.edg32 = m->edg32.as<float>();
+    a.ctr32 = m->ctr32.as<float>(); a.rad32 = m->rad32.as<float>();
+    a.tri = m->tri.as<double>(); a.vtx = m->vtx.as<double>(); a.edg = m->edg.as<double>(); a.ctr = m->ctr.as<double>();
+    a.count = d_cnt.as<int>();
+    a.ties = d_ties.as<unsigned long long>();
+
+    int qblocks = (int)std::min<int64_t>((C + kQWarps - 1) / kQWarps, 152 * 64);
+    lst_query<0><<<qblocks, 32 * kQWarps, 0, st>>>(a);
+    m->launches += 1;
+    m->launches += exclusive_scan<long long, int>(d_cnt.as<int>(), C, d_seg.as<long long>(), d_scan.as<long long>(), st);
+    long long total = 0;
+    CK(cudaMemcpyAsync(&total, d_seg.as<long long>() + C, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    CK(d_keys.reserve(sizeof(unsigned long long) * std::max<long long>(total, 1)));
+    a.seg_off = d_seg.as<long long>();
+    a.keys = d_keys.as<unsigned long long>();
+    lst_query<1><<<qblocks, 32 * kQWarps, 0, st>>>(a);
+    lst_sort<<<(unsigned)std::min<int64_t>(C, 152 * 32), 256, 0, st>>>(a.seg_off, a.keys, C, m->flags.as<unsigned>());
+    int *c_dil = d_cnt.as<int>(), *c_re = c_dil + (C + 1), *c_rc = c_re + (C + 1);
+    lst_classify<<<(C + 255) / 256, 256, 0, st>>>(a.seg_off, a.keys, C, c_dil, c_re, c_rc);
+    m->launches += 3;
+    CK(m->dil_off.reserve(sizeof(int) * (C + 1)));
+    CK(m->tmp.reserve(sizeof(int) * 2 * (C + 1) + sizeof(int) * (scan_work_items(C) + 8)));
+    int *o_re = m->tmp.as<int>(), *o_rc = o_re + (C + 1), *sw = o_rc + (C + 1);
+    m->launches += exclusive_scan<int, int>(c_dil, C, m->dil_off.as<int>(), sw, st);
+    m->launches += exclusive_scan<int, int>(c_re, C, o_re, sw, st);
+    m->launches += exclusive_scan<int, int>(c_rc, C, o_rc, sw, st);
+    int tot[3];
+    unsigned flags = 0;
+    unsigned long long ties = 0;
+    CK(cudaMemcpyAsync(&tot[0], m->dil_off.as<int>() + C, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&tot[1], o_re + C, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&tot[2], o_rc + C, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&flags, m->flags.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&ties, d_ties.p, sizeof(ties), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (flags & kFlagCapacity) {
+        fail(cudaSuccess, "");
+        set_error("aica_build_interaction_list: a cell has more than %d neighbour cells", kSortMax);
+        return AICA_ERR_CAPACITY;
+    }
+    int64_t n_work = (int64_t)tot[0] + tot[1];
+    CK(m->dil_ids.reserve(sizeof(int) * std::max(tot[0], 1)));
+    CK(m->ref_src.reserve(sizeof(int) * std::max(tot[2], 1)));
+    CK(m->ref_n.reserve(sizeof(int) * 3 * std::max(tot[2], 1)));
+    CK(m->ref_off.reserve(sizeof(int) * (tot[2] + 1)));
+    CK(m->ref_ids.reserve(sizeof(int) * std::max(tot[1], 1)));
+    CK(m->work_off.reserve(sizeof(int) * (C + 1)));
+    CK(m->work_split.reserve(sizeof(int) * C));
+    CK(m->work.reserve(sizeof(WorkEntry) * std::max<int64_t>(n_work, 1)));
+    CK(m->work_d32.reserve(sizeof(float4) * std::max<int64_t>(n_work, 1)));
+    FillArgs f{};
+    f.C = C;
+    f.seg_off = a.seg_off;
+    f.keys = a.keys;
+    f.o_dil = m->dil_off.as<int>();
+    f.o_re = o_re;
+    f.o_rc = o_rc;
+    f.orgk = a.orgk;
+    for (int d = 0; d < 3; ++d) f.L[d] = a.L[d];
+    f.dil_ids = m->dil_ids.as<int>();
+    f.ref_src = m->ref_src.as<int>();
+    f.ref_n = m->ref_n.as<int>();
+    f.ref_off = m->ref_off.as<int>();
+    f.ref_ids = m->ref_ids.as<int>();
+    f.work_off = m->work_off.as<int>();
+    f.work_split = m->work_split.as<int>();
+    f.work = m->work.as<WorkEntry>();
+    f.work_d32 = m->work_d32.as<float4>();
+    lst_fill<<<(C + 1 + 255) / 256, 256, 0, st>>>(f);
+    m->launches += 1;
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+#undef CK
+    d_boff.release(); d_bcell.release(); d_cnt.release(); d_seg.release(); d_keys.release(); d_scan.release();
+    d_ties.release();
+    m->n_dil = tot[0];
+    m->n_ref_ids = tot[1];
+    m->n_ref = tot[2];
+    m->n_work = n_work;
+    m->n_ties = (int64_t)ties;
+    m->rc = rc;
+    m->skin = skin;
+    m->built = true;
+    return AICA_OK;
+}
+
+extern "C" aica_status aica_get_list_info(const aica_mesh *m, aica_list_info *info) {
+    if (!m || !info) { set_error("aica_get_list_info: NULL argument"); return AICA_ERR_INVALID_ARG; }
+    if (!m->built) { set_error("aica_get_list_info: lists not built"); return AICA_ERR_NOT_BUILT; }
+    info->n_cells = m->n_cells;
+    info->n_dil = m->n_dil;
+    info->n_ref = m->n_ref;
+    info->n_ref_ids = m->n_ref_ids;
+    info->n_ties = m->n_ties;
+    info->rc = m->rc;
+    info->skin = m->skin;
+    return AICA_OK;
+}
+
+extern "C" aica_status aica_get_lists(const aica_mesh *m, int64_t *dil_off, int32_t *dil_ids, int32_t *ref_src,
+                                      int32_t *ref_n, int64_t *ref_off, int32_t *ref_ids) {
+    if (!m) { set_error("aica_get_lists: mesh is NULL"); return AICA_ERR_INVALID_ARG; }
+    if (!m->built) { set_error("aica_get_lists: lists not built"); return AICA_ERR_NOT_BUILT; }
+    const int64_t C = m->n_cells;
+    if (dil_off) {
+        std::vector<int> t(C + 1);
+        AICA_CUDA(cudaMemcpy(t.data(), m->dil_off.p, sizeof(int) * (C + 1), cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i <= C; ++i) dil_off[i] = t[i];
+    }
+    if (dil_ids && m->n_dil)
+        AICA_CUDA(cudaMemcpy(dil_ids, m->dil_ids.p, sizeof(int) * m->n_dil, cudaMemcpyDeviceToHost));
+    if (ref_src && m->n_ref)
+        AICA_CUDA(cudaMemcpy(ref_src, m->ref_src.p, sizeof(int) * m->n_ref, cudaMemcpyDeviceToHost));
+    if (ref_n && m->n_ref)
+        AICA_CUDA(cudaMemcpy(ref_n, m->ref_n.p, sizeof(int) * 3 * m->n_ref, cudaMemcpyDeviceToHost));
+    if (ref_off) {
+        std::vector<int> t(m->n_ref + 1);
+        AICA_CUDA(cudaMemcpy(t.data(), m->ref_off.p, sizeof(int) * (m->n_ref + 1), cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i <= m->n_ref; ++i) ref_off[i] = t[i];
+    }
+    if (ref_ids && m->n_ref_ids)
+        AICA_CUDA(cudaMemcpy(ref_ids, m->ref_ids.p, sizeof(int) * m->n_ref_ids, cudaMemcpyDeviceToHost));
+    return AICA_OK;
+}

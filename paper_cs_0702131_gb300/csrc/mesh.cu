@@ -1,0 +1,317 @@
+// Mesh ingest: validation, fan triangulation, per-cell geometry, dyadic cell
+// origins and the point-location bucket grid (step a1 of the hot path; runs
+// once, like the list construction it feeds, App. A).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "aica_internal.cuh"
+
+namespace {
+
+struct CellTri {
+    int64_t cell;
+    int64_t a, b, c;
+};
+
+template <class T>
+cudaError_t upload(aica::DevBuf &buf, const std::vector<T> &h) {
+    size_t n = h.size() * sizeof(T);
+    cudaError_t e = buf.reserve(n > 0 ? n : sizeof(T));
+    if (e != cudaSuccess) return e;
+    if (n) e = cudaMemcpy(buf.p, h.data(), n, cudaMemcpyHostToDevice);
+    return e;
+}
+
+}  // namespace
+
+extern "C" aica_status aica_mesh_create(const double *points, int64_t n_points, const int64_t *face_offsets,
+                                        const int64_t *face_vertices, int64_t n_faces, const int64_t *owner,
+                                        const int64_t *neighbour, int64_t n_cells, const aica_box *box,
+                                        aica_mesh **out) {
+    using namespace aica;
+    if (!out) { set_error("aica_mesh_create: out is NULL"); return AICA_ERR_INVALID_ARG; }
+    *out = nullptr;
+    if (!points || !face_offsets || !face_vertices || !owner || !neighbour || !box) {
+        set_error("aica_mesh_create: NULL input array");
+        return AICA_ERR_INVALID_ARG;
+    }
+    if (n_points < 4 || n_faces < 4 || n_cells < 1 || n_cells > (int64_t)INT32_MAX / 2) {
+        set_error("aica_mesh_create: bad sizes (points %lld, faces %lld, cells %lld)", (long long)n_points,
+                  (long long)n_faces, (long long)n_cells);
+        return AICA_ERR_INVALID_ARG;
+    }
+    for (int d = 0; d < 3; ++d)
+        if (box->periodic[d] && !(box->L[d] > 0 && isfinite(box->L[d]))) {
+            set_error("aica_mesh_create: periodic axis %d needs L > 0", d);
+            return AICA_ERR_INVALID_ARG;
+        }
+
+    // ---- faces -> oriented triangles per cell (fan from the lowest vertex id)
+    std::vector<int64_t> tcount(n_cells + 1, 0);
+    if (face_offsets[0] != 0) { set_error("face_offsets[0] must be 0"); return AICA_ERR_BAD_MESH; }
+    for (int64_t f = 0; f < n_faces; ++f) {
+        int64_t k = face_offsets[f + 1] - face_offsets[f];
+        if (k < 3) { set_error("face %lld has %lld vertices", (long long)f, (long long)k); return AICA_ERR_BAD_MESH; }
+        if (owner[f] < 0 || owner[f] >= n_cells || neighbour[f] < -1 || neighbour[f] >= n_cells ||
+            neighbour[f] == owner[f]) {
+            set_error("face %lld: bad owner/neighbour", (long long)f);
+            return AICA_ERR_BAD_MESH;
+        }
+        tcount[owner[f] + 1] += k - 2;
+        if (neighbour[f] >= 0) tcount[neighbour[f] + 1] += k - 2;
+    }
+    for (int64_t c = 0; c < n_cells; ++c) tcount[c + 1] += tcount[c];
+    int64_t T = tcount[n_cells];
+    std::vector<int64_t> tv(3 * T);
+    std::vector<int64_t> fillc(n_cells, 0);
+    for (int64_t f = 0; f < n_faces; ++f) {
+        const int64_t *v = face_vertices + face_offsets[f];
+        int64_t k = face_offsets[f + 1] - face_offsets[f];
+        int64_t r = 0;
+        for (int64_t i = 0; i < k; ++i) {
+            if (v[i] < 0 || v[i] >= n_points) { set_error("face %lld: vertex out of range", (long long)f); return AICA_ERR_BAD_MESH; }
+            if (v[i] < v[r]) r = i;
+        }
+        for (int64_t i = 1; i + 1 < k; ++i) {
+            int64_t a = v[r], b = v[(r + i) % k], c = v[(r + i + 1) % k];
+            int64_t o = tcount[owner[f]] + fillc[owner[f]]++;
+            tv[3 * o] = a; tv[3 * o + 1] = b; tv[3 * o + 2] = c;
+            if (neighbour[f] >= 0) {
+                int64_t q = tcount[neighbour[f]] + fillc[neighbour[f]]++;
+                tv[3 * q] = a; tv[3 * q + 1] = c; tv[3 * q + 2] = b;
+            }
+        }
+    }
+
+    // ---- per-cell checks and geometry
+    std::vector<int32_t> h_tri_off(n_cells + 1), h_vtx_off(n_cells + 1), h_edg_off(n_cells + 1), h_ntri(n_cells);
+    std::vector<double> h_tri(9 * T), h_ctr(3 * n_cells), h_rad(n_cells), h_lo(3 * n_cells), h_hi(3 * n_cells),
+        h_org(3 * n_cells);
+    std::vector<double> h_vtx, h_edg;
+    std::vector<int32_t> h_orgk(3 * n_cells);
+    h_vtx.reserve(3 * T);
+    h_edg.reserve(6 * T);
+    int max_tri = 0, max_vtx = 0, max_edg = 0;
+    std::vector<int64_t> vs, es;
+    std::vector<std::pair<int64_t, int64_t>> de;
+    h_tri_off[0] = h_vtx_off[0] = h_edg_off[0] = 0;
+    for (int64_t c = 0; c < n_cells; ++c) {
+        int64_t t0 = tcount[c], t1 = tcount[c + 1];
+        int nt = (int)(t1 - t0);
+        vs.clear(); de.clear();
+        for (int64_t t = t0; t < t1; ++t)
+            for (int i = 0; i < 3; ++i) {
+                vs.push_back(tv[3 * t + i]);
+                de.emplace_back(tv[3 * t + i], tv[3 * t + (i + 1) % 3]);
+            }
+        std::sort(vs.begin(), vs.end());
+        vs.erase(std::unique(vs.begin(), vs.end()), vs.end());
+        // closed, consistently oriented surface: every directed edge once, its reverse once
+        std::sort(de.begin(), de.end());
+        bool closed = nt >= 4;
+        for (size_t i = 0; closed && i < de.size(); ++i) {
+            if (i + 1 < de.size() && de[i] == de[i + 1]) closed = false;
+            if (!std::binary_search(de.begin(), de.end(), std::make_pair(de[i].second, de[i].first))) closed = false;
+        }
+        if (!closed) { set_error("cell %lld is not a closed oriented surface", (long long)c); return AICA_ERR_BAD_MESH; }
+        int ne = (int)de.size() / 2;
+        if (nt > kMaxTri || (int)vs.size() > kMaxVtx || ne > kMaxEdg) {
+            set_error("cell %lld exceeds %d triangles / %d vertices / %d edges", (long long)c, kMaxTri, kMaxVtx, kMaxEdg);
+            return AICA_ERR_CAPACITY;
+        }
+        max_tri = std::max(max_tri, nt);
+        max_vtx = std::max(max_vtx, (int)vs.size());
+        max_edg = std::max(max_edg, ne);
+        double C[3] = {0, 0, 0}, lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int64_t v : vs)
+            for (int d = 0; d < 3; ++d) {
+                double x = points[3 * v + d];
+                if (!isfinite(x)) { set_error("vertex %lld is not finite", (long long)v); return AICA_ERR_BAD_MESH; }
+                C[d] += x;
+                lo[d] = std::min(lo[d], x);
+                hi[d] = std::max(hi[d], x);
+            }
+        double rad = 0;
+        for (int d = 0; d < 3; ++d) C[d] /= (double)vs.size();
+        for (int64_t v : vs) {
+            double s = 0;
+            for (int d = 0; d < 3; ++d) s += (points[3 * v + d] - C[d]) * (points[3 * v + d] - C[d]);
+            rad = std::max(rad, sqrt(s));
+            h_vtx.insert(h_vtx.end(), points + 3 * v, points + 3 * v + 3);
+        }
+        for (int d = 0; d < 3; ++d) {
+            if (box->periodic[d] && (lo[d] < -1e-9 * box->L[d] || hi[d] > box->L[d] * (1 + 1e-9))) {
+                set_error("cell %lld leaves the periodic box on axis %d", (long long)c, d);
+                return AICA_ERR_BAD_MESH;
+            }
+            h_ctr[3 * c + d] = C[d];
+            h_lo[3 * c + d] = lo[d];
+            h_hi[3 * c + d] = hi[d];
+            h_org[3 * c + d] = rint(C[d] * 1024.0) / 1024.0;   // dyadic: exact in FP32 differences
+            if (fabs(h_org[3 * c + d]) > 1e6) { set_error("cell %lld: coordinates beyond 1e6", (long long)c); return AICA_ERR_BAD_MESH; }
+            h_orgk[3 * c + d] = (int32_t)rint(C[d] * 1024.0);
+        }
+        h_rad[c] = rad;
+        // star-shaped about C: every (C, triangle) tetrahedron has positive volume
+        for (int64_t t = t0; t < t1; ++t) {
+            const double *a = points + 3 * tv[3 * t], *b = points + 3 * tv[3 * t + 1], *e = points + 3 * tv[3 * t + 2];
+            double u[3], w[3], q[3];
+            for (int d = 0; d < 3; ++d) { u[d] = a[d] - C[d]; w[d] = b[d] - C[d]; q[d] = e[d] - C[d]; }
+            double vol = u[0] * (w[1] * q[2] - w[2] * q[1]) - u[1] * (w[0] * q[2] - w[2] * q[0]) +
+                         u[2] * (w[0] * q[1] - w[1] * q[0]);
+            double scale = sqrt((u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) * (w[0] * w[0] + w[1] * w[1] + w[2] * w[2]) *
+                                (q[0] * q[0] + q[1] * q[1] + q[2] * q[2]));
+            if (!(vol > 1e-12 * scale)) {
+                set_error("cell %lld: tetrahedron from the vertex mean to triangle %lld is not positive",
+                          (long long)c, (long long)(t - t0));
+                return AICA_ERR_BAD_MESH;
+            }
+            for (int i = 0; i < 3; ++i)
+                for (int d = 0; d < 3; ++d) h_tri[9 * t + 3 * i + d] = points[3 * tv[3 * t + i] + d];
+        }
+        // unique undirected edges (fan diagonals included)
+        for (auto &p : de)
+            if (p.first < p.second) {
+                h_edg.insert(h_edg.end(), points + 3 * p.first, points + 3 * p.first + 3);
+                h_edg.insert(h_edg.end(), points + 3 * p.second, points + 3 * p.second + 3);
+            }
+        h_tri_off[c + 1] = (int32_t)t1;
+        h_vtx_off[c + 1] = h_vtx_off[c] + (int32_t)vs.size();
+        h_edg_off[c + 1] = h_edg_off[c] + ne;
+        h_ntri[c] = nt;
+    }
+    if (T > INT32_MAX / 2) { set_error("too many triangles"); return AICA_ERR_CAPACITY; }
+    std::vector<float> h_tri32(9 * T), h_vtx32(h_vtx.size()), h_edg32(h_edg.size()), h_ctr32(3 * n_cells),
+        h_rad32(n_cells);
+    double max_local = 0;
+    for (int64_t c = 0; c < n_cells; ++c) {
+        for (int64_t i = 3 * (int64_t)h_tri_off[c]; i < 3 * (int64_t)h_tri_off[c + 1]; ++i)
+            for (int d = 0; d < 3; ++d) {
+                double x = h_tri[3 * i + d] - h_org[3 * c + d];
+                max_local = std::max(max_local, fabs(x));
+                h_tri32[3 * i + d] = (float)x;
+            }
+        for (int64_t i = h_vtx_off[c]; i < h_vtx_off[c + 1]; ++i)
+            for (int d = 0; d < 3; ++d) h_vtx32[3 * i + d] = (float)(h_vtx[3 * i + d] - h_org[3 * c + d]);
+        for (int64_t i = 2 * (int64_t)h_edg_off[c]; i < 2 * (int64_t)h_edg_off[c + 1]; ++i)
+            for (int d = 0; d < 3; ++d) h_edg32[3 * i + d] = (float)(h_edg[3 * i + d] - h_org[3 * c + d]);
+        for (int d = 0; d < 3; ++d) h_ctr32[3 * c + d] = (float)(h_ctr[3 * c + d] - h_org[3 * c + d]);
+        h_rad32[c] = (float)(h_rad[c] * (1 + 1e-6)) + 1e-6f;
+    }
+
+    // ---- point-location bucket grid over the mesh bounding box
+    double glo[3], ghi[3];
+    for (int d = 0; d < 3; ++d) {
+        glo[d] = INFINITY; ghi[d] = -INFINITY;
+        for (int64_t c = 0; c < n_cells; ++c) {
+            glo[d] = std::min(glo[d], h_lo[3 * c + d]);
+            ghi[d] = std::max(ghi[d], h_hi[3 * c + d]);
+        }
+    }
+    double vol = 1;
+    for (int d = 0; d < 3; ++d) vol *= std::max(ghi[d] - glo[d], 1e-300);
+    // bucket edge: half the geometric-mean cell bounding-box edge
+    double lg = 0;
+    for (int64_t c = 0; c < n_cells; ++c)
+        for (int d = 0; d < 3; ++d) lg += log(std::max(h_hi[3 * c + d] - h_lo[3 * c + d], 1e-12));
+    double h0 = 0.5 * exp(lg / (3.0 * (double)n_cells));
+    (void)vol;
+    int G[3];
+    double gh[3];
+    for (int d = 0; d < 3; ++d) {
+        G[d] = std::max(1, std::min(1024, (int)floor((ghi[d] - glo[d]) / h0)));
+        gh[d] = (ghi[d] - glo[d]) / G[d];
+    }
+    int64_t nb = (int64_t)G[0] * G[1] * G[2];
+    std::vector<int32_t> h_bkt_off(nb + 1, 0);
+    std::vector<int32_t> h_bkt_cells;
+    auto range = [&](int64_t c, int d, int &i0, int &i1) {
+        i0 = (int)floor((h_lo[3 * c + d] - glo[d]) / gh[d] - 1e-6);
+        i1 = (int)floor((h_hi[3 * c + d] - glo[d]) / gh[d] + 1e-6);
+        i0 = std::max(i0, 0);
+        i1 = std::min(i1, G[d] - 1);
+    };
+    for (int pass = 0; pass < 2; ++pass) {
+        std::vector<int32_t> fillb(pass ? nb : 0, 0);
+        if (pass) h_bkt_cells.resize(h_bkt_off[nb]);
+        for (int64_t c = 0; c < n_cells; ++c) {
+            int r0[3], r1[3];
+            for (int d = 0; d < 3; ++d) range(c, d, r0[d], r1[d]);
+            for (int x = r0[0]; x <= r1[0]; ++x)
+                for (int y = r0[1]; y <= r1[1]; ++y)
+                    for (int z = r0[2]; z <= r1[2]; ++z) {
+                        int64_t b = ((int64_t)x * G[1] + y) * G[2] + z;
+                        if (!pass) h_bkt_off[b + 1]++;
+                        else h_bkt_cells[h_bkt_off[b] + fillb[b]++] = (int32_t)c;
+                    }
+        }
+        if (!pass) {
+            for (int64_t b = 0; b < nb; ++b) h_bkt_off[b + 1] += h_bkt_off[b];
+            if (h_bkt_off[nb] < 0 || (int64_t)h_bkt_off[nb] > (int64_t)INT32_MAX / 2) {
+                set_error("bucket grid too large");
+                return AICA_ERR_CAPACITY;
+            }
+        }
+    }
+
+    aica_mesh *m = new (std::nothrow) aica_mesh();
+    if (!m) { set_error("host allocation failed"); return AICA_ERR_OOM; }
+    cudaGetDevice(&m->device);
+    m->n_cells = n_cells;
+    m->n_points = n_points;
+    m->box = *box;
+    m->max_tri = max_tri; m->max_vtx = max_vtx; m->max_edg = max_edg;
+    m->max_local = max_local;
+    for (int d = 0; d < 3; ++d) { m->G[d] = G[d]; m->glo[d] = glo[d]; m->gh[d] = gh[d]; }
+    cudaError_t e = cudaSuccess;
+    const char *what = "upload";
+    if (e == cudaSuccess) e = upload(m->tri_off, h_tri_off);
+    if (e == cudaSuccess) e = upload(m->tri, h_tri);
+    if (e == cudaSuccess) e = upload(m->ntri, h_ntri);
+    if (e == cudaSuccess) e = upload(m->vtx_off, h_vtx_off);
+    if (e == cudaSuccess) e = upload(m->vtx, h_vtx);
+    if (e == cudaSuccess) e = upload(m->edg_off, h_edg_off);
+    if (e == cudaSuccess) e = upload(m->edg, h_edg);
+    if (e == cudaSuccess) e = upload(m->ctr, h_ctr);
+    if (e == cudaSuccess) e = upload(m->rad, h_rad);
+    if (e == cudaSuccess) e = upload(m->lo, h_lo);
+    if (e == cudaSuccess) e = upload(m->hi, h_hi);
+    if (e == cudaSuccess) e = upload(m->org, h_org);
+    if (e == cudaSuccess) e = upload(m->orgk, h_orgk);
+    if (e == cudaSuccess) e = upload(m->tri32, h_tri32);
+    if (e == cudaSuccess) e = upload(m->vtx32, h_vtx32);
+    if (e == cudaSuccess) e = upload(m->edg32, h_edg32);
+    if (e == cudaSuccess) e = upload(m->ctr32, h_ctr32);
+    if (e == cudaSuccess) e = upload(m->rad32, h_rad32);
+    if (e == cudaSuccess) e = upload(m->bkt_off, h_bkt_off);
+    if (e == cudaSuccess) e = upload(m->bkt_cells, h_bkt_cells);
+    if (e == cudaSuccess) { e = m->flags.reserve(16); what = "flags"; }
+    if (e == cudaSuccess) e = cudaMemset(m->flags.p, 0, 16);
+    if (e == cudaSuccess) { e = m->acc.reserve(256); what = "acc"; }
+    if (e != cudaSuccess) {
+        aica_status s = e == cudaErrorMemoryAllocation ? AICA_ERR_OOM : AICA_ERR_CUDA;
+        cuda_fail(e, what);
+        aica_mesh_destroy(m);
+        return s;
+    }
+    m->h_ctr.swap(h_ctr);
+    m->h_rad.swap(h_rad);
+    *out = m;
+    return AICA_OK;
+}
+
+extern "C" void aica_mesh_destroy(aica_mesh *m) {
+    if (!m) return;
+    aica::DevBuf *bufs[] = {&m->tri_off, &m->tri, &m->vtx_off, &m->vtx, &m->edg_off, &m->edg, &m->ctr, &m->rad,
+                            &m->lo, &m->hi, &m->org, &m->ntri, &m->orgk, &m->tri32, &m->vtx32, &m->edg32, &m->ctr32, &m->rad32, &m->bkt_off, &m->bkt_cells, &m->dil_off,
+                            &m->dil_ids, &m->ref_src, &m->ref_n, &m->ref_off, &m->ref_ids, &m->work_off,
+                            &m->work, &m->work_d32, &m->work_split, &m->proc_order, &m->cell_of, &m->order,
+                            &m->cell_off, &m->fill, &m->xloc, &m->xs64, &m->scratch_i32, &m->facc,
+                            &m->vsorted, &m->acc, &m->flags, &m->params, &m->tmp};
+    for (auto *b : bufs) b->release();
+    delete m;
+}

@@ -1,0 +1,92 @@
+"""The hand-written adjoint against the autograd-of-oracle reference, finite
+differences and torch.autograd.gradcheck (FP64)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import torch_ref
+from paper_cs_0702131_gb300 import synth
+from paper_cs_0702131_gb300.aica import LJForce, Mesh
+from gpu_helpers import gpu_setup
+
+pytestmark = pytest.mark.gpu
+
+
+def _two_species_small(seed=0, n=4, hexes=3, rc=2.5):
+    rng = np.random.default_rng(seed)
+    a = synth.A_FCC_08
+    L = n * a
+    box = dict(L=np.array([L, L, L]), periodic=np.array([1, 1, 1], np.int32))
+    pos = synth.wrap(synth.jitter(synth.fcc_sites(n, n, n, a), 0.05, rng), box["L"], box["periodic"])
+    sp = np.zeros(len(pos), np.int32)
+    sp[rng.permutation(len(pos))[: len(pos) // 2]] = 1
+    mesh = synth.hex_mesh((hexes,) * 3, (0, 0, 0), box["L"], 0.15, rng)
+    return dict(pos=pos, species=sp, eps=np.array([1.0, 1.5]), sigma=np.array([1.0, 0.88]), rc=rc, box=box,
+                mesh=mesh, skin=1e-3)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 2e-4)])
+@pytest.mark.parametrize("which", ["t0", "mix"])
+def test_vjp_matches_autograd_of_oracle(which, prec, tol):
+    c = synth.make("t0", 2) if which == "t0" else _two_species_small(1)
+    m, *_ = gpu_setup(c)
+    v = np.random.default_rng(3).normal(size=c["pos"].shape)
+    gx, ge, gs, _ = torch_ref.vjp(c["pos"], c["species"], c["eps"], c["sigma"], c["rc"], c["box"], v)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    gp, ge_g, gs_g = m.forces_backward(c["eps"], c["sigma"], torch.tensor(v, dtype=dt, device="cuda"), prec)
+    assert np.abs(gp.double().cpu().numpy() - gx).max() <= tol * np.abs(gx).max()
+    np.testing.assert_allclose(ge_g.cpu().numpy(), ge, rtol=tol, atol=tol * np.abs(ge).max())
+    np.testing.assert_allclose(gs_g.cpu().numpy(), gs, rtol=tol, atol=tol * np.abs(gs).max())
+
+
+def test_force_matching_loss_c4():
+    """c4: loss = sum |F - F_t|^2, F_t from parameters scaled by 1.05; backward
+    against the autograd reference and FP64 central differences."""
+    c = synth.make("c4", 0)
+    m, pos, sp, _ = gpu_setup(c)
+    F, _, _ = m.forces(c["eps"], c["sigma"], "fp64")
+    Ft, _, _ = m.forces(c["eps"] * 1.05, c["sigma"] * 1.05, "fp64")
+    v = 2 * (F - Ft)                         # dL/dF
+    gp, ge_g, gs_g = m.forces_backward(c["eps"], c["sigma"], v, "fp64")
+    gx, ge, gs, _ = torch_ref.vjp(c["pos"], c["species"], c["eps"], c["sigma"], c["rc"], c["box"], v.cpu().numpy())
+    assert np.abs(gp.cpu().numpy() - gx).max() <= 1e-10 * np.abs(gx).max()
+    np.testing.assert_allclose(ge_g.cpu().numpy(), ge, rtol=1e-10)
+    np.testing.assert_allclose(gs_g.cpu().numpy(), gs, rtol=1e-10)
+
+    def loss(eps, sig, p=None):
+        if p is not None:
+            m.bin(p, sp, outputs=False)
+        Fx, _, _ = m.forces(eps, sig, "fp64")
+        return float(((Fx - Ft) ** 2).sum())
+
+    h = 1e-6
+    for s in range(2):
+        d = np.zeros(2)
+        d[s] = h
+        fd = (loss(c["eps"] + d, c["sigma"]) - loss(c["eps"] - d, c["sigma"])) / (2 * h)
+        assert abs(fd - ge_g[s].item()) <= 1e-5 * abs(ge_g[s].item()) + 1e-6
+        fd = (loss(c["eps"], c["sigma"] + d) - loss(c["eps"], c["sigma"] - d)) / (2 * h)
+        assert abs(fd - gs_g[s].item()) <= 1e-5 * abs(gs_g[s].item()) + 1e-6
+    rng = np.random.default_rng(2)
+    for k in rng.choice(len(c["pos"]), 16, replace=False):
+        ax = int(rng.integers(3))
+        p = pos.clone()
+        p[k, ax] += h
+        lp = loss(c["eps"], c["sigma"], p)
+        p[k, ax] -= 2 * h
+        lm = loss(c["eps"], c["sigma"], p)
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - gp[k, ax].item()) <= 1e-4 * max(1.0, abs(gp[k, ax].item()))
+    m.bin(pos, sp, outputs=False)
+
+
+def test_gradcheck_fp64():
+    c = _two_species_small(4, n=2, hexes=2, rc=1.6)
+    m = Mesh(c["mesh"], c["box"])
+    m.build_lists(c["rc"], 1e-3)
+    pos = torch.tensor(c["pos"], dtype=torch.float64, device="cuda", requires_grad=True)
+    sp = torch.tensor(c["species"], dtype=torch.int32, device="cuda")
+    eps = torch.tensor(c["eps"], dtype=torch.float64, requires_grad=True)
+    sig = torch.tensor(c["sigma"], dtype=torch.float64, requires_grad=True)
+    f = lambda p, e, s: LJForce.apply(p, e, s, m, sp, "fp64")
+    assert torch.autograd.gradcheck(f, (pos, eps, sig), eps=1e-6, atol=1e-6, rtol=1e-5)

@@ -1,0 +1,71 @@
+"""GPU binning against the oracle: cell ids, binned order and offsets bit-exact."""
+import itertools
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_cs_0702131_gb300 import synth
+from paper_cs_0702131_gb300.aica import AicaError, Mesh
+from gpu_helpers import gpu_setup, oracle_all
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("name", ["t0", "c1", "h0", "c4", "c2"])
+def test_binning_equals_oracle(name):
+    c = synth.make(name, 2)
+    m, pos, sp, (cell_of, order, cell_off) = gpu_setup(c)
+    o = oracle_all(c, lists=False)
+    np.testing.assert_array_equal(cell_of, o["cell"])
+    np.testing.assert_array_equal(order, o["order"])
+    np.testing.assert_array_equal(cell_off, o["cell_off"])
+
+
+def test_binning_after_displacement_large():
+    c = synth.make("c2", 4)
+    rng = np.random.default_rng(7)
+    c["pos"] = synth.random_displacement(c["pos"], 0.5, rng, c["box"]["L"], c["box"]["periodic"])
+    m, pos, sp, (cell_of, order, cell_off) = gpu_setup(c)
+    o = oracle_all(c, lists=False)
+    np.testing.assert_array_equal(cell_of, o["cell"])
+    np.testing.assert_array_equal(order, o["order"])
+
+
+@pytest.mark.parametrize("tets", [False, True])
+def test_ties_on_faces_edges_vertices(tets):
+    N, W = 4, 0.5
+    box = dict(L=np.array([N * W] * 3), periodic=np.array([1, 1, 1], np.int32))
+    mesh = synth.hex_mesh((N, N, N), (0, 0, 0), box["L"], 0.0, np.random.default_rng(0), tets=tets)
+    rng = np.random.default_rng(3)
+    p = rng.integers(0, 8 * N, size=(3000, 3)) * (W / 8)
+    p[:500, 1] = p[:500, 0]
+    p[500:1000, 2] = p[500:1000, 1]
+    p[1000:1500, 2] = p[1000:1500, 0]
+    p[1500:1600] = rng.integers(-8, 8 * N + 8, size=(100, 3)) * (W / 8)   # wrap through the box faces
+    cfg = dict(mesh=mesh, box=box, pos=p, species=np.zeros(len(p), np.int32), rc=0.4, skin=0.0)
+    m, pos, sp, (cell_of, order, cell_off) = gpu_setup(cfg)
+    o = oracle_all(cfg, lists=False)
+    np.testing.assert_array_equal(cell_of, o["cell"])
+    np.testing.assert_array_equal(order, o["order"])
+
+
+def test_outside_molecules_reported():
+    c = synth.nanochannel(0, nfcc=(12, 4, 12), hex_shape=(8, 4, 8), post_radius=2.0)
+    pos = c["pos"].copy()
+    pos[5, 1] = 100.0            # far above the open y boundary
+    m = Mesh(c["mesh"], c["box"])
+    m.build_lists(2.5, 1e-3)
+    P = torch.tensor(pos, device="cuda")
+    S = torch.zeros(len(pos), dtype=torch.int32, device="cuda")
+    with pytest.raises(AicaError) as e:
+        m.bin(P, S)
+    assert e.value.name == "AICA_ERR_OUTSIDE_MESH"
+    m.set_deferred(True)
+    cell_of, order, cell_off = m.bin(P, S)
+    assert cell_of[5].item() == -1 and cell_off[-1].item() == len(pos) - 1
+    with pytest.raises(AicaError):
+        m.check()
+    F, ev, cnt = m.forces([1.0], [1.0], "fp64")
+    assert torch.all(F[5] == 0)

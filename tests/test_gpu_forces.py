@@ -1,0 +1,87 @@
+"""GPU forces, energy, virial and pair counts against the oracle (§2.3).
+
+Tolerances: FP64 path |dF| <= 1e-12 sum_l |f_kl| per component, FP32 path
+1e-5 of the same scale; energy and virial against sum |u| and sum |r.f|
+(1e-12 FP64, 1e-6 FP32).  Pair counts are integers and must be equal: the
+FP32 path re-decides pairs near the cut-off in FP64.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_cs_0702131_gb300 import synth
+from gpu_helpers import assert_forces, gpu_setup, oracle_all
+
+pytestmark = pytest.mark.gpu
+TOL = {"fp64": (1e-12, 1e-12), "fp32": (1e-5, 1e-6)}
+
+
+def _check_all(c, prec, with_counts=True, shift=False):
+    m, pos, sp, _ = gpu_setup(c)
+    F, ev, cnt = m.forces(c["eps"], c["sigma"], prec, shift=shift)
+    ref = oracle.lj(c["pos"], c["species"], c["eps"], c["sigma"], c["rc"], c["box"], shift=shift)
+    tf, te = TOL[prec]
+    assert_forces(F.double().cpu().numpy(), ref, tf)
+    ev = ev.cpu().numpy()
+    assert abs(ev[0] - ref["U"]) <= te * ref["Uabs"]
+    assert np.abs(ev[1:] - ref["W"]).max() <= te * ref["Wabs"]
+    cnt = cnt.cpu().numpy()
+    assert cnt[3] + cnt[4] + cnt[5] // 2 == ref["pairs"]
+    if with_counts:
+        o = oracle_all(c)
+        np.testing.assert_array_equal(cnt, o["loop"]["counts"])
+    return m
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", ["t0", "c1", "h0"])
+def test_forces_small_full(name, prec):
+    _check_all(synth.make(name, 1), prec)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_forces_two_species_c4(prec):
+    _check_all(synth.make("c4", 0), prec, with_counts=False)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_forces_nanochannel_small(prec):
+    c = synth.nanochannel(1, nfcc=(12, 4, 12), hex_shape=(8, 4, 8), post_radius=2.0)
+    c["skin"] = 1e-3
+    _check_all(c, prec)
+
+
+def test_energy_shift():
+    _check_all(synth.make("c1", 3), "fp32", with_counts=False, shift=True)
+    _check_all(synth.make("c1", 3), "fp64", with_counts=False, shift=True)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_forces_c2_full(prec):
+    _check_all(synth.make("c2", 0), prec, with_counts=False)
+
+
+def test_forces_c5_sampled():
+    c = synth.make("c5", 0)
+    m, pos, sp, _ = gpu_setup(c)
+    rng = np.random.default_rng(0)
+    idx = np.sort(rng.choice(len(c["pos"]), 256, replace=False))
+    ref = oracle.lj(c["pos"], c["species"], c["eps"], c["sigma"], c["rc"], c["box"], idx=idx)
+    for prec in ("fp32", "fp64"):
+        F, ev, cnt = m.forces(c["eps"], c["sigma"], prec)
+        assert_forces(F.double().cpu().numpy(), ref, TOL[prec][0], idx=idx)
+        Fs = F.double().sum(0).abs().max().item()
+        assert Fs <= 1e-4 * len(c["pos"])           # Newton's third law, summed in FP32 / FP64
+        # FCC near rho 0.8, rc 3: about 43 pairs per molecule
+        n_in = cnt[3].item() + cnt[4].item() + cnt[5].item() // 2
+        assert 42.0 < n_in / len(c["pos"]) < 44.0
+
+
+def test_repeat_calls_stable():
+    c = synth.make("t0", 4)
+    m, *_ = gpu_setup(c)
+    a = m.forces(c["eps"], c["sigma"], "fp64")
+    b = m.forces(c["eps"], c["sigma"], "fp64")
+    np.testing.assert_allclose(a[0].cpu().numpy(), b[0].cpu().numpy(), rtol=0, atol=1e-12)
+    np.testing.assert_array_equal(a[2].cpu().numpy(), b[2].cpu().numpy())
