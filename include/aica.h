@@ -176,6 +176,14 @@ aica_status aica_forces_backward(aica_mesh *mesh, const aica_lj *lj, aica_precis
 aica_status aica_set_deferred_checks(aica_mesh *mesh, int deferred);
 aica_status aica_check_status(aica_mesh *mesh, void *stream);
 
+/* Measurement hook.  With enable != 0 every aica_forces call records a pair
+ * of CUDA events on its stream around its pair kernel (no synchronization).
+ * aica_take_kernel_times synchronizes on the recorded events, writes up to
+ * cap durations in milliseconds (oldest first) to the host array ms, sets *n
+ * to the number written and forgets them.  Not for use under stream capture. */
+aica_status aica_set_kernel_timing(aica_mesh *mesh, int enable);
+aica_status aica_take_kernel_times(aica_mesh *mesh, float *ms, int64_t cap, int64_t *n);
+
 /* Number of kernels the last call on this mesh launched (for accounting). */
 int64_t aica_last_launch_count(const aica_mesh *mesh);
 

@@ -87,8 +87,9 @@ def lj(pos, species, eps, sigma, rc, box, shift=False, idx=None):
     """All-pairs minimum-image LJ forces (the plain definition).
 
     Returns dict(F [m,3], Fabs [m] = sum_l |f_kl|, U, W [6] (xx,yy,zz,xy,xz,yz),
-    Uabs = sum |u|, Wabs = sum |r . f| over pairs, pairs = number of unordered
-    pairs within rc (only when idx is None)).
+    Uabs = sum |u|, Wabs = sum |r . f| over pairs, row_pairs = number of
+    (k, l) within rc over the computed rows, pairs = number of unordered pairs
+    within rc (only when idx is None)).
     Requires rc < L/2 on periodic axes, where the minimum image is unique.
     """
     pos = _c(pos, np.float64)
@@ -103,7 +104,7 @@ def lj(pos, species, eps, sigma, rc, box, shift=False, idx=None):
     lib().oracle_lj(n, pos, _c(species, np.int32), len(eps), _c(eps, np.float64), _c(sigma, np.float64),
                     float(rc), _c(box["L"], np.float64), _c(box["periodic"], np.int32), int(bool(shift)),
                     None if idx_arr is None else idx_arr.ctypes.data, m, F, Fabs, ev, ab, cnt)
-    out = dict(F=F, Fabs=Fabs, U=ev[0], W=ev[1:].copy(), Uabs=ab[0], Wabs=ab[1])
+    out = dict(F=F, Fabs=Fabs, U=ev[0], W=ev[1:].copy(), Uabs=ab[0], Wabs=ab[1], row_pairs=int(cnt[0]))
     if idx is None:
         out["pairs"] = int(cnt[0]) // 2
     return out

@@ -68,6 +68,9 @@ SIGNATURES = {
     "aica_set_deferred_checks": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "aica_check_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "aica_last_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
+    "aica_set_kernel_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "aica_take_kernel_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                              ctypes.POINTER(ctypes.c_int64)]),
     "aica_last_error": (ctypes.c_char_p, []),
     "aica_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -200,6 +203,17 @@ def aica_last_launch_count(h):
     return int(lib().aica_last_launch_count(h))
 
 
+def aica_set_kernel_timing(h, enable):
+    _check(lib().aica_set_kernel_timing(h, int(bool(enable))))
+
+
+def aica_take_kernel_times(h, cap=1 << 16):
+    ms = np.zeros(cap, np.float32)
+    n = ctypes.c_int64()
+    _check(lib().aica_take_kernel_times(h, ms.ctypes.data, cap, ctypes.byref(n)))
+    return ms[: n.value].copy()
+
+
 # ---------------------------------------------------------------- convenience
 def _prec(p):
     if p in ("fp32", AICA_FP32, torch.float32):
@@ -279,6 +293,13 @@ class Mesh:
 
     def set_deferred(self, deferred=True):
         aica_set_deferred_checks(self.h, deferred)
+
+    def set_kernel_timing(self, enable=True):
+        aica_set_kernel_timing(self.h, enable)
+
+    def take_kernel_times(self):
+        """Durations (ms) of the pair kernels recorded since the last take."""
+        return aica_take_kernel_times(self.h)
 
     def check(self):
         aica_check_status(self.h)

@@ -9,6 +9,8 @@
 
 #include "../../include/aica.h"
 
+struct aica_mesh;
+
 namespace aica {
 
 // Per-cell limits of the list builder and binning kernels.
@@ -24,6 +26,9 @@ enum : unsigned {
     kFlagSpecies = 2u,   // a species index is out of range
     kFlagCapacity = 4u,  // a per-cell capacity of a kernel was exceeded
 };
+
+cudaError_t timing_begin(aica_mesh *m, cudaStream_t st, cudaEvent_t *stop);
+cudaError_t timing_end(cudaEvent_t stop, cudaStream_t st);
 
 // Thread-local last error message.
 void set_error(const char *fmt, ...);
@@ -116,4 +121,7 @@ struct aica_mesh {
 
     bool deferred = false;
     int64_t launches = 0;
+    bool timing = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> tev;   // recorded, not yet taken
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> tfree;  // reusable
 };

@@ -58,3 +58,46 @@ extern "C" aica_status aica_check_status(aica_mesh *m, void *stream) {
 }
 
 extern "C" int64_t aica_last_launch_count(const aica_mesh *m) { return m ? m->launches : 0; }
+
+extern "C" aica_status aica_set_kernel_timing(aica_mesh *m, int enable) {
+    if (!m) { aica::set_error("aica_set_kernel_timing: mesh is NULL"); return AICA_ERR_INVALID_ARG; }
+    m->timing = enable != 0;
+    return AICA_OK;
+}
+
+extern "C" aica_status aica_take_kernel_times(aica_mesh *m, float *ms, int64_t cap, int64_t *n) {
+    if (!m || !n || (cap > 0 && !ms)) { aica::set_error("aica_take_kernel_times: NULL argument"); return AICA_ERR_INVALID_ARG; }
+    int64_t k = 0;
+    for (auto &p : m->tev) {
+        AICA_CUDA(cudaEventSynchronize(p.second));
+        float t = 0;
+        AICA_CUDA(cudaEventElapsedTime(&t, p.first, p.second));
+        if (k < cap) ms[k] = t;
+        ++k;
+        m->tfree.push_back(p);
+    }
+    m->tev.clear();
+    *n = k < cap ? k : cap;
+    return AICA_OK;
+}
+
+namespace aica {
+// start/stop events around a measured kernel (see aica_set_kernel_timing)
+cudaError_t timing_begin(aica_mesh *m, cudaStream_t st, cudaEvent_t *stop) {
+    *stop = nullptr;
+    if (!m->timing) return cudaSuccess;
+    std::pair<cudaEvent_t, cudaEvent_t> p;
+    if (!m->tfree.empty()) {
+        p = m->tfree.back();
+        m->tfree.pop_back();
+    } else {
+        cudaError_t e = cudaEventCreate(&p.first);
+        if (e == cudaSuccess) e = cudaEventCreate(&p.second);
+        if (e != cudaSuccess) return e;
+    }
+    m->tev.push_back(p);
+    *stop = p.second;
+    return cudaEventRecord(p.first, st);
+}
+cudaError_t timing_end(cudaEvent_t stop, cudaStream_t st) { return stop ? cudaEventRecord(stop, st) : cudaSuccess; }
+}  // namespace aica

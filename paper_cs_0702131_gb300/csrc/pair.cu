@@ -778,6 +778,8 @@ extern "C" aica_status aica_forces(aica_mesh *m, const aica_lj *lj, aica_precisi
     AICA_CUDA(cudaMemsetAsync(m->acc.p, 0, 16 * sizeof(double), st));
     const bool multi = a.S > 1, shift = lj->shift != 0;
     const int grid = pair_grid(a.C);
+    cudaEvent_t tstop;
+    AICA_CUDA(timing_begin(m, st, &tstop));
     if (!f64) {
         if (multi) {
             if (shift) pair_fwd32<true, true><<<grid, kPairThreads, 0, st>>>(a);
@@ -795,11 +797,12 @@ extern "C" aica_status aica_forces(aica_mesh *m, const aica_lj *lj, aica_precisi
             else pair_fwd64<false, false><<<grid, kPairThreads, 0, st>>>(a);
         }
     }
+    AICA_CUDA(timing_end(tstop, st));
     if (n > 0) {
         if (f64) unsort_forces<double><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m->inv.as<int>(), n, m->facc.p, (double *)force_out, 1);
         else unsort_forces<float><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m->inv.as<int>(), n, m->facc.p, (float *)force_out, 0);
     }
-    m->launches = 2;
+    m->launches = n > 0 ? 2 : 1;
     if (ev_out || counts_out) {
         finish_sums<<<1, 32, 0, st>>>(m->acc.as<double>(), ev_out, (long long *)counts_out);
         m->launches++;
