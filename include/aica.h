@@ -140,8 +140,11 @@ aica_status aica_bin_molecules(aica_mesh *mesh, const double *pos, const int32_t
                                int32_t *cell_of, int32_t *order, int32_t *cell_off, void *stream);
 
 /* Forces, potential energy and virial over the AICA pair set (§2.3):
- * same-cell pairs, DIL pairs with Newton's third law, and real-referred pairs
- * acting on the real molecule only, for the last binned molecules.
+ * same-cell pairs, DIL pairs and periodic (real-referred) pairs, for the last
+ * binned molecules.  §2.3 evaluates a real-referred pair once from each side,
+ * acting on the real molecule only, because its source may live on another
+ * processor; on one device each periodic image pair is evaluated once with
+ * Newton's third law instead, which gives the same forces.
  *   prec   AICA_FP32: FP32 pair arithmetic on cell-local coordinates, FP64
  *          energy/virial sums, and r^2 < rc^2 decided in FP64 whenever the
  *          FP32 value lies within 1e-5 rc^2 of the cut-off;
@@ -151,8 +154,9 @@ aica_status aica_bin_molecules(aica_mesh *mesh, const double *pos, const int32_t
  *   ev_out     device double [7], optional: U, Wxx, Wyy, Wzz, Wxy, Wxz, Wyz
  *              with W_ab = sum over pairs of r_a f_b, each physical pair once
  *   counts_out device int64 [6], optional: evaluated pairs {same-cell, DIL,
- *              real-referred}, then pairs within rc in the same order; each
- *              real-referred pair is evaluated once from each side.
+ *              periodic image} (every molecule pair of every scheduled cell
+ *              pair, each physical pair once), then the pairs within rc in
+ *              the same order; their sum is the number of pairs within rc.
  * AICA_ERR_NOT_BUILT without lists and binning. */
 aica_status aica_forces(aica_mesh *mesh, const aica_lj *lj, aica_precision prec, void *force_out,
                         double *ev_out, int64_t *counts_out, void *stream);
@@ -163,9 +167,9 @@ aica_status aica_forces(aica_mesh *mesh, const aica_lj *lj, aica_precision prec,
  *   grad_eps   device double [S], optional: dL/d eps_s
  *   grad_sigma device double [S], optional: dL/d sigma_s
  * Pair terms are recomputed over the same pair set (nothing is stored by the
- * forward call).  A real-referred pair moves the real molecule's force, so
- * its position gradient also reaches the source molecule of the referred
- * copy.  The cut-off is not differentiated. */
+ * forward call).  A periodic image pair couples a molecule to the source
+ * molecule of the referred copy, so both receive position gradient.  The
+ * cut-off is not differentiated. */
 aica_status aica_forces_backward(aica_mesh *mesh, const aica_lj *lj, aica_precision prec,
                                  const void *grad_force, void *grad_pos, double *grad_eps,
                                  double *grad_sigma, void *stream);
@@ -183,6 +187,13 @@ aica_status aica_check_status(aica_mesh *mesh, void *stream);
  * to the number written and forgets them.  Not for use under stream capture. */
 aica_status aica_set_kernel_timing(aica_mesh *mesh, int enable);
 aica_status aica_take_kernel_times(aica_mesh *mesh, float *ms, int64_t cap, int64_t *n);
+
+/* Work the last aica_forces call actually performed (host int64 out[2]):
+ * out[0] pair distance tests, out[1] bounding-sphere tests of partner cells
+ * and molecules.  The kernels skip cells and molecules that cannot be within
+ * rc, so out[0] is below the evaluated counts of aica_forces.  Synchronizes
+ * `stream`. */
+aica_status aica_get_work_counters(aica_mesh *mesh, int64_t *out, void *stream);
 
 /* Number of kernels the last call on this mesh launched (for accounting). */
 int64_t aica_last_launch_count(const aica_mesh *mesh);

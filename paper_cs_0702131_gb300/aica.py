@@ -68,6 +68,7 @@ SIGNATURES = {
     "aica_set_deferred_checks": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "aica_check_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "aica_last_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
+    "aica_get_work_counters": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "aica_set_kernel_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "aica_take_kernel_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                               ctypes.POINTER(ctypes.c_int64)]),
@@ -203,6 +204,12 @@ def aica_last_launch_count(h):
     return int(lib().aica_last_launch_count(h))
 
 
+def aica_get_work_counters(h):
+    out = np.zeros(2, np.int64)
+    _check(lib().aica_get_work_counters(h, out.ctypes.data, _stream()))
+    return out
+
+
 def aica_set_kernel_timing(h, enable):
     _check(lib().aica_set_kernel_timing(h, int(bool(enable))))
 
@@ -296,6 +303,10 @@ class Mesh:
 
     def set_kernel_timing(self, enable=True):
         aica_set_kernel_timing(self.h, enable)
+
+    def last_stats(self):
+        """[pair distance tests, sphere tests] of the last forces call."""
+        return aica_get_work_counters(self.h)
 
     def take_kernel_times(self):
         """Durations (ms) of the pair kernels recorded since the last take."""

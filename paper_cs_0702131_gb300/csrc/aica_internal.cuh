@@ -113,6 +113,10 @@ struct aica_mesh {
     int64_t n_mol = 0, cap_mol = 0;
     aica::DevBuf cell_of, order, cell_off, fill, xloc, xs64, scratch_i32, inv;
     int max_species = -1;                    // from the last checked binning, -1 if unknown
+    aica::DevBuf sph;                        // [C] float4 molecule bounding sphere per cell (local frame)
+    aica::DevBuf part;                       // per-warp partial sums of the pair kernels
+    int64_t n_mol_prev = -1;                 // molecule count of the previous binning
+    bool hint_valid = false;                 // cell_of holds that binning (a search hint)
     aica::DevBuf facc, vsorted;              // force / gradient accumulators in binned order
     aica::DevBuf acc;                        // double[16] sums + uint64 counters
     aica::DevBuf flags;                      // unsigned[4] device error flags

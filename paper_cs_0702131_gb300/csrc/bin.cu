@@ -28,6 +28,8 @@ namespace {
 
 struct BinArgs {
     int64_t n;
+    const int *hint;       // previous cell of each molecule (or NULL)
+    float glo_f[3], inv_gh_f[3], gh_f[3];
     const double *pos;
     const int *species;
     double L[3];
@@ -86,6 +88,12 @@ __device__ bool cell_contains(const BinArgs &a, int c, float3 q, const double *p
     return false;
 }
 
+// p relative to the dyadic origin c_k * 2^-10 of cell c, in FP32 (one rounding)
+__device__ __forceinline__ float3 local_to(const BinArgs &a, const double *p, int c) {
+    return make_float3((float)(p[0] - a.orgk[3 * c] * (1.0 / 1024.0)), (float)(p[1] - a.orgk[3 * c + 1] * (1.0 / 1024.0)),
+                       (float)(p[2] - a.orgk[3 * c + 2] * (1.0 / 1024.0)));
+}
+
 __global__ void __launch_bounds__(256) bin_locate(BinArgs a) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= a.n) return;
@@ -96,20 +104,25 @@ __global__ void __launch_bounds__(256) bin_locate(BinArgs a) {
         p[d] = a.pos[3 * k + d];
         if (a.per[d]) p[d] = wrap_coord(p[d], a.L[d]);
         if (!(p[d] >= a.glo[d] && p[d] <= a.ghi[d])) ok = false;
-        ib[d] = min(max((int)floor((p[d] - a.glo[d]) / a.gh[d]), 0), a.G[d] - 1);
+        // bucket index in FP32; the buckets are registered with a tolerance
+        ib[d] = min(max((int)floorf((float)(p[d] - a.glo[d]) * a.inv_gh_f[d]), 0), a.G[d] - 1);
     }
     int found = -1;
-    if (ok) {
+    // the molecule's previous cell first (a search hint: the test is exact either way)
+    int h = a.hint ? a.hint[k] : -1;
+    if (ok && h >= 0 && cell_contains(a, h, local_to(a, p, h), p)) found = h;
+    if (ok && found < 0) {
         int b = (ib[0] * a.G[1] + ib[1]) * a.G[2] + ib[2];
         // dyadic bucket origin: p relative to it is one rounding from exact
         int kb[3];
         float3 pb;
-        for (int d = 0; d < 3; ++d) kb[d] = (int)rint((a.glo[d] + (ib[d] + 0.5) * a.gh[d]) * 1024.0);
+        for (int d = 0; d < 3; ++d) kb[d] = (int)rintf((a.glo_f[d] + ((float)ib[d] + 0.5f) * a.gh_f[d]) * 1024.0f);
         pb.x = (float)(p[0] - kb[0] * (1.0 / 1024.0));
         pb.y = (float)(p[1] - kb[1] * (1.0 / 1024.0));
         pb.z = (float)(p[2] - kb[2] * (1.0 / 1024.0));
         for (int i = a.bkt_off[b]; i < a.bkt_off[b + 1]; ++i) {
             int c = a.bkt_cells[i];
+            if (c == h) continue;
             float3 q = make_float3(pb.x - (float)(a.orgk[3 * c] - kb[0]) * (1.0f / 1024.0f),
                                    pb.y - (float)(a.orgk[3 * c + 1] - kb[1]) * (1.0f / 1024.0f),
                                    pb.z - (float)(a.orgk[3 * c + 2] - kb[2]) * (1.0f / 1024.0f));
@@ -183,6 +196,29 @@ __global__ void __launch_bounds__(256) bin_gather(BinArgs a, const int *order, c
     if ((threadIdx.x & 31) == 0) atomicMax((int *)a.flags + 1, mx);
 }
 
+// Per-cell bounding sphere of its molecules in the cell's local frame:
+// centre = mean, radius = max distance, rounded up.  Used by the pair kernels
+// to skip cell pairs and partner molecules that cannot be within rc.
+__global__ void __launch_bounds__(256) bin_spheres(const int *cell_off, int C, const float4 *xloc, float4 *sph) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    int s = cell_off[c], e = cell_off[c + 1];
+    float cx = 0.f, cy = 0.f, cz = 0.f;
+    for (int i = s; i < e; ++i) {
+        float4 x = xloc[i];
+        cx += x.x; cy += x.y; cz += x.z;
+    }
+    float inv = e > s ? 1.f / (float)(e - s) : 0.f;
+    cx *= inv; cy *= inv; cz *= inv;
+    float r2 = 0.f;
+    for (int i = s; i < e; ++i) {
+        float4 x = xloc[i];
+        float dx = x.x - cx, dy = x.y - cy, dz = x.z - cz;
+        r2 = fmaxf(r2, dx * dx + dy * dy + dz * dz);
+    }
+    sph[c] = make_float4(cx, cy, cz, sqrtf(r2) * (1.f + 1e-5f) + 1e-5f);
+}
+
 }  // namespace
 }  // namespace aica
 
@@ -200,6 +236,7 @@ extern "C" aica_status aica_bin_molecules(aica_mesh *m, const double *pos, const
     m->launches = 0;
     m->binned = false;
     if (n > m->cap_mol) {
+        m->hint_valid = false;
         int64_t cap = std::max<int64_t>(n, 1024);
         AICA_CUDA(m->cell_of.reserve(sizeof(int) * cap));
         AICA_CUDA(m->order.reserve(sizeof(int) * cap));
@@ -212,6 +249,7 @@ extern "C" aica_status aica_bin_molecules(aica_mesh *m, const double *pos, const
     }
     AICA_CUDA(m->cell_off.reserve(sizeof(int) * (C + 1)));
     AICA_CUDA(m->fill.reserve(sizeof(int) * (C + 1)));
+    AICA_CUDA(m->sph.reserve(sizeof(float4) * C));
     AICA_CUDA(m->scratch_i32.reserve(sizeof(int) * (scan_work_items(C) + 8)));
     m->n_mol = n;
     BinArgs a{};
@@ -236,6 +274,13 @@ extern "C" aica_status aica_bin_molecules(aica_mesh *m, const double *pos, const
     a.tri = m->tri.as<double>();
     a.ctr = m->ctr.as<double>();
     a.max_local = (float)(m->max_local * (1 + 1e-6));
+    for (int d = 0; d < 3; ++d) {
+        a.glo_f[d] = (float)m->glo[d];
+        a.gh_f[d] = (float)m->gh[d];
+        a.inv_gh_f[d] = (float)(1.0 / m->gh[d]);
+    }
+    // the previous binning of the same molecules is a search hint (exact result regardless)
+    a.hint = (m->hint_valid && m->n_mol_prev == n) ? m->cell_of.as<int>() : nullptr;
     a.cell_of = m->cell_of.as<int>();
     a.flags = m->flags.as<unsigned>();
     int *cnt = m->fill.as<int>();
@@ -258,6 +303,10 @@ extern "C" aica_status aica_bin_molecules(aica_mesh *m, const double *pos, const
                                        m->inv.as<int>());
         m->launches += 3;
     }
+    bin_spheres<<<(C + 255) / 256, 256, 0, st>>>(off, C, m->xloc.as<float4>(), m->sph.as<float4>());
+    m->launches += 1;
+    m->n_mol_prev = n;
+    m->hint_valid = true;
     AICA_CUDA(cudaGetLastError());
     if (cell_of && n) AICA_CUDA(cudaMemcpyAsync(cell_of, a.cell_of, sizeof(int) * n, cudaMemcpyDeviceToDevice, st));
     if (order && n) AICA_CUDA(cudaMemcpyAsync(order, m->order.p, sizeof(int) * n, cudaMemcpyDeviceToDevice, st));

@@ -57,6 +57,18 @@ extern "C" aica_status aica_check_status(aica_mesh *m, void *stream) {
     return AICA_OK;
 }
 
+extern "C" aica_status aica_get_work_counters(aica_mesh *m, int64_t *out, void *stream) {
+    if (!m || !out) { aica::set_error("aica_get_work_counters: NULL argument"); return AICA_ERR_INVALID_ARG; }
+    if (!m->acc.p) { out[0] = out[1] = 0; return AICA_OK; }
+    unsigned long long v[2];
+    cudaStream_t st = (cudaStream_t)stream;
+    AICA_CUDA(cudaMemcpyAsync(v, (const unsigned long long *)m->acc.p + 14, sizeof(v), cudaMemcpyDeviceToHost, st));
+    AICA_CUDA(cudaStreamSynchronize(st));
+    out[0] = (int64_t)v[0];
+    out[1] = (int64_t)v[1];
+    return AICA_OK;
+}
+
 extern "C" int64_t aica_last_launch_count(const aica_mesh *m) { return m ? m->launches : 0; }
 
 extern "C" aica_status aica_set_kernel_timing(aica_mesh *m, int enable) {

@@ -17,7 +17,8 @@
 //                   pass 0 counts, pass 1 writes keys (image, B)
 //   lst_sort        per-segment bitonic sort of the keys
 //   lst_classify    per-cell counts of DIL entries, referred cells, entries
-//   lst_fill        CSR outputs and the pair schedule
+//   lst_fill        CSR outputs and the pair schedule (each cell's DIL, then
+//                   the periodic image pairs it owns: every image pair once)
 #include <math.h>
 
 #include <algorithm>
@@ -271,11 +272,19 @@ __device__ __forceinline__ void key_fields(unsigned long long k, int &B, int &np
     npz = (int)(nk & 0xff) - 128;
 }
 
+// The pair schedule evaluates every periodic image pair once, with Newton's
+// third law: of the mirror entries (A sees B at +n) and (B sees A at -n) it
+// keeps the one with B > A, or B == A and n lexicographically positive.
+__device__ __forceinline__ bool canonical_image(int A, int B, int nx, int ny, int nz) {
+    if (B != A) return B > A;
+    return nx > 0 || (nx == 0 && (ny > 0 || (ny == 0 && nz > 0)));
+}
+
 __global__ void lst_classify(const long long *seg_off, const unsigned long long *keys, int C, int *c_dil, int *c_re,
-                             int *c_rc) {
+                             int *c_rc, int *c_rw) {
     int A = blockIdx.x * blockDim.x + threadIdx.x;
     if (A >= C) return;
-    int nd = 0, nr = 0, ng = 0;
+    int nd = 0, nr = 0, ng = 0, nw = 0;
     int px = 1000, py = 0, pz = 0;
     for (long long i = seg_off[A]; i < seg_off[A + 1]; ++i) {
         int B, x, y, z;
@@ -284,6 +293,7 @@ __global__ void lst_classify(const long long *seg_off, const unsigned long long 
             nd += B > A;
         } else {
             nr++;
+            nw += canonical_image(A, B, -x, -y, -z);
             if (x != px || y != py || z != pz) ng++;
             px = x; py = y; pz = z;
         }
@@ -291,13 +301,14 @@ __global__ void lst_classify(const long long *seg_off, const unsigned long long 
     c_dil[A] = nd;
     c_re[A] = nr;
     c_rc[A] = ng;
+    c_rw[A] = nw;
 }
 
 struct FillArgs {
     int C;
     const long long *seg_off;
     const unsigned long long *keys;
-    const int *o_dil, *o_re, *o_rc;
+    const int *o_dil, *o_re, *o_rc, *o_rw;
     const int *orgk;
     double L[3];
     int *dil_ids, *ref_src, *ref_n, *ref_off, *ref_ids;
@@ -310,16 +321,16 @@ __global__ void lst_fill(FillArgs f) {
     int A = blockIdx.x * blockDim.x + threadIdx.x;
     if (A > f.C) return;
     if (A == f.C) {
-        f.work_off[f.C] = f.o_dil[f.C] + f.o_re[f.C];
+        f.work_off[f.C] = f.o_dil[f.C] + f.o_rw[f.C];
         f.ref_off[f.o_rc[f.C]] = f.o_re[f.C];
         return;
     }
     int wd = f.o_dil[A], wr = f.o_re[A], g = f.o_rc[A];
     int nd = f.o_dil[A + 1] - wd;
-    int w0 = wd + wr;
+    int w0 = wd + f.o_rw[A];
     f.work_off[A] = w0;
     f.work_split[A] = w0 + nd;
-    int id = 0, ir = 0;
+    int id = 0, ir = 0, iw = 0;
     int px = 1000, py = 0, pz = 0;
     for (long long i = f.seg_off[A]; i < f.seg_off[A + 1]; ++i) {
         int B, x, y, z;
@@ -341,8 +352,10 @@ __global__ void lst_fill(FillArgs f) {
                 px = x; py = y; pz = z;
             }
             f.ref_ids[wr + ir] = B;
-            slot = w0 + nd + ir;
             ir++;
+            if (!canonical_image(A, B, -x, -y, -z)) continue;
+            slot = w0 + nd + iw;
+            iw++;
         }
         // partner B seen from A: its molecules shifted by n = -n'
         int nx = -x, ny = -y, nz = -z;
@@ -429,7 +442,7 @@ extern "C" aica_status aica_build_interaction_list(aica_mesh *m, double rc, doub
     CK(d_bcell.reserve(sizeof(int) * C));
     CK(cudaMemcpyAsync(d_boff.p, boff.data(), sizeof(int) * (nb + 1), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(d_bcell.p, bcell.data(), sizeof(int) * C, cudaMemcpyHostToDevice, st));
-    CK(d_cnt.reserve(sizeof(int) * 3 * (C + 1)));
+    CK(d_cnt.reserve(sizeof(int) * 4 * (C + 1)));
     CK(d_seg.reserve(sizeof(long long) * (C + 1)));
     CK(d_scan.reserve(sizeof(long long) * (scan_work_items(C) + 8)));
     CK(d_ties.reserve(sizeof(unsigned long long)));
@@ -469,21 +482,23 @@ extern "C" aica_status aica_build_interaction_list(aica_mesh *m, double rc, doub
     a.keys = d_keys.as<unsigned long long>();
     lst_query<1><<<qblocks, 32 * kQWarps, 0, st>>>(a);
     lst_sort<<<(unsigned)std::min<int64_t>(C, 152 * 32), 256, 0, st>>>(a.seg_off, a.keys, C, m->flags.as<unsigned>());
-    int *c_dil = d_cnt.as<int>(), *c_re = c_dil + (C + 1), *c_rc = c_re + (C + 1);
-    lst_classify<<<(C + 255) / 256, 256, 0, st>>>(a.seg_off, a.keys, C, c_dil, c_re, c_rc);
+    int *c_dil = d_cnt.as<int>(), *c_re = c_dil + (C + 1), *c_rc = c_re + (C + 1), *c_rw = c_rc + (C + 1);
+    lst_classify<<<(C + 255) / 256, 256, 0, st>>>(a.seg_off, a.keys, C, c_dil, c_re, c_rc, c_rw);
     m->launches += 3;
     CK(m->dil_off.reserve(sizeof(int) * (C + 1)));
-    CK(m->tmp.reserve(sizeof(int) * 2 * (C + 1) + sizeof(int) * (scan_work_items(C) + 8)));
-    int *o_re = m->tmp.as<int>(), *o_rc = o_re + (C + 1), *sw = o_rc + (C + 1);
+    CK(m->tmp.reserve(sizeof(int) * 3 * (C + 1) + sizeof(int) * (scan_work_items(C) + 8)));
+    int *o_re = m->tmp.as<int>(), *o_rc = o_re + (C + 1), *o_rw = o_rc + (C + 1), *sw = o_rw + (C + 1);
     m->launches += exclusive_scan<int, int>(c_dil, C, m->dil_off.as<int>(), sw, st);
     m->launches += exclusive_scan<int, int>(c_re, C, o_re, sw, st);
     m->launches += exclusive_scan<int, int>(c_rc, C, o_rc, sw, st);
-    int tot[3];
+    m->launches += exclusive_scan<int, int>(c_rw, C, o_rw, sw, st);
+    int tot[4];
     unsigned flags = 0;
     unsigned long long ties = 0;
     CK(cudaMemcpyAsync(&tot[0], m->dil_off.as<int>() + C, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(&tot[1], o_re + C, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(&tot[2], o_rc + C, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&tot[3], o_rw + C, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(&flags, m->flags.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(&ties, d_ties.p, sizeof(ties), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -492,7 +507,7 @@ extern "C" aica_status aica_build_interaction_list(aica_mesh *m, double rc, doub
         set_error("aica_build_interaction_list: a cell has more than %d neighbour cells", kSortMax);
         return AICA_ERR_CAPACITY;
     }
-    int64_t n_work = (int64_t)tot[0] + tot[1];
+    int64_t n_work = (int64_t)tot[0] + tot[3];
     CK(m->dil_ids.reserve(sizeof(int) * std::max(tot[0], 1)));
     CK(m->ref_src.reserve(sizeof(int) * std::max(tot[2], 1)));
     CK(m->ref_n.reserve(sizeof(int) * 3 * std::max(tot[2], 1)));
@@ -509,6 +524,7 @@ extern "C" aica_status aica_build_interaction_list(aica_mesh *m, double rc, doub
     f.o_dil = m->dil_off.as<int>();
     f.o_re = o_re;
     f.o_rc = o_rc;
+    f.o_rw = o_rw;
     f.orgk = a.orgk;
     for (int d = 0; d < 3; ++d) f.L[d] = a.L[d];
     f.dil_ids = m->dil_ids.as<int>();

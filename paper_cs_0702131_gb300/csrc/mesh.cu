@@ -230,8 +230,9 @@ extern "C" aica_status aica_mesh_create(const double *points, int64_t n_points, 
     std::vector<int32_t> h_bkt_off(nb + 1, 0);
     std::vector<int32_t> h_bkt_cells;
     auto range = [&](int64_t c, int d, int &i0, int &i1) {
-        i0 = (int)floor((h_lo[3 * c + d] - glo[d]) / gh[d] - 1e-6);
-        i1 = (int)floor((h_hi[3 * c + d] - glo[d]) / gh[d] + 1e-6);
+        // tolerance covers the FP32 bucket index of the point-location kernel
+        i0 = (int)floor((h_lo[3 * c + d] - glo[d]) / gh[d] - 1e-3);
+        i1 = (int)floor((h_hi[3 * c + d] - glo[d]) / gh[d] + 1e-3);
         i0 = std::max(i0, 0);
         i1 = std::min(i1, G[d] - 1);
     };
@@ -310,7 +311,7 @@ extern "C" void aica_mesh_destroy(aica_mesh *m) {
                             &m->lo, &m->hi, &m->org, &m->ntri, &m->orgk, &m->tri32, &m->vtx32, &m->edg32, &m->ctr32, &m->rad32, &m->bkt_off, &m->bkt_cells, &m->dil_off,
                             &m->dil_ids, &m->ref_src, &m->ref_n, &m->ref_off, &m->ref_ids, &m->work_off,
                             &m->work, &m->work_d32, &m->work_split, &m->proc_order, &m->cell_of, &m->order,
-                            &m->cell_off, &m->fill, &m->inv, &m->xloc, &m->xs64, &m->scratch_i32, &m->facc,
+                            &m->cell_off, &m->fill, &m->inv, &m->sph, &m->part, &m->xloc, &m->xs64, &m->scratch_i32, &m->facc,
                             &m->vsorted, &m->acc, &m->flags, &m->params, &m->tmp};
     for (auto *b : bufs) b->release();
     for (auto *v : {&m->tev, &m->tfree})

@@ -1,30 +1,42 @@
 // Pair-force kernels (steps a5-a10): the force loops of §2.3 on the binned
 // molecules and the per-cell pair schedule built with the lists.
 //
-// Schedule.  For real cell I the schedule holds its DIL cells (pairs with
-// Newton's third law, §2.3 "real-real") and, after work_split[I], every
-// referred cell (c, n) whose real-cell list contains I: those pairs act on
-// I's molecules only (§2.3 "real-referred"; the source molecules get their
-// share from the mirror referred cell).  Same-cell pairs (sorted index
-// k' > k) are walked first.  A referred molecule is never copied: it is the
-// source molecule read through the cell-pair shift Delta = o_J + n.L - o_I
+// Schedule.  For real cell I the schedule lists its DIL cells (J > I, App.
+// A.1) and then the periodic image pairs (J, n) it owns.  §2.3 evaluates a
+// real-referred pair from both sides, each time acting on the real molecule
+// only, because the source molecule may live on another processor; on one
+// device the source molecule is in memory, so each periodic image pair is
+// evaluated once with Newton's third law (the reaction goes to the source
+// molecule).  Forces are the same; the referred work halves.  Same-cell pairs
+// (sorted index k' > k, §2.3) come first.  A referred molecule is never
+// copied: it is read through the cell-pair shift Delta = o_J + n.L - o_I
 // (step a5).
 //
-// Layout.  One warp walks one cell I at a time (cells interleaved over all
-// warps of the grid).  Up to NI molecules of I sit in registers; the lanes
-// stream the concatenated molecules of the partner cells, 32 at a time (a
-// load-balanced expansion of the partner list: warp scan of partner sizes,
-// then a 5-step binary search per lane).  Each lane evaluates its partner
-// molecule against the NI molecules of I; reactions on the partner molecule
-// are summed in registers and added once per (partner molecule, I-chunk)
-// with a vector atomic; forces on I's molecules are reduced over the warp.
+// Culling.  Per step every cell carries the bounding sphere of its molecules
+// (computed at binning).  A partner cell whose sphere is farther than rc from
+// I's, and a partner molecule farther than rc from I's sphere, cannot hold a
+// pair within rc (triangle inequality; margins above the FP32 cut-off) and is
+// skipped.  The counters still report every pair of every scheduled cell pair
+// as "evaluated".
+//
+// FP32 layout.  One warp walks one cell I at a time; up to NI molecules of I
+// (4 for cells of a few molecules, 8 otherwise) sit in registers.  Partner
+// molecules are expanded from the cell ranges of 32 schedule entries at a
+// time (warp scan + binary search), culled, and compacted into a per-warp
+// shared-memory queue; each batch of 32 queued partners is evaluated with one
+// partner per lane against all molecules of the chunk (branch-free pair body).
+// A lane sums its partner's reaction in registers and adds it with one vector
+// atomic; forces on I's molecules are summed over the warp once per chunk.
 //
 // Precision (FP32 path).  Coordinates are cell-local (dyadic cell origins,
 // so o_J - o_I is exact in FP32).  Pairs whose FP32 r^2 falls within 1e-5
 // rc^2 of the cut-off are re-decided in FP64 exactly as the all-pairs
-// definition computes r^2, so the evaluated-within-rc pair set is the same as
-// in FP64.  Energy and virial are summed per cell in FP32, carried across
-// cells with compensated (Kahan) summation and reduced in FP64.
+// definition computes r^2, so the pair set within rc is the same as in FP64.
+// The virial sum over pairs of r (x) f is accumulated as
+// sum_k x_k (x) F_k + sum_l x_l (x) F_l over the forces each tile adds (both
+// in I's frame; every pair contributes f and -f, so the origin cancels).
+// Energy and virial are summed per lane in FP32 over at most four cells, then
+// in FP64 per warp; a finalize kernel adds the warps.
 #include <math.h>
 #include <string.h>
 
@@ -36,27 +48,31 @@ namespace aica {
 namespace {
 
 constexpr int kPairThreads = 256;
-constexpr int NI = 8;
+constexpr int kWarps = kPairThreads / 32;
+constexpr int kParts = 16;           // per-warp partial sums: U, W[6], counters[8]
+constexpr int NI = 8;                // i-molecules per chunk in the FP64 kernel
 
 struct SpeciesTab {
-    float4 f[kMaxSpecies * kMaxSpecies];    // sig2, 24 eps, 4 eps, u(rc) for FP32
+    float4 f[kMaxSpecies * kMaxSpecies];    // sigma^2, 24 eps, 4 eps, u(rc) for FP32
     double d[kMaxSpecies * kMaxSpecies][4]; // same in FP64
 };
 
 struct PairArgs {
     int C;
-    const int *cell_off, *work_off, *work_split;
+    const int *cell_off, *work_off;
     const WorkEntry *work;
     const float4 *work_d32;
     const float4 *xloc;
     const double *xs64;
-    float rc2_f, rc2_lo, rc2_hi;
+    const float4 *sph;           // per-cell molecule bounding spheres (local frame)
+    float rc2_lo, rc2_hi;
     double rc2_d;
     double L[3];
     int S;
     void *facc;                  // float4 (FP32) or double4 (FP64), binned order
     const void *vs;              // backward: grad_force in binned order (float4 / double4)
-    double *acc;                 // [0..6] U, W; [8..13] counters (as unsigned long long); [16..] grads
+    double *acc;                 // [0..6] U, W; [8..15] counters (as unsigned long long); [16..] grads
+    double *part;                // per-warp partial sums [warps][kParts]
     SpeciesTab tab;
 };
 
@@ -67,69 +83,6 @@ __device__ __forceinline__ float rcp_approx(float x) {
 }
 
 template <class R> struct R3 { R x, y, z; };
-
-template <class R> struct CellAcc {
-    R u, w[6];
-    __device__ void zero() { u = 0; for (int i = 0; i < 6; ++i) w[i] = 0; }
-    __device__ void scale(R s) { u *= s; for (int i = 0; i < 6; ++i) w[i] *= s; }
-};
-
-// compensated running sum
-struct Kahan {
-    float s = 0.f, c = 0.f;
-    __device__ __forceinline__ void add(float v) {
-        float y = v - c;
-        float t = s + y;
-        c = (t - s) - y;
-        s = t;
-    }
-};
-
-struct Counters {
-    unsigned long long eval[3] = {0, 0, 0};
-    unsigned within[3] = {0, 0, 0};
-};
-
-// FP64 re-decision of r^2 < rc^2 with the all-pairs definition's operation order
-__device__ __noinline__ bool band_in(const PairArgs &a, int k, int l, int np) {
-    const double *xk = a.xs64 + 3 * (size_t)k, *xl = a.xs64 + 3 * (size_t)l;
-    double dx = __dsub_rn(__dsub_rn(xk[0], xl[0]), __dmul_rn(a.L[0], (double)unpack_n(np, 0)));
-    double dy = __dsub_rn(__dsub_rn(xk[1], xl[1]), __dmul_rn(a.L[1], (double)unpack_n(np, 1)));
-    double dz = __dsub_rn(__dsub_rn(xk[2], xl[2]), __dmul_rn(a.L[2], (double)unpack_n(np, 2)));
-    double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-    return r2 < a.rc2_d;
-}
-
-// ---------------------------------------------------------------- FP32 pair
-template <bool MULTI, bool SHIFT>
-__device__ __forceinline__ void pair32(const PairArgs &a, const float4 *tab, float rx, float ry, float rz, float r2,
-                                       int spi, int spj, R3<float> &fi, R3<float> &fj, CellAcc<float> &acc,
-                                       bool newton) {
-    float sig2, c24, c4, ush;
-    if (MULTI) {
-        float4 t = tab[spi * kMaxSpecies + spj];
-        sig2 = t.x; c24 = t.y; c4 = t.z; ush = t.w;
-    } else {
-        float4 t = tab[0];
-        sig2 = t.x; c24 = t.y; c4 = t.z; ush = t.w;
-    }
-    float inv = rcp_approx(r2);
-    float s = sig2 * inv;
-    float s3 = s * s * s;
-    float fs = (c24 * inv) * s3 * fmaf(2.f, s3, -1.f);
-    float fx = fs * rx, fy = fs * ry, fz = fs * rz;
-    fi.x += fx; fi.y += fy; fi.z += fz;
-    if (newton) { fj.x -= fx; fj.y -= fy; fj.z -= fz; }
-    float u = c4 * s3 * (s3 - 1.f);
-    if (SHIFT) u -= ush;
-    acc.u += u;
-    acc.w[0] = fmaf(rx, fx, acc.w[0]);
-    acc.w[1] = fmaf(ry, fy, acc.w[1]);
-    acc.w[2] = fmaf(rz, fz, acc.w[2]);
-    acc.w[3] = fmaf(rx, fy, acc.w[3]);
-    acc.w[4] = fmaf(rx, fz, acc.w[4]);
-    acc.w[5] = fmaf(ry, fz, acc.w[5]);
-}
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -142,13 +95,133 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// Stream the partner molecules of entries [e0, e1) against the NI-chunk of I.
-template <bool NEWTON, bool MULTI, bool SHIFT>
-__device__ __forceinline__ void stream32(const PairArgs &a, const float4 *tab, int e0, int e1, int kbase, int ni,
-                                         const float4 (&xi)[NI], R3<float> (&fi)[NI], CellAcc<float> &acc,
-                                         Counters &cnt, int lane) {
-    float4 *facc = (float4 *)a.facc;
-    const int cat = NEWTON ? 1 : 2;
+// FP64 re-decision of r^2 < rc^2 with the all-pairs definition's operation order
+__device__ __noinline__ bool band_in(const PairArgs &a, int k, int l, int np) {
+    const double *xk = a.xs64 + 3 * (size_t)k, *xl = a.xs64 + 3 * (size_t)l;
+    double dx = __dsub_rn(__dsub_rn(xk[0], xl[0]), __dmul_rn(a.L[0], (double)unpack_n(np, 0)));
+    double dy = __dsub_rn(__dsub_rn(xk[1], xl[1]), __dmul_rn(a.L[1], (double)unpack_n(np, 1)));
+    double dz = __dsub_rn(__dsub_rn(xk[2], xl[2]), __dmul_rn(a.L[2], (double)unpack_n(np, 2)));
+    double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    return r2 < a.rc2_d;
+}
+
+// Per-lane running sums: U and the six virial components (FP32, flushed to
+// FP64 every few cells) and counters.
+struct Sums {
+    float v[7];
+    unsigned eval[3], within[3], tests, culls;
+    __device__ void zero() {
+#pragma unroll
+        for (int i = 0; i < 7; ++i) v[i] = 0.f;
+        for (int i = 0; i < 3; ++i) eval[i] = within[i] = 0;
+        tests = culls = 0;
+    }
+    __device__ __forceinline__ void outer(float ax, float ay, float az, float bx, float by, float bz) {
+        v[1] = fmaf(ax, bx, v[1]);
+        v[2] = fmaf(ay, by, v[2]);
+        v[3] = fmaf(az, bz, v[3]);
+        v[4] = fmaf(ax, by, v[4]);
+        v[5] = fmaf(ax, bz, v[5]);
+        v[6] = fmaf(ay, bz, v[6]);
+    }
+};
+
+// Write the warp's partial sums (FP64) and counters to part[warp].
+template <class Flt>
+__device__ void store_partials(double *part, int gwarp, const double (&dsum)[7], const unsigned (&cv)[8], int lane) {
+    double *row = part + (size_t)gwarp * kParts;
+    for (int i = 0; i < 8; ++i) {
+        unsigned s = __reduce_add_sync(0xffffffffu, cv[i]);
+        if (lane == 0) row[7 + i] = (double)s;
+    }
+    if (lane == 0)
+        for (int i = 0; i < 7; ++i) row[i] = dsum[i];
+    if (lane == 0) row[15] = 0.0;
+}
+
+// ------------------------------------------------------------------ FP32 path
+// Per-warp queue of partner molecules that survived culling: position in I's
+// frame (species bits in .w), binned index and image vector.
+constexpr int kQ = 64;
+struct WarpQueue {
+    float4 x[kQ];
+    int l[kQ];
+    int np[kQ];
+};
+
+// Lennard-Jones force factor and energy for r^2, branch-free.
+template <bool MULTI, bool SHIFT>
+__device__ __forceinline__ void lj32(const float4 *tab, int spi, int spj, float r2, float &fs, float &u) {
+    float4 t = MULTI ? tab[spi * kMaxSpecies + spj] : tab[0];
+    float inv = rcp_approx(r2);
+    float s = t.x * inv;
+    float s3 = s * s * s;
+    fs = (t.y * inv) * s3 * fmaf(2.f, s3, -1.f);
+    u = t.z * s3 * (s3 - 1.f);
+    if (SHIFT) u -= t.w;
+}
+
+// The molecules of I's current chunk (registers) and their accumulated forces.
+template <int NI_>
+struct IChunk {
+    float4 x[NI_];
+    R3<float> f[NI_];
+    int k0, ni;
+};
+
+// One lane's partner molecule xj against the chunk: every pair with
+// r^2 < rc^2 (FP32, with the FP64 re-decision near the cut) adds f to the
+// chunk's molecule and -f to the partner's reaction.  Returns the number of
+// pairs within rc.  `kmin` masks pairs with k <= l for same-cell pairs.
+template <int NI_, bool MULTI, bool SHIFT>
+__device__ __forceinline__ unsigned eval_partner(const PairArgs &a, const float4 *tab, IChunk<NI_> &c, float4 xj,
+                                                 int l, int np, int lmax_k, R3<float> &fj, float &u_acc) {
+    unsigned nin = 0;
+#pragma unroll
+    for (int t = 0; t < NI_; ++t) {
+        if (t < c.ni) {
+            float rx = c.x[t].x - xj.x, ry = c.x[t].y - xj.y, rz = c.x[t].z - xj.z;
+            float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
+            bool ok = c.k0 + t < lmax_k;
+            bool in = ok && r2 < a.rc2_lo;
+            bool band = ok && r2 >= a.rc2_lo && r2 < a.rc2_hi;
+            if (__any_sync(0xffffffffu, band))
+                if (band) in = band_in(a, c.k0 + t, l, np);
+            float fs, u;
+            lj32<MULTI, SHIFT>(tab, __float_as_int(c.x[t].w), __float_as_int(xj.w), r2, fs, u);
+            fs = in ? fs : 0.f;
+            u_acc += in ? u : 0.f;
+            nin += in;
+            float fx = fs * rx, fy = fs * ry, fz = fs * rz;
+            c.f[t].x += fx; c.f[t].y += fy; c.f[t].z += fz;
+            fj.x -= fx; fj.y -= fy; fj.z -= fz;
+        }
+    }
+    return nin;
+}
+
+// Stream the molecules of the partner cells of entries [e0, e1) against the
+// chunk: cull cells and molecules against I's sphere, compact survivors into
+// the warp queue, and evaluate them 32 at a time (lane = partner molecule).
+template <int NI_, bool MULTI, bool SHIFT>
+__device__ __forceinline__ void stream32(const PairArgs &a, const float4 *tab, IChunk<NI_> &c, Sums &sm, int e0,
+                                         int e1, float4 sI, float rcut, WarpQueue &q, int lane) {
+    const float cull_i = (rcut + sI.w) * (rcut + sI.w) * 1.00002f + 1e-5f;
+    auto run = [&](int count) {
+        bool valid = lane < count;
+        float4 xj = valid ? q.x[lane] : make_float4(1e18f, 1e18f, 1e18f, 0.f);
+        int l = valid ? q.l[lane] : 0, np = valid ? q.np[lane] : 0;
+        if (lane == 0) sm.tests += (unsigned)(count * c.ni);
+        R3<float> fj = {0.f, 0.f, 0.f};
+        unsigned nin = eval_partner<NI_, MULTI, SHIFT>(a, tab, c, xj, l, np, 0x7fffffff, fj, sm.v[0]);
+        if (np != 0) sm.within[2] += nin;
+        else sm.within[1] += nin;
+        if (nin) {
+            atomicAdd((float4 *)a.facc + l, make_float4(fj.x, fj.y, fj.z, 0.f));
+            sm.outer(xj.x, xj.y, xj.z, fj.x, fj.y, fj.z);
+        }
+    };
+    int qn = 0;
     for (int eb = e0; eb < e1; eb += 32) {
         int e = eb + lane;
         int js = 0, n = 0, np = 0;
@@ -158,9 +231,17 @@ __device__ __forceinline__ void stream32(const PairArgs &a, const float4 *tab, i
             js = a.cell_off[we.j];
             n = a.cell_off[we.j + 1] - js;
             np = we.n;
-            d = a.work_d32[e];
+            if (n > 0) {
+                if (np != 0) sm.eval[2] += (unsigned)(n * c.ni);
+                else sm.eval[1] += (unsigned)(n * c.ni);
+                d = a.work_d32[e];
+                float4 sJ = a.sph[we.j];
+                float dx = sJ.x + d.x - sI.x, dy = sJ.y + d.y - sI.y, dz = sJ.z + d.z - sI.z;
+                float R = rcut + sI.w + sJ.w;
+                sm.culls++;
+                if (dx * dx + dy * dy + dz * dz > R * R * 1.00002f + 1e-5f) n = 0;
+            }
         }
-        cnt.eval[cat] += (unsigned long long)(n * ni);
         int inc = n;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -181,124 +262,129 @@ __device__ __forceinline__ void stream32(const PairArgs &a, const float4 *tab, i
             float dy = __shfl_sync(0xffffffffu, d.y, o);
             float dz = __shfl_sync(0xffffffffu, d.z, o);
             int npl = __shfl_sync(0xffffffffu, np, o);
-            bool valid = p < total;
+            bool alive = false;
             int l = jsl + (p - exl);
-            float4 xl = valid ? a.xloc[l] : make_float4(1e18f, 1e18f, 1e18f, 0.f);
-            float xjx = xl.x + dx, xjy = xl.y + dy, xjz = xl.z + dz;
-            int spj = __float_as_int(xl.w);
-            R3<float> fj = {0.f, 0.f, 0.f};
-#pragma unroll
-            for (int t = 0; t < NI; ++t) {
-                if (t < ni) {
-                    float rx = xi[t].x - xjx, ry = xi[t].y - xjy, rz = xi[t].z - xjz;
-                    float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
-                    if (r2 < a.rc2_hi) {
-                        bool in = r2 < a.rc2_lo || band_in(a, kbase + t, l, npl);
-                        if (in) {
-                            pair32<MULTI, SHIFT>(a, tab, rx, ry, rz, r2, __float_as_int(xi[t].w), spj, fi[t], fj, acc,
-                                                 NEWTON);
-                            cnt.within[cat]++;
-                        }
-                    }
-                }
+            float4 xj;
+            if (p < total) {
+                float4 xl = a.xloc[l];
+                xj = make_float4(xl.x + dx, xl.y + dy, xl.z + dz, xl.w);
+                float cx = xj.x - sI.x, cy = xj.y - sI.y, cz = xj.z - sI.z;
+                alive = cx * cx + cy * cy + cz * cz <= cull_i;
+                sm.culls++;
             }
-            if (NEWTON && valid && (fj.x != 0.f || fj.y != 0.f || fj.z != 0.f))
-                atomicAdd(facc + l, make_float4(fj.x, fj.y, fj.z, 0.f));
+            unsigned bal = __ballot_sync(0xffffffffu, alive);
+            if (alive) {
+                int s = qn + __popc(bal & ((1u << lane) - 1u));
+                q.x[s] = xj;
+                q.l[s] = l;
+                q.np[s] = npl;
+            }
+            qn += __popc(bal);
+            __syncwarp();
+            if (qn >= 32) {
+                run(32);
+                __syncwarp();
+                qn -= 32;
+                if (lane < qn) {
+                    q.x[lane] = q.x[32 + lane];
+                    q.l[lane] = q.l[32 + lane];
+                    q.np[lane] = q.np[32 + lane];
+                }
+                __syncwarp();
+            }
         }
+    }
+    if (qn > 0) {
+        run(qn);
+        __syncwarp();
     }
 }
 
-template <bool MULTI, bool SHIFT>
-__global__ void __launch_bounds__(kPairThreads) pair_fwd32(PairArgs a) {
+template <int NI_, bool MULTI, bool SHIFT>
+__global__ void __launch_bounds__(kPairThreads, NI_ <= 4 ? 3 : 2) pair_fwd32(PairArgs a) {
     __shared__ float4 tab[kMaxSpecies * kMaxSpecies];
-    __shared__ double red[kPairThreads / 32][16];
+    __shared__ WarpQueue queues[kWarps];
+    __shared__ double dsums[kWarps][8];
     for (int i = threadIdx.x; i < kMaxSpecies * kMaxSpecies; i += blockDim.x) tab[i] = a.tab.f[i];
-    __syncthreads();
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int nwarps = gridDim.x * (kPairThreads / 32);
-    float4 *facc = (float4 *)a.facc;
-    Kahan tot[7];
-    Counters cnt;
-    for (int I = blockIdx.x * (kPairThreads / 32) + wib; I < a.C; I += nwarps) {
+    if (lane < 8) dsums[wib][lane] = 0.0;
+    __syncthreads();
+    const int gwarp = blockIdx.x * kWarps + wib;
+    const int nwarps = gridDim.x * kWarps;
+    WarpQueue &q = queues[wib];
+    double *dsum = dsums[wib];
+    const float rcut = sqrtf(a.rc2_hi);
+    Sums sm;
+    sm.zero();
+    int ncell = 0;
+    for (int I = gwarp; I < a.C; I += nwarps) {
         const int sI = a.cell_off[I], nI = a.cell_off[I + 1] - sI;
         if (nI == 0) continue;
-        const int e0 = a.work_off[I], es = a.work_split[I], e1 = a.work_off[I + 1];
-        CellAcc<float> acc;
-        acc.zero();
-        for (int pass = 0; pass < 2; ++pass) {       // 0: real-referred (one-sided), 1: same-cell + DIL
-            if (pass == 0 && es == e1) continue;
-            for (int i0 = 0; i0 < nI; i0 += NI) {
-                const int ni = min(NI, nI - i0);
-                float4 xi[NI];
-                R3<float> fi[NI];
+        const int e0 = a.work_off[I], e1 = a.work_off[I + 1];
+        const float4 sph = a.sph[I];
+        for (int i0 = 0; i0 < nI; i0 += NI_) {
+            IChunk<NI_> c;
+            c.k0 = sI + i0;
+            c.ni = min(NI_, nI - i0);
 #pragma unroll
-                for (int t = 0; t < NI; ++t) {
-                    xi[t] = t < ni ? a.xloc[sI + i0 + t] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    fi[t] = {0.f, 0.f, 0.f};
+            for (int t = 0; t < NI_; ++t) {
+                c.x[t] = t < c.ni ? a.xloc[c.k0 + t] : make_float4(1e18f, 1e18f, 1e18f, 0.f);
+                c.f[t] = {0.f, 0.f, 0.f};
+            }
+            // same-cell pairs k' > k (sorted order): lanes over k' in I
+            for (int lb = i0 + 1; lb < nI; lb += 32) {
+                int li = lb + lane;
+                bool valid = li < nI;
+                int l = sI + li;
+                float4 xl = valid ? a.xloc[l] : make_float4(2e18f, 2e18f, 2e18f, 0.f);
+                R3<float> fj = {0.f, 0.f, 0.f};
+                unsigned nin = eval_partner<NI_, MULTI, SHIFT>(a, tab, c, xl, l, 0, valid ? l : 0, fj, sm.v[0]);
+                sm.within[0] += nin;
+                if (nin) {
+                    atomicAdd((float4 *)a.facc + l, make_float4(fj.x, fj.y, fj.z, 0.f));
+                    sm.outer(xl.x, xl.y, xl.z, fj.x, fj.y, fj.z);
                 }
-                if (pass == 0) {
-                    stream32<false, MULTI, SHIFT>(a, tab, es, e1, sI + i0, ni, xi, fi, acc, cnt, lane);
-                } else {
-                    // same-cell pairs k' > k (sorted order), Newton's third law
-                    for (int lb = i0 + 1; lb < nI; lb += 32) {
-                        int li = lb + lane;
-                        bool valid = li < nI;
-                        int l = sI + li;
-                        float4 xl = valid ? a.xloc[l] : make_float4(1e18f, 1e18f, 1e18f, 0.f);
-                        R3<float> fj = {0.f, 0.f, 0.f};
+            }
+            if (lane == 0) sm.tests += (unsigned)(c.ni * (2 * nI - 2 * i0 - c.ni - 1) / 2);
+            stream32<NI_, MULTI, SHIFT>(a, tab, c, sm, e0, e1, sph, rcut, q, lane);
+            // forces on the chunk's molecules: warp sums, one vector atomic each, k-side virial
 #pragma unroll
-                        for (int t = 0; t < NI; ++t) {
-                            if (t < ni && li > i0 + t) {
-                                float rx = xi[t].x - xl.x, ry = xi[t].y - xl.y, rz = xi[t].z - xl.z;
-                                float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
-                                if (r2 < a.rc2_hi && (r2 < a.rc2_lo || band_in(a, sI + i0 + t, l, 0))) {
-                                    pair32<MULTI, SHIFT>(a, tab, rx, ry, rz, r2, __float_as_int(xi[t].w),
-                                                         __float_as_int(xl.w), fi[t], fj, acc, true);
-                                    cnt.within[0]++;
-                                }
-                            }
-                        }
-                        if (valid && (fj.x != 0.f || fj.y != 0.f || fj.z != 0.f))
-                            atomicAdd(facc + l, make_float4(fj.x, fj.y, fj.z, 0.f));
-                    }
-                    stream32<true, MULTI, SHIFT>(a, tab, e0, es, sI + i0, ni, xi, fi, acc, cnt, lane);
-                }
-                // forces on I's molecules: warp sums, one vector atomic each
-#pragma unroll
-                for (int t = 0; t < NI; ++t) {
-                    if (t < ni) {
-                        float x = warp_sum(fi[t].x), y = warp_sum(fi[t].y), z = warp_sum(fi[t].z);
-                        if (lane == t) atomicAdd(facc + sI + i0 + t, make_float4(x, y, z, 0.f));
+            for (int t = 0; t < NI_; ++t) {
+                if (t < c.ni) {
+                    float x = warp_sum(c.f[t].x), y = warp_sum(c.f[t].y), z = warp_sum(c.f[t].z);
+                    if (lane == t) {
+                        atomicAdd((float4 *)a.facc + c.k0 + t, make_float4(x, y, z, 0.f));
+                        sm.outer(c.x[t].x, c.x[t].y, c.x[t].z, x, y, z);
                     }
                 }
             }
-            if (pass == 0) acc.scale(0.5f);   // each referred pair is evaluated from both sides
         }
-        if (lane == 0) cnt.eval[0] += (unsigned long long)nI * (nI - 1) / 2;
-        tot[0].add(acc.u);
+        if (lane == 0) sm.eval[0] += (unsigned)(nI * (nI - 1) / 2);
+        if (++ncell == 4) {          // flush the FP32 running sums to FP64
+            ncell = 0;
 #pragma unroll
-        for (int i = 0; i < 6; ++i) tot[i + 1].add(acc.w[i]);
+            for (int i = 0; i < 7; ++i) {
+                float s = warp_sum(sm.v[i]);
+                if (lane == 0) dsum[i] += (double)s;
+                sm.v[i] = 0.f;
+            }
+        }
     }
-    // block reduction, then one FP64 / 64-bit atomic per value
-    double v[13];
-    for (int i = 0; i < 7; ++i) v[i] = warp_sum((double)tot[i].s - (double)tot[i].c);
-    for (int i = 0; i < 3; ++i) v[7 + i] = warp_sum((double)cnt.eval[i]);
-    for (int i = 0; i < 3; ++i) v[10 + i] = warp_sum((double)cnt.within[i]);
-    if (lane == 0)
-        for (int i = 0; i < 13; ++i) red[wib][i] = v[i];
-    __syncthreads();
-    if (threadIdx.x < 13) {
-        double s = 0;
-        for (int w = 0; w < kPairThreads / 32; ++w) s += red[w][threadIdx.x];
-        if (threadIdx.x < 7) atomicAdd(a.acc + threadIdx.x, s);
-        else atomicAdd((unsigned long long *)(a.acc + 8) + (threadIdx.x - 7), (unsigned long long)llrint(s));
+    double fin[7];
+#pragma unroll
+    for (int i = 0; i < 7; ++i) {
+        float s = warp_sum(sm.v[i]);
+        fin[i] = dsum[i] + (double)s;
     }
+    unsigned cv[8] = {sm.eval[0], sm.eval[1], sm.eval[2], sm.within[0], sm.within[1], sm.within[2], sm.tests,
+                      sm.culls};
+    store_partials<float>(a.part, gwarp, fin, cv, lane);
 }
 
-// ---------------------------------------------------------------- FP64 pair
+// ------------------------------------------------------------------ FP64 path
 template <bool MULTI, bool SHIFT>
 __device__ __forceinline__ void pair64(const double (*tab)[4], double rx, double ry, double rz, double r2, int spi,
-                                       int spj, R3<double> &fi, R3<double> &fj, CellAcc<double> &acc, bool newton) {
+                                       int spj, R3<double> &fi, R3<double> &fj, double (&acc)[7]) {
     const double *t = MULTI ? tab[spi * kMaxSpecies + spj] : tab[0];
     double inv = 1.0 / r2;
     double s = t[0] * inv;
@@ -306,12 +392,12 @@ __device__ __forceinline__ void pair64(const double (*tab)[4], double rx, double
     double fs = t[1] * inv * s3 * (2.0 * s3 - 1.0);
     double fx = fs * rx, fy = fs * ry, fz = fs * rz;
     fi.x += fx; fi.y += fy; fi.z += fz;
-    if (newton) { fj.x -= fx; fj.y -= fy; fj.z -= fz; }
+    fj.x -= fx; fj.y -= fy; fj.z -= fz;
     double u = t[2] * s3 * (s3 - 1.0);
     if (SHIFT) u -= t[3];
-    acc.u += u;
-    acc.w[0] += rx * fx; acc.w[1] += ry * fy; acc.w[2] += rz * fz;
-    acc.w[3] += rx * fy; acc.w[4] += rx * fz; acc.w[5] += ry * fz;
+    acc[0] += u;
+    acc[1] += rx * fx; acc[2] += ry * fy; acc[3] += rz * fz;
+    acc[4] += rx * fy; acc[5] += rx * fz; acc[6] += ry * fz;
 }
 
 __device__ __forceinline__ void atomic_add3(double *p, double x, double y, double z) {
@@ -329,150 +415,203 @@ __device__ __forceinline__ void sep64(const double *xk, const double *xl, const 
     r2 = __dadd_rn(__dadd_rn(__dmul_rn(rx, rx), __dmul_rn(ry, ry)), __dmul_rn(rz, rz));
 }
 
-template <bool NEWTON, bool MULTI, bool SHIFT>
-__device__ __forceinline__ void stream64(const PairArgs &a, const double (*tab)[4], int e0, int e1, int ni,
-                                         const double (&xi)[NI][3], const int (&spi)[NI], R3<double> (&fi)[NI],
-                                         CellAcc<double> &acc, Counters &cnt, int lane) {
-    double *facc = (double *)a.facc;
-    const int cat = NEWTON ? 1 : 2;
-    for (int eb = e0; eb < e1; eb += 32) {
-        int e = eb + lane;
-        int js = 0, n = 0, np = 0;
-        if (e < e1) {
-            WorkEntry we = a.work[e];
-            js = a.cell_off[we.j];
-            n = a.cell_off[we.j + 1] - js;
-            np = we.n;
-        }
-        cnt.eval[cat] += (unsigned long long)(n * ni);
-        int inc = n;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += y;
-        }
-        const int total = __shfl_sync(0xffffffffu, inc, 31);
-        const int exc = inc - n;
-        for (int p0 = 0; p0 < total; p0 += 32) {
-            int p = p0 + lane;
-            int o = 0;
-#pragma unroll
-            for (int step = 16; step > 0; step >>= 1)
-                if (__shfl_sync(0xffffffffu, inc, o + step - 1) <= p) o += step;
-            int jsl = __shfl_sync(0xffffffffu, js, o);
-            int exl = __shfl_sync(0xffffffffu, exc, o);
-            int npl = __shfl_sync(0xffffffffu, np, o);
-            if (p >= total) continue;
-            int l = jsl + (p - exl);
-            const double *xl = a.xs64 + 3 * (size_t)l;
-            int spj = __float_as_int(a.xloc[l].w);
-            R3<double> fj = {0, 0, 0};
-            bool any = false;
-#pragma unroll
-            for (int t = 0; t < NI; ++t) {
-                if (t < ni) {
-                    double rx, ry, rz, r2;
-                    sep64(xi[t], xl, a.L, npl, rx, ry, rz, r2);
-                    if (r2 < a.rc2_d) {
-                        pair64<MULTI, SHIFT>(tab, rx, ry, rz, r2, spi[t], spj, fi[t], fj, acc, NEWTON);
-                        cnt.within[cat]++;
-                        any = true;
-                    }
-                }
-            }
-            if (NEWTON && any) atomic_add3(facc + 4 * (size_t)l, fj.x, fj.y, fj.z);
-        }
-    }
-}
-
+// FP64: one warp per cell, lanes over the culled partner molecules (queue
+// batches of 32), up to NI molecules of I per chunk in registers.
 template <bool MULTI, bool SHIFT>
 __global__ void __launch_bounds__(kPairThreads) pair_fwd64(PairArgs a) {
     __shared__ double tab[kMaxSpecies * kMaxSpecies][4];
-    __shared__ double red[kPairThreads / 32][16];
+    __shared__ WarpQueue queues[kWarps];
     for (int i = threadIdx.x; i < kMaxSpecies * kMaxSpecies; i += blockDim.x)
         for (int c = 0; c < 4; ++c) tab[i][c] = a.tab.d[i][c];
     __syncthreads();
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int nwarps = gridDim.x * (kPairThreads / 32);
+    const int gwarp = blockIdx.x * kWarps + wib;
+    const int nwarps = gridDim.x * kWarps;
     double *facc = (double *)a.facc;
-    CellAcc<double> tot;
-    tot.zero();
-    Counters cnt;
-    for (int I = blockIdx.x * (kPairThreads / 32) + wib; I < a.C; I += nwarps) {
+    WarpQueue &q = queues[wib];
+    const float rcut = sqrtf(a.rc2_hi);
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    unsigned eval[3] = {0, 0, 0}, within[3] = {0, 0, 0}, tests = 0, culls = 0;
+    for (int I = gwarp; I < a.C; I += nwarps) {
         const int sI = a.cell_off[I], nI = a.cell_off[I + 1] - sI;
         if (nI == 0) continue;
-        const int e0 = a.work_off[I], es = a.work_split[I], e1 = a.work_off[I + 1];
-        CellAcc<double> acc;
-        acc.zero();
-        for (int pass = 0; pass < 2; ++pass) {
-            if (pass == 0 && es == e1) continue;
-            for (int i0 = 0; i0 < nI; i0 += NI) {
-                const int ni = min(NI, nI - i0);
-                double xi[NI][3];
-                int spi[NI];
-                R3<double> fi[NI];
+        const int e0 = a.work_off[I], e1 = a.work_off[I + 1];
+        const float4 sI4 = a.sph[I];
+        const float cull_i = (rcut + sI4.w) * (rcut + sI4.w) * 1.00002f + 1e-5f;
+        for (int i0 = 0; i0 < nI; i0 += NI) {
+            const int ni = min(NI, nI - i0);
+            double xi[NI][3];
+            int spi[NI];
+            R3<double> fi[NI];
 #pragma unroll
-                for (int t = 0; t < NI; ++t) {
-                    int k = sI + i0 + min(t, ni - 1);
-                    for (int c = 0; c < 3; ++c) xi[t][c] = a.xs64[3 * (size_t)k + c];
-                    spi[t] = __float_as_int(a.xloc[k].w);
-                    fi[t] = {0, 0, 0};
-                }
-                if (pass == 0) {
-                    stream64<false, MULTI, SHIFT>(a, tab, es, e1, ni, xi, spi, fi, acc, cnt, lane);
-                } else {
-                    for (int lb = i0 + 1; lb < nI; lb += 32) {
-                        int li = lb + lane;
-                        if (li < nI) {
-                            int l = sI + li;
-                            const double *xl = a.xs64 + 3 * (size_t)l;
-                            int spj = __float_as_int(a.xloc[l].w);
-                            R3<double> fj = {0, 0, 0};
-                            bool any = false;
+            for (int t = 0; t < NI; ++t) {
+                int k = sI + i0 + min(t, ni - 1);
+                for (int c = 0; c < 3; ++c) xi[t][c] = a.xs64[3 * (size_t)k + c];
+                spi[t] = __float_as_int(a.xloc[k].w);
+                fi[t] = {0, 0, 0};
+            }
+            // same-cell pairs k' > k
+            for (int lb = i0 + 1; lb < nI; lb += 32) {
+                int li = lb + lane;
+                if (li < nI) {
+                    int l = sI + li;
+                    const double *xl = a.xs64 + 3 * (size_t)l;
+                    int spj = __float_as_int(a.xloc[l].w);
+                    R3<double> fj = {0, 0, 0};
+                    bool any = false;
 #pragma unroll
-                            for (int t = 0; t < NI; ++t) {
-                                if (t < ni && li > i0 + t) {
-                                    double rx, ry, rz, r2;
-                                    sep64(xi[t], xl, a.L, 0, rx, ry, rz, r2);
-                                    if (r2 < a.rc2_d) {
-                                        pair64<MULTI, SHIFT>(tab, rx, ry, rz, r2, spi[t], spj, fi[t], fj, acc, true);
-                                        cnt.within[0]++;
-                                        any = true;
-                                    }
-                                }
+                    for (int t = 0; t < NI; ++t) {
+                        if (t < ni && li > i0 + t) {
+                            double rx, ry, rz, r2;
+                            sep64(xi[t], xl, a.L, 0, rx, ry, rz, r2);
+                            if (r2 < a.rc2_d) {
+                                pair64<MULTI, SHIFT>(tab, rx, ry, rz, r2, spi[t], spj, fi[t], fj, acc);
+                                within[0]++;
+                                any = true;
                             }
-                            if (any) atomic_add3(facc + 4 * (size_t)l, fj.x, fj.y, fj.z);
                         }
                     }
-                    stream64<true, MULTI, SHIFT>(a, tab, e0, es, ni, xi, spi, fi, acc, cnt, lane);
+                    if (any) atomic_add3(facc + 4 * (size_t)l, fj.x, fj.y, fj.z);
                 }
+            }
+            if (lane == 0) tests += (unsigned)(ni * (2 * nI - 2 * i0 - ni - 1) / 2);
+            // partners: cull, compact, evaluate in batches of 32
+            int qn = 0;
+            auto run = [&](int count) {
+                if (lane == 0) tests += (unsigned)(count * ni);
+                if (lane < count) {
+                    int l = q.l[lane], npl = q.np[lane];
+                    int spj = __float_as_int(q.x[lane].w);
+                    const double *xl = a.xs64 + 3 * (size_t)l;
+                    R3<double> fj = {0, 0, 0};
+                    bool any = false;
+                    unsigned nin = 0;
 #pragma unroll
-                for (int t = 0; t < NI; ++t) {
-                    if (t < ni) {
-                        double x = warp_sum(fi[t].x), y = warp_sum(fi[t].y), z = warp_sum(fi[t].z);
-                        if (lane == t) atomic_add3(facc + 4 * (size_t)(sI + i0 + t), x, y, z);
+                    for (int t = 0; t < NI; ++t) {
+                        if (t < ni) {
+                            double rx, ry, rz, r2;
+                            sep64(xi[t], xl, a.L, npl, rx, ry, rz, r2);
+                            if (r2 < a.rc2_d) {
+                                pair64<MULTI, SHIFT>(tab, rx, ry, rz, r2, spi[t], spj, fi[t], fj, acc);
+                                nin++;
+                                any = true;
+                            }
+                        }
+                    }
+                    if (npl != 0) within[2] += nin;
+                    else within[1] += nin;
+                    if (any) atomic_add3(facc + 4 * (size_t)l, fj.x, fj.y, fj.z);
+                }
+                __syncwarp();
+            };
+            for (int eb = e0; eb < e1; eb += 32) {
+                int e = eb + lane;
+                int js = 0, n = 0, np = 0;
+                float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (e < e1) {
+                    WorkEntry we = a.work[e];
+                    js = a.cell_off[we.j];
+                    n = a.cell_off[we.j + 1] - js;
+                    np = we.n;
+                    if (n > 0) {
+                        if (np != 0) eval[2] += (unsigned)(n * ni);
+                        else eval[1] += (unsigned)(n * ni);
+                        d = a.work_d32[e];
+                        float4 sJ = a.sph[we.j];
+                        float dx = sJ.x + d.x - sI4.x, dy = sJ.y + d.y - sI4.y, dz = sJ.z + d.z - sI4.z;
+                        float R = rcut + sI4.w + sJ.w;
+                        culls++;
+                        if (dx * dx + dy * dy + dz * dz > R * R * 1.00002f + 1e-5f) n = 0;
+                    }
+                }
+                int inc = n;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    int y = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= o) inc += y;
+                }
+                const int total = __shfl_sync(0xffffffffu, inc, 31);
+                const int exc = inc - n;
+                for (int p0 = 0; p0 < total; p0 += 32) {
+                    int p = p0 + lane;
+                    int o = 0;
+#pragma unroll
+                    for (int step = 16; step > 0; step >>= 1)
+                        if (__shfl_sync(0xffffffffu, inc, o + step - 1) <= p) o += step;
+                    int jsl = __shfl_sync(0xffffffffu, js, o);
+                    int exl = __shfl_sync(0xffffffffu, exc, o);
+                    float dx = __shfl_sync(0xffffffffu, d.x, o);
+                    float dy = __shfl_sync(0xffffffffu, d.y, o);
+                    float dz = __shfl_sync(0xffffffffu, d.z, o);
+                    int npl = __shfl_sync(0xffffffffu, np, o);
+                    bool alive = false;
+                    int l = jsl + (p - exl);
+                    float4 xj;
+                    if (p < total) {
+                        float4 xl = a.xloc[l];
+                        xj = make_float4(xl.x + dx, xl.y + dy, xl.z + dz, xl.w);
+                        float cx = xj.x - sI4.x, cy = xj.y - sI4.y, cz = xj.z - sI4.z;
+                        alive = cx * cx + cy * cy + cz * cz <= cull_i;
+                        culls++;
+                    }
+                    unsigned bal = __ballot_sync(0xffffffffu, alive);
+                    if (alive) {
+                        int s = qn + __popc(bal & ((1u << lane) - 1u));
+                        q.x[s] = xj;
+                        q.l[s] = l;
+                        q.np[s] = npl;
+                    }
+                    qn += __popc(bal);
+                    __syncwarp();
+                    if (qn >= 32) {
+                        run(32);
+                        qn -= 32;
+                        if (lane < qn) {
+                            q.x[lane] = q.x[32 + lane];
+                            q.l[lane] = q.l[32 + lane];
+                            q.np[lane] = q.np[32 + lane];
+                        }
+                        __syncwarp();
                     }
                 }
             }
-            if (pass == 0) acc.scale(0.5);
+            if (qn > 0) run(qn);
+#pragma unroll
+            for (int t = 0; t < NI; ++t) {
+                if (t < ni) {
+                    double x = warp_sum(fi[t].x), y = warp_sum(fi[t].y), z = warp_sum(fi[t].z);
+                    if (lane == t) atomic_add3(facc + 4 * (size_t)(sI + i0 + t), x, y, z);
+                }
+            }
         }
-        if (lane == 0) cnt.eval[0] += (unsigned long long)nI * (nI - 1) / 2;
-        tot.u += acc.u;
-        for (int i = 0; i < 6; ++i) tot.w[i] += acc.w[i];
+        if (lane == 0) eval[0] += (unsigned)(nI * (nI - 1) / 2);
     }
-    double v[13];
-    v[0] = warp_sum(tot.u);
-    for (int i = 0; i < 6; ++i) v[1 + i] = warp_sum(tot.w[i]);
-    for (int i = 0; i < 3; ++i) v[7 + i] = warp_sum((double)cnt.eval[i]);
-    for (int i = 0; i < 3; ++i) v[10 + i] = warp_sum((double)cnt.within[i]);
-    if (lane == 0)
-        for (int i = 0; i < 13; ++i) red[wib][i] = v[i];
+    double dsum[7];
+    for (int i = 0; i < 7; ++i) dsum[i] = warp_sum(acc[i]);
+    unsigned cv[8] = {eval[0], eval[1], eval[2], within[0], within[1], within[2], tests, culls};
+    store_partials<double>(a.part, gwarp, dsum, cv, lane);
+}
+
+// Sum the per-warp partials into acc[0..6] (FP64) and acc[8..15] (counters),
+// which must be zero on entry: one row per thread, block sums, one atomic per
+// value and block.
+__global__ void __launch_bounds__(256) finalize_partials(const double *part, int nwarps, double *acc) {
+    __shared__ double sh[256 / 32][kParts];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double s[15];
+    for (int i = 0; i < 15; ++i) s[i] = 0;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nwarps; r += gridDim.x * blockDim.x)
+        for (int i = 0; i < 15; ++i) s[i] += part[(size_t)r * kParts + i];
+    for (int i = 0; i < 15; ++i) {
+        double v = warp_sum(s[i]);
+        if (lane == 0) sh[w][i] = v;
+    }
     __syncthreads();
-    if (threadIdx.x < 13) {
-        double s = 0;
-        for (int w = 0; w < kPairThreads / 32; ++w) s += red[w][threadIdx.x];
-        if (threadIdx.x < 7) atomicAdd(a.acc + threadIdx.x, s);
-        else atomicAdd((unsigned long long *)(a.acc + 8) + (threadIdx.x - 7), (unsigned long long)llrint(s));
+    if (threadIdx.x < 15) {
+        double v = 0;
+        for (int j = 0; j < 256 / 32; ++j) v += sh[j][threadIdx.x];
+        if (threadIdx.x < 7) atomicAdd(acc + threadIdx.x, v);
+        else atomicAdd((unsigned long long *)(acc + 8) + (threadIdx.x - 7), (unsigned long long)llrint(v));
     }
 }
 
@@ -505,10 +644,12 @@ __global__ void finish_sums(const double *acc, double *ev, long long *counts) {
 
 // ---------------------------------------------------------------- adjoint
 // Per pair with r = x_k - x_l', f = g(r^2) r, g = 24 e inv s3 (2 s3 - 1):
-//   J = df/dr = g I + 2 g' r r^T,  g' = dg/d(r^2) = 24 e inv^2 (4 s3 - 14 s6)
-//   with w = v_k - v_l (Newton pairs) or w = v_k (one-sided): dL/dr = J w,
-//   x_k gets +J w, the partner (for referred pairs its source molecule) -J w;
-//   dL/d eps_ab = g (r.w) / eps_ab,  dL/d sigma_ab = 24 e inv (24 s6 - 6 s3) (r.w) / sigma_ab.
+//   J = df/dr = g I + 2 g' r r^T,  g' = dg/d(r^2) = 24 e inv^2 (4 s3 - 14 s6).
+// With w = v_k - v_l (v = dL/dF; every scheduled pair carries Newton's third
+// law, periodic image pairs included): dL/dr = J w, x_k gets +J w and the
+// partner (for an image pair, its source molecule) gets -J w;
+// dL/d eps_ab = g (r.w) / eps_ab and dL/d sigma_ab = 24 e inv (24 s6 - 6 s3) (r.w) / sigma_ab,
+// chained to the species parameters through the mixing rule.
 struct BwdTab {
     double eps, sig2, inv_eps, inv_sig, fa, fb;   // fa, fb: d eps_ab / d eps_a, d eps_ab / d eps_b
 };
@@ -588,39 +729,36 @@ __device__ __forceinline__ void add_grad(void *g, int s, R x, R y, R z) {
     else atomic_add3((double *)g + 4 * (size_t)s, (double)x, (double)y, (double)z);
 }
 
-// Warp per cell I, lanes over (partner molecule, I molecule) pairs of one
-// entry batch at a time: simple and exact; the adjoint is not the hot path.
+// Warp per cell I, lanes over the (molecule of I, partner molecule) pairs of
+// one schedule entry at a time; the adjoint is not on the per-step path.
 template <class R>
 __global__ void __launch_bounds__(kPairThreads) pair_bwd(BwdArgs b) {
     const PairArgs &a = b.p;
     __shared__ BwdTab tab[kMaxSpeciesBwd * kMaxSpeciesBwd];
-    __shared__ double red[kPairThreads / 32][2 * kMaxSpeciesBwd];
+    __shared__ double red[kWarps][2 * kMaxSpeciesBwd];
     for (int i = threadIdx.x; i < kMaxSpeciesBwd * kMaxSpeciesBwd; i += blockDim.x) tab[i] = b.t[i];
     __syncthreads();
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int nwarps = gridDim.x * (kPairThreads / 32);
+    const int nwarps = gridDim.x * kWarps;
     BwdLane<double> tot;
     for (int q = 0; q < kMaxSpeciesBwd; ++q) tot.ge[q] = tot.gs[q] = 0;
-    for (int I = blockIdx.x * (kPairThreads / 32) + wib; I < a.C; I += nwarps) {
+    for (int I = blockIdx.x * kWarps + wib; I < a.C; I += nwarps) {
         const int sI = a.cell_off[I], nI = a.cell_off[I + 1] - sI;
         if (nI == 0) continue;
-        const int e0 = a.work_off[I], es = a.work_split[I], e1 = a.work_off[I + 1];
+        const int e0 = a.work_off[I], e1 = a.work_off[I + 1];
         BwdLane<R> gl;
         for (int q = 0; q < kMaxSpeciesBwd; ++q) gl.ge[q] = gl.gs[q] = R(0);
-        // entry -1: the cell itself (pairs k' > k); then e0..e1
+        // entry e0 - 1 stands for the cell itself (pairs k' > k)
         for (int e = e0 - 1; e < e1; ++e) {
             int J, np = 0;
             float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
-            bool newton;
             if (e < e0) {
                 J = I;
-                newton = true;
             } else {
                 WorkEntry we = a.work[e];
                 J = we.j;
                 np = we.n;
                 d = a.work_d32[e];
-                newton = e < es;
             }
             const int sJ = a.cell_off[J], nJ = a.cell_off[J + 1] - sJ;
             const int npairs = nI * nJ;
@@ -635,14 +773,10 @@ __global__ void __launch_bounds__(kPairThreads) pair_bwd(BwdArgs b) {
                 if (!in) continue;
                 R vkx, vky, vkz, vlx, vly, vlz;
                 ldv<R>(a.vs, k, vkx, vky, vkz);
-                R wx = vkx, wy = vky, wz = vkz;
-                if (newton) {
-                    ldv<R>(a.vs, l, vlx, vly, vlz);
-                    wx -= vlx; wy -= vly; wz -= vlz;
-                }
+                ldv<R>(a.vs, l, vlx, vly, vlz);
                 R3<R> gi = {0, 0, 0}, gj = {0, 0, 0};
-                bwd_pair<R>(tab, b.S, rx, ry, rz, r2, __float_as_int(xk.w), __float_as_int(a.xloc[l].w), wx, wy,
-                            wz, gi, gj, gl);
+                bwd_pair<R>(tab, b.S, rx, ry, rz, r2, __float_as_int(xk.w), __float_as_int(a.xloc[l].w), vkx - vlx,
+                            vky - vly, vkz - vlz, gi, gj, gl);
                 add_grad<R>(a.facc, k, gi.x, gi.y, gi.z);
                 add_grad<R>(a.facc, l, gj.x, gj.y, gj.z);
             }
@@ -662,7 +796,7 @@ __global__ void __launch_bounds__(kPairThreads) pair_bwd(BwdArgs b) {
     __syncthreads();
     if (threadIdx.x < 2 * kMaxSpeciesBwd) {
         double s = 0;
-        for (int w = 0; w < kPairThreads / 32; ++w) s += red[w][threadIdx.x];
+        for (int w = 0; w < kWarps; ++w) s += red[w][threadIdx.x];
         atomicAdd(a.acc + 16 + threadIdx.x, s);
     }
 }
@@ -689,10 +823,10 @@ __global__ void finish_bwd(const double *acc, int S, double *ge, double *gs) {
     }
 }
 
+// grid: enough warps to fill the GPU, at least two cells per warp
 int pair_grid(int C) {
-    int warps = kPairThreads / 32;
-    int need = (C + warps - 1) / warps;
-    return std::max(1, std::min(need, 152 * 8));
+    int need = (C + 2 * kWarps - 1) / (2 * kWarps);
+    return std::max(1, std::min(need, 152 * 16));
 }
 
 aica_status fill_params(aica_mesh *m, const aica_lj *lj, int max_s, PairArgs &a) {
@@ -731,19 +865,19 @@ void fill_common(aica_mesh *m, PairArgs &a) {
     a.C = (int)m->n_cells;
     a.cell_off = m->cell_off.as<int>();
     a.work_off = m->work_off.as<int>();
-    a.work_split = m->work_split.as<int>();
     a.work = m->work.as<WorkEntry>();
     a.work_d32 = m->work_d32.as<float4>();
     a.xloc = m->xloc.as<float4>();
     a.xs64 = m->xs64.as<double>();
+    a.sph = m->sph.as<float4>();
     double rc2 = m->rc * m->rc;
     a.rc2_d = rc2;
-    a.rc2_f = (float)rc2;
     a.rc2_lo = (float)(rc2 * (1 - 1e-5));
     a.rc2_hi = (float)(rc2 * (1 + 1e-5));
     for (int d = 0; d < 3; ++d) a.L[d] = m->box.periodic[d] ? m->box.L[d] : 0.0;
     a.facc = m->facc.p;
     a.acc = m->acc.as<double>();
+    a.part = m->part.as<double>();
 }
 
 aica_status check_flags(aica_mesh *m, cudaStream_t st) {
@@ -754,6 +888,17 @@ aica_status check_flags(aica_mesh *m, cudaStream_t st) {
     if (flags & kFlagOutside) { set_error("some molecules lie in no cell"); return AICA_ERR_OUTSIDE_MESH; }
     if (flags & kFlagCapacity) { set_error("a kernel capacity was exceeded"); return AICA_ERR_CAPACITY; }
     return AICA_OK;
+}
+
+template <int TI>
+void launch_fwd32(const PairArgs &a, bool multi, bool shift, int grid, cudaStream_t st) {
+    if (multi) {
+        if (shift) pair_fwd32<TI, true, true><<<grid, kPairThreads, 0, st>>>(a);
+        else pair_fwd32<TI, true, false><<<grid, kPairThreads, 0, st>>>(a);
+    } else {
+        if (shift) pair_fwd32<TI, false, true><<<grid, kPairThreads, 0, st>>>(a);
+        else pair_fwd32<TI, false, false><<<grid, kPairThreads, 0, st>>>(a);
+    }
 }
 
 }  // namespace
@@ -770,6 +915,8 @@ extern "C" aica_status aica_forces(aica_mesh *m, const aica_lj *lj, aica_precisi
     PairArgs a{};
     aica_status s = fill_params(m, lj, kMaxSpecies, a);
     if (s != AICA_OK) return s;
+    const int grid = pair_grid((int)m->n_cells);
+    AICA_CUDA(m->part.reserve(sizeof(double) * kParts * grid * kWarps));
     fill_common(m, a);
     m->launches = 0;
     const int64_t n = m->n_mol;
@@ -777,17 +924,12 @@ extern "C" aica_status aica_forces(aica_mesh *m, const aica_lj *lj, aica_precisi
     if (n > 0) AICA_CUDA(cudaMemsetAsync(m->facc.p, 0, (f64 ? 4 * sizeof(double) : sizeof(float4)) * n, st));
     AICA_CUDA(cudaMemsetAsync(m->acc.p, 0, 16 * sizeof(double), st));
     const bool multi = a.S > 1, shift = lj->shift != 0;
-    const int grid = pair_grid(a.C);
     cudaEvent_t tstop;
     AICA_CUDA(timing_begin(m, st, &tstop));
     if (!f64) {
-        if (multi) {
-            if (shift) pair_fwd32<true, true><<<grid, kPairThreads, 0, st>>>(a);
-            else pair_fwd32<true, false><<<grid, kPairThreads, 0, st>>>(a);
-        } else {
-            if (shift) pair_fwd32<false, true><<<grid, kPairThreads, 0, st>>>(a);
-            else pair_fwd32<false, false><<<grid, kPairThreads, 0, st>>>(a);
-        }
+        // i-chunk width: 4 for cells of a few molecules (tetrahedra), 8 otherwise
+        if ((double)n < 5.0 * (double)a.C) launch_fwd32<4>(a, multi, shift, grid, st);
+        else launch_fwd32<8>(a, multi, shift, grid, st);
     } else {
         if (multi) {
             if (shift) pair_fwd64<true, true><<<grid, kPairThreads, 0, st>>>(a);
@@ -798,11 +940,13 @@ extern "C" aica_status aica_forces(aica_mesh *m, const aica_lj *lj, aica_precisi
         }
     }
     AICA_CUDA(timing_end(tstop, st));
+    finalize_partials<<<(grid * kWarps + 255) / 256, 256, 0, st>>>(a.part, grid * kWarps, a.acc);
+    m->launches = 2;
     if (n > 0) {
         if (f64) unsort_forces<double><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m->inv.as<int>(), n, m->facc.p, (double *)force_out, 1);
         else unsort_forces<float><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m->inv.as<int>(), n, m->facc.p, (float *)force_out, 0);
+        m->launches++;
     }
-    m->launches = n > 0 ? 2 : 1;
     if (ev_out || counts_out) {
         finish_sums<<<1, 32, 0, st>>>(m->acc.as<double>(), ev_out, (long long *)counts_out);
         m->launches++;

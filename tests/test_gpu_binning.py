@@ -23,14 +23,18 @@ def test_binning_equals_oracle(name):
     np.testing.assert_array_equal(cell_off, o["cell_off"])
 
 
-def test_binning_after_displacement_large():
+@pytest.mark.parametrize("dist", [0.01, 0.5])
+def test_rebinning_after_displacement(dist):
+    """Re-binning uses the previous cells as a search hint; the result stays exact."""
     c = synth.make("c2", 4)
+    m, pos, sp, _ = gpu_setup(c)
     rng = np.random.default_rng(7)
-    c["pos"] = synth.random_displacement(c["pos"], 0.5, rng, c["box"]["L"], c["box"]["periodic"])
-    m, pos, sp, (cell_of, order, cell_off) = gpu_setup(c)
+    c["pos"] = synth.random_displacement(c["pos"], dist, rng, c["box"]["L"], c["box"]["periodic"])
+    cell_of, order, cell_off = m.bin(torch.tensor(c["pos"], device="cuda"), sp)
     o = oracle_all(c, lists=False)
-    np.testing.assert_array_equal(cell_of, o["cell"])
-    np.testing.assert_array_equal(order, o["order"])
+    np.testing.assert_array_equal(cell_of.cpu().numpy(), o["cell"])
+    np.testing.assert_array_equal(order.cpu().numpy(), o["order"])
+    np.testing.assert_array_equal(cell_off.cpu().numpy(), o["cell_off"])
 
 
 @pytest.mark.parametrize("tets", [False, True])
