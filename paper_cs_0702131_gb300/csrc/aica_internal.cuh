@@ -96,6 +96,7 @@ struct aica_mesh {
     int G[3] = {1, 1, 1};
     double glo[3] = {0, 0, 0}, gh[3] = {1, 1, 1};
     aica::DevBuf bkt_off, bkt_cells;
+    aica::DevBuf nbr_off, nbr;                               // face neighbours of each cell (CSR)
     // Host copies kept for the list builder's bucket grid.
     std::vector<double> h_ctr, h_rad;
 
@@ -105,7 +106,7 @@ struct aica_mesh {
     int64_t n_dil = 0, n_ref = 0, n_ref_ids = 0, n_ties = 0, n_work = 0;
     aica::DevBuf dil_off, dil_ids, ref_src, ref_n, ref_off, ref_ids;   // int32 (ref_n: 3 int32)
     aica::DevBuf work_off, work, work_d32;   // [C+1] int32 (index of first DIL entry), WorkEntry, float4 shift
-    aica::DevBuf work_split;                 // [C] int32: first referred entry of each cell
+    aica::DevBuf work_split;                 // [C] int32: first periodic-image entry of each cell
     aica::DevBuf proc_order;                 // [C] int32: cell processing order (spatially local)
 
     // Binned molecules (device), valid when binned.
@@ -115,6 +116,7 @@ struct aica_mesh {
     int max_species = -1;                    // from the last checked binning, -1 if unknown
     aica::DevBuf sph;                        // [C] float4 molecule bounding sphere per cell (local frame)
     aica::DevBuf part;                       // per-warp partial sums of the pair kernels
+    aica::DevBuf miss;                       // molecules whose previous cell no longer holds them
     int64_t n_mol_prev = -1;                 // molecule count of the previous binning
     bool hint_valid = false;                 // cell_of holds that binning (a search hint)
     aica::DevBuf facc, vsorted;              // force / gradient accumulators in binned order

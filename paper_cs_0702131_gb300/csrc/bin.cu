@@ -8,6 +8,11 @@
 //                other (star-shaped) cells by the cone from the vertex mean
 //                through each face triangle.  FP32 filter on cell-local
 //                coordinates, FP64 and exact slow paths (predicates.cuh).
+//   bin_locate_hint / bin_locate_miss   when the same molecules were binned
+//                before: test each molecule's previous cell, collect the
+//                ones that left it, then search those among the face
+//                neighbours of the previous cell and finally the grid.  The
+//                previous cell is only a search order: the test is exact.
 //   bin_count    warp-aggregated histogram of cells (match_any + one atomic)
 //   (scan)       cell offsets
 //   bin_scatter  warp-aggregated slot claims
@@ -29,6 +34,8 @@ namespace {
 struct BinArgs {
     int64_t n;
     const int *hint;       // previous cell of each molecule (or NULL)
+    const int *nbr_off, *nbr;
+    int *miss;             // [0] = count, then molecule indices
     float glo_f[3], inv_gh_f[3], gh_f[3];
     const double *pos;
     const int *species;
@@ -94,46 +101,95 @@ __device__ __forceinline__ float3 local_to(const BinArgs &a, const double *p, in
                        (float)(p[2] - a.orgk[3 * c + 2] * (1.0 / 1024.0)));
 }
 
-__global__ void __launch_bounds__(256) bin_locate(BinArgs a) {
-    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= a.n) return;
-    double p[3];
-    bool ok = true;
-    int ib[3];
+__device__ __forceinline__ void wrapped_position(const BinArgs &a, int64_t k, double *p, bool &ok) {
+    ok = true;
     for (int d = 0; d < 3; ++d) {
         p[d] = a.pos[3 * k + d];
         if (a.per[d]) p[d] = wrap_coord(p[d], a.L[d]);
         if (!(p[d] >= a.glo[d] && p[d] <= a.ghi[d])) ok = false;
+    }
+}
+
+// Search the bucket grid for the cell holding p (skipping cell `skip`).
+__device__ int grid_search(const BinArgs &a, const double *p, int skip) {
+    int ib[3];
+    for (int d = 0; d < 3; ++d)
         // bucket index in FP32; the buckets are registered with a tolerance
         ib[d] = min(max((int)floorf((float)(p[d] - a.glo[d]) * a.inv_gh_f[d]), 0), a.G[d] - 1);
+    const int b = (ib[0] * a.G[1] + ib[1]) * a.G[2] + ib[2];
+    // dyadic bucket origin: p relative to it is one rounding from exact
+    int kb[3];
+    for (int d = 0; d < 3; ++d) kb[d] = (int)rintf((a.glo_f[d] + ((float)ib[d] + 0.5f) * a.gh_f[d]) * 1024.0f);
+    const float3 pb = make_float3((float)(p[0] - kb[0] * (1.0 / 1024.0)), (float)(p[1] - kb[1] * (1.0 / 1024.0)),
+                                  (float)(p[2] - kb[2] * (1.0 / 1024.0)));
+    for (int i = a.bkt_off[b]; i < a.bkt_off[b + 1]; ++i) {
+        const int c = a.bkt_cells[i];
+        if (c == skip) continue;
+        const float3 q = make_float3(pb.x - (float)(a.orgk[3 * c] - kb[0]) * (1.0f / 1024.0f),
+                                     pb.y - (float)(a.orgk[3 * c + 1] - kb[1]) * (1.0f / 1024.0f),
+                                     pb.z - (float)(a.orgk[3 * c + 2] - kb[2]) * (1.0f / 1024.0f));
+        if (cell_contains(a, c, q, p)) return c;
     }
-    int found = -1;
-    // the molecule's previous cell first (a search hint: the test is exact either way)
-    int h = a.hint ? a.hint[k] : -1;
-    if (ok && h >= 0 && cell_contains(a, h, local_to(a, p, h), p)) found = h;
-    if (ok && found < 0) {
-        int b = (ib[0] * a.G[1] + ib[1]) * a.G[2] + ib[2];
-        // dyadic bucket origin: p relative to it is one rounding from exact
-        int kb[3];
-        float3 pb;
-        for (int d = 0; d < 3; ++d) kb[d] = (int)rintf((a.glo_f[d] + ((float)ib[d] + 0.5f) * a.gh_f[d]) * 1024.0f);
-        pb.x = (float)(p[0] - kb[0] * (1.0 / 1024.0));
-        pb.y = (float)(p[1] - kb[1] * (1.0 / 1024.0));
-        pb.z = (float)(p[2] - kb[2] * (1.0 / 1024.0));
-        for (int i = a.bkt_off[b]; i < a.bkt_off[b + 1]; ++i) {
-            int c = a.bkt_cells[i];
-            if (c == h) continue;
-            float3 q = make_float3(pb.x - (float)(a.orgk[3 * c] - kb[0]) * (1.0f / 1024.0f),
-                                   pb.y - (float)(a.orgk[3 * c + 1] - kb[1]) * (1.0f / 1024.0f),
-                                   pb.z - (float)(a.orgk[3 * c + 2] - kb[2]) * (1.0f / 1024.0f));
-            if (cell_contains(a, c, q, p)) {
-                found = c;
-                break;
-            }
-        }
-    }
+    return -1;
+}
+
+// Full search for every molecule (no previous cells).
+__global__ void __launch_bounds__(256) bin_locate(BinArgs a) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= a.n) return;
+    double p[3];
+    bool ok;
+    wrapped_position(a, k, p, ok);
+    const int found = ok ? grid_search(a, p, -1) : -1;
     a.cell_of[k] = found;
     if (found < 0) atomicOr(a.flags, kFlagOutside);
+}
+
+// Previous cell first; molecules that left it go to the miss list.
+__global__ void __launch_bounds__(256) bin_locate_hint(BinArgs a) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool miss = false;
+    if (k < a.n) {
+        double p[3];
+        bool ok;
+        wrapped_position(a, k, p, ok);
+        const int h = a.hint[k];
+        if (ok && h >= 0 && cell_contains(a, h, local_to(a, p, h), p)) {
+            a.cell_of[k] = h;
+        } else if (ok) {
+            miss = true;
+        } else {
+            a.cell_of[k] = -1;
+            atomicOr(a.flags, kFlagOutside);
+        }
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, miss);
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == 0 && bal) base = atomicAdd(a.miss, __popc(bal));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (miss) a.miss[1 + base + __popc(bal & ((1u << lane) - 1u))] = (int)k;
+}
+
+// Molecules that left their previous cell: its face neighbours, then the grid.
+__global__ void __launch_bounds__(256) bin_locate_miss(BinArgs a) {
+    const int nm = a.miss[0];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nm; i += gridDim.x * blockDim.x) {
+        const int k = a.miss[1 + i];
+        double p[3];
+        bool ok;
+        wrapped_position(a, k, p, ok);
+        const int h = a.hint[k];
+        int found = -1;
+        if (h >= 0)
+            for (int j = a.nbr_off[h]; j < a.nbr_off[h + 1] && found < 0; ++j) {
+                const int c = a.nbr[j];
+                if (cell_contains(a, c, local_to(a, p, c), p)) found = c;
+            }
+        if (found < 0) found = grid_search(a, p, h);
+        a.cell_of[k] = found;
+        if (found < 0) atomicOr(a.flags, kFlagOutside);
+    }
 }
 
 __global__ void __launch_bounds__(256) bin_count(const int *cell_of, int64_t n, int *cnt) {
@@ -250,6 +306,7 @@ extern "C" aica_status aica_bin_molecules(aica_mesh *m, const double *pos, const
     AICA_CUDA(m->cell_off.reserve(sizeof(int) * (C + 1)));
     AICA_CUDA(m->fill.reserve(sizeof(int) * (C + 1)));
     AICA_CUDA(m->sph.reserve(sizeof(float4) * C));
+    AICA_CUDA(m->miss.reserve(sizeof(int) * (std::max<int64_t>(n, 1) + 1)));
     AICA_CUDA(m->scratch_i32.reserve(sizeof(int) * (scan_work_items(C) + 8)));
     m->n_mol = n;
     BinArgs a{};
@@ -281,6 +338,9 @@ extern "C" aica_status aica_bin_molecules(aica_mesh *m, const double *pos, const
     }
     // the previous binning of the same molecules is a search hint (exact result regardless)
     a.hint = (m->hint_valid && m->n_mol_prev == n) ? m->cell_of.as<int>() : nullptr;
+    a.nbr_off = m->nbr_off.as<int>();
+    a.nbr = m->nbr.as<int>();
+    a.miss = m->miss.as<int>();
     a.cell_of = m->cell_of.as<int>();
     a.flags = m->flags.as<unsigned>();
     int *cnt = m->fill.as<int>();
@@ -289,9 +349,17 @@ extern "C" aica_status aica_bin_molecules(aica_mesh *m, const double *pos, const
     AICA_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (C + 1), st));
     unsigned nb = (unsigned)((n + 255) / 256);
     if (n > 0) {
-        bin_locate<<<nb, 256, 0, st>>>(a);
+        if (a.hint) {
+            AICA_CUDA(cudaMemsetAsync(m->miss.p, 0, sizeof(int), st));
+            bin_locate_hint<<<nb, 256, 0, st>>>(a);
+            bin_locate_miss<<<152 * 4, 256, 0, st>>>(a);
+            m->launches += 2;
+        } else {
+            bin_locate<<<nb, 256, 0, st>>>(a);
+            m->launches += 1;
+        }
         bin_count<<<nb, 256, 0, st>>>(a.cell_of, n, cnt);
-        m->launches += 2;
+        m->launches += 1;
     }
     m->launches += exclusive_scan<int, int>(cnt, C, off, m->scratch_i32.as<int>(), st);
     AICA_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (C + 1), st));

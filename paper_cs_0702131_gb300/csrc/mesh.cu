@@ -259,6 +259,24 @@ extern "C" aica_status aica_mesh_create(const double *points, int64_t n_points, 
         }
     }
 
+    // face neighbours of each cell (point-location search order after a move)
+    std::vector<int32_t> h_nbr_off(n_cells + 1, 0), h_nbr;
+    for (int64_t f = 0; f < n_faces; ++f)
+        if (neighbour[f] >= 0) {
+            h_nbr_off[owner[f] + 1]++;
+            h_nbr_off[neighbour[f] + 1]++;
+        }
+    for (int64_t c = 0; c < n_cells; ++c) h_nbr_off[c + 1] += h_nbr_off[c];
+    h_nbr.resize(h_nbr_off[n_cells]);
+    {
+        std::vector<int32_t> fl(h_nbr_off.begin(), h_nbr_off.end() - 1);
+        for (int64_t f = 0; f < n_faces; ++f)
+            if (neighbour[f] >= 0) {
+                h_nbr[fl[owner[f]]++] = (int32_t)neighbour[f];
+                h_nbr[fl[neighbour[f]]++] = (int32_t)owner[f];
+            }
+    }
+
     aica_mesh *m = new (std::nothrow) aica_mesh();
     if (!m) { set_error("host allocation failed"); return AICA_ERR_OOM; }
     cudaGetDevice(&m->device);
@@ -288,6 +306,8 @@ extern "C" aica_status aica_mesh_create(const double *points, int64_t n_points, 
     if (e == cudaSuccess) e = upload(m->edg32, h_edg32);
     if (e == cudaSuccess) e = upload(m->ctr32, h_ctr32);
     if (e == cudaSuccess) e = upload(m->rad32, h_rad32);
+    if (e == cudaSuccess) e = upload(m->nbr_off, h_nbr_off);
+    if (e == cudaSuccess) e = upload(m->nbr, h_nbr);
     if (e == cudaSuccess) e = upload(m->bkt_off, h_bkt_off);
     if (e == cudaSuccess) e = upload(m->bkt_cells, h_bkt_cells);
     if (e == cudaSuccess) { e = m->flags.reserve(16); what = "flags"; }
@@ -308,7 +328,7 @@ extern "C" aica_status aica_mesh_create(const double *points, int64_t n_points, 
 extern "C" void aica_mesh_destroy(aica_mesh *m) {
     if (!m) return;
     aica::DevBuf *bufs[] = {&m->tri_off, &m->tri, &m->vtx_off, &m->vtx, &m->edg_off, &m->edg, &m->ctr, &m->rad,
-                            &m->lo, &m->hi, &m->org, &m->ntri, &m->orgk, &m->tri32, &m->vtx32, &m->edg32, &m->ctr32, &m->rad32, &m->bkt_off, &m->bkt_cells, &m->dil_off,
+                            &m->lo, &m->hi, &m->org, &m->ntri, &m->orgk, &m->tri32, &m->vtx32, &m->edg32, &m->ctr32, &m->rad32, &m->bkt_off, &m->bkt_cells, &m->nbr_off, &m->nbr, &m->dil_off,
                             &m->dil_ids, &m->ref_src, &m->ref_n, &m->ref_off, &m->ref_ids, &m->work_off,
                             &m->work, &m->work_d32, &m->work_split, &m->proc_order, &m->cell_of, &m->order,
                             &m->cell_off, &m->fill, &m->inv, &m->sph, &m->part, &m->xloc, &m->xs64, &m->scratch_i32, &m->facc,

@@ -33,7 +33,7 @@
 // rc^2 of the cut-off are re-decided in FP64 exactly as the all-pairs
 // definition computes r^2, so the pair set within rc is the same as in FP64.
 // The virial sum over pairs of r (x) f is accumulated as
-// sum_k x_k (x) F_k + sum_l x_l (x) F_l over the forces each tile adds (both
+// sum_k x_k (x) F_k + sum_l x_l (x) F_l over the forces each warp adds (both
 // in I's frame; every pair contributes f and -f, so the origin cancels).
 // Energy and virial are summed per lane in FP32 over at most four cells, then
 // in FP64 per warp; a finalize kernel adds the warps.
@@ -149,10 +149,15 @@ struct WarpQueue {
     int np[kQ];
 };
 
-// Lennard-Jones force factor and energy for r^2, branch-free.
+// Same-cell candidates carry this marker in their image field: they pair
+// only with chunk molecules of lower binned index (k' > k, §2.3).
+constexpr int kSameCell = 1 << 24;
+
+// Lennard-Jones force factor and energy for r^2, branch-free.  t0 holds the
+// single-species parameters (sigma^2, 24 eps, 4 eps, u(rc)).
 template <bool MULTI, bool SHIFT>
-__device__ __forceinline__ void lj32(const float4 *tab, int spi, int spj, float r2, float &fs, float &u) {
-    float4 t = MULTI ? tab[spi * kMaxSpecies + spj] : tab[0];
+__device__ __forceinline__ void lj32(const float4 *tab, float4 t0, int spi, int spj, float r2, float &fs, float &u) {
+    float4 t = MULTI ? tab[spi * kMaxSpecies + spj] : t0;
     float inv = rcp_approx(r2);
     float s = t.x * inv;
     float s3 = s * s * s;
@@ -172,11 +177,12 @@ struct IChunk {
 // One lane's partner molecule xj against the chunk: every pair with
 // r^2 < rc^2 (FP32, with the FP64 re-decision near the cut) adds f to the
 // chunk's molecule and -f to the partner's reaction.  Returns the number of
-// pairs within rc.  `kmin` masks pairs with k <= l for same-cell pairs.
+// pairs within rc.  Only chunk molecules k < lmax_k take part.
 template <int NI_, bool MULTI, bool SHIFT>
 __device__ __forceinline__ unsigned eval_partner(const PairArgs &a, const float4 *tab, IChunk<NI_> &c, float4 xj,
                                                  int l, int np, int lmax_k, R3<float> &fj, float &u_acc) {
     unsigned nin = 0;
+    const float4 t0 = tab[0];
 #pragma unroll
     for (int t = 0; t < NI_; ++t) {
         if (t < c.ni) {
@@ -188,7 +194,7 @@ __device__ __forceinline__ unsigned eval_partner(const PairArgs &a, const float4
             if (__any_sync(0xffffffffu, band))
                 if (band) in = band_in(a, c.k0 + t, l, np);
             float fs, u;
-            lj32<MULTI, SHIFT>(tab, __float_as_int(c.x[t].w), __float_as_int(xj.w), r2, fs, u);
+            lj32<MULTI, SHIFT>(tab, t0, __float_as_int(c.x[t].w), __float_as_int(xj.w), r2, fs, u);
             fs = in ? fs : 0.f;
             u_acc += in ? u : 0.f;
             nin += in;
@@ -205,7 +211,7 @@ __device__ __forceinline__ unsigned eval_partner(const PairArgs &a, const float4
 // the warp queue, and evaluate them 32 at a time (lane = partner molecule).
 template <int NI_, bool MULTI, bool SHIFT>
 __device__ __forceinline__ void stream32(const PairArgs &a, const float4 *tab, IChunk<NI_> &c, Sums &sm, int e0,
-                                         int e1, float4 sI, float rcut, WarpQueue &q, int lane) {
+                                         int e1, float4 sI, float rcut, WarpQueue &q, int qn, int lane) {
     const float cull_i = (rcut + sI.w) * (rcut + sI.w) * 1.00002f + 1e-5f;
     auto run = [&](int count) {
         bool valid = lane < count;
@@ -213,15 +219,17 @@ __device__ __forceinline__ void stream32(const PairArgs &a, const float4 *tab, I
         int l = valid ? q.l[lane] : 0, np = valid ? q.np[lane] : 0;
         if (lane == 0) sm.tests += (unsigned)(count * c.ni);
         R3<float> fj = {0.f, 0.f, 0.f};
-        unsigned nin = eval_partner<NI_, MULTI, SHIFT>(a, tab, c, xj, l, np, 0x7fffffff, fj, sm.v[0]);
-        if (np != 0) sm.within[2] += nin;
+        const bool same = np == kSameCell;
+        unsigned nin = eval_partner<NI_, MULTI, SHIFT>(a, tab, c, xj, l, same ? 0 : np, same ? l : 0x7fffffff, fj,
+                                                       sm.v[0]);
+        if (same) sm.within[0] += nin;
+        else if (np != 0) sm.within[2] += nin;
         else sm.within[1] += nin;
         if (nin) {
             atomicAdd((float4 *)a.facc + l, make_float4(fj.x, fj.y, fj.z, 0.f));
             sm.outer(xj.x, xj.y, xj.z, fj.x, fj.y, fj.z);
         }
     };
-    int qn = 0;
     for (int eb = e0; eb < e1; eb += 32) {
         int e = eb + lane;
         int js = 0, n = 0, np = 0;
@@ -331,22 +339,24 @@ __global__ void __launch_bounds__(kPairThreads, NI_ <= 4 ? 3 : 2) pair_fwd32(Pai
                 c.x[t] = t < c.ni ? a.xloc[c.k0 + t] : make_float4(1e18f, 1e18f, 1e18f, 0.f);
                 c.f[t] = {0.f, 0.f, 0.f};
             }
-            // same-cell pairs k' > k (sorted order): lanes over k' in I
+            // same-cell pairs k' > k (sorted order): I's later molecules enter
+            // the queue first, marked so they pair only with lower indices
+            int qn = 0;
             for (int lb = i0 + 1; lb < nI; lb += 32) {
-                int li = lb + lane;
-                bool valid = li < nI;
-                int l = sI + li;
-                float4 xl = valid ? a.xloc[l] : make_float4(2e18f, 2e18f, 2e18f, 0.f);
-                R3<float> fj = {0.f, 0.f, 0.f};
-                unsigned nin = eval_partner<NI_, MULTI, SHIFT>(a, tab, c, xl, l, 0, valid ? l : 0, fj, sm.v[0]);
-                sm.within[0] += nin;
-                if (nin) {
-                    atomicAdd((float4 *)a.facc + l, make_float4(fj.x, fj.y, fj.z, 0.f));
-                    sm.outer(xl.x, xl.y, xl.z, fj.x, fj.y, fj.z);
+                const int li = lb + lane;
+                if (li < nI) {
+                    q.x[qn + lane] = a.xloc[sI + li];
+                    q.l[qn + lane] = sI + li;
+                    q.np[qn + lane] = kSameCell;
+                }
+                qn += min(32, nI - lb);
+                __syncwarp();
+                if (qn >= 32) {          // only for cells of more than 33 molecules
+                    qn = 0;
+                    stream32<NI_, MULTI, SHIFT>(a, tab, c, sm, 0, 0, sph, rcut, q, 32, lane);
                 }
             }
-            if (lane == 0) sm.tests += (unsigned)(c.ni * (2 * nI - 2 * i0 - c.ni - 1) / 2);
-            stream32<NI_, MULTI, SHIFT>(a, tab, c, sm, e0, e1, sph, rcut, q, lane);
+            stream32<NI_, MULTI, SHIFT>(a, tab, c, sm, e0, e1, sph, rcut, q, qn, lane);
             // forces on the chunk's molecules: warp sums, one vector atomic each, k-side virial
 #pragma unroll
             for (int t = 0; t < NI_; ++t) {
@@ -890,14 +900,14 @@ aica_status check_flags(aica_mesh *m, cudaStream_t st) {
     return AICA_OK;
 }
 
-template <int TI>
+template <int NI_>
 void launch_fwd32(const PairArgs &a, bool multi, bool shift, int grid, cudaStream_t st) {
     if (multi) {
-        if (shift) pair_fwd32<TI, true, true><<<grid, kPairThreads, 0, st>>>(a);
-        else pair_fwd32<TI, true, false><<<grid, kPairThreads, 0, st>>>(a);
+        if (shift) pair_fwd32<NI_, true, true><<<grid, kPairThreads, 0, st>>>(a);
+        else pair_fwd32<NI_, true, false><<<grid, kPairThreads, 0, st>>>(a);
     } else {
-        if (shift) pair_fwd32<TI, false, true><<<grid, kPairThreads, 0, st>>>(a);
-        else pair_fwd32<TI, false, false><<<grid, kPairThreads, 0, st>>>(a);
+        if (shift) pair_fwd32<NI_, false, true><<<grid, kPairThreads, 0, st>>>(a);
+        else pair_fwd32<NI_, false, false><<<grid, kPairThreads, 0, st>>>(a);
     }
 }
 
