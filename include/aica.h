@@ -174,6 +174,35 @@ aica_status aica_forces_backward(aica_mesh *mesh, const aica_lj *lj, aica_precis
                                  const void *grad_force, void *grad_pos, double *grad_eps,
                                  double *grad_sigma, void *stream);
 
+/* Stable counting sort of molecules by cell that allocates no device memory.
+ * The paper has no counterpart; this entry point exists for callers that
+ * cannot allocate device memory while they run: code recorded into a CUDA
+ * graph or a stream capture (cudaMalloc is not capturable), real-time loops
+ * that forbid allocation, and hosts whose device memory belongs to another
+ * allocator.  It runs the sort stage of aica_bin_molecules (histogram,
+ * prefix sum, scatter, per-cell order by original index) for cells the
+ * caller already knows, with its workspace in a fixed device array inside
+ * the library instead of allocated memory.
+ *   cell_of  device [n] int32: cell of each molecule in [0, n_cells), or -1
+ *            (the molecule is left out)
+ *   order    device [n] out: order[s] = original index of slot s for
+ *            s < cell_off[n_cells]; later entries are not written
+ *   cell_off device [n_cells+1] out: cell c holds slots cell_off[c] ..
+ *            cell_off[c+1]
+ * The results equal those of aica_bin_molecules for the same cells.
+ * Limits: n_cells <= 1048576 and n <= 2^30, else AICA_ERR_CAPACITY /
+ * AICA_ERR_INVALID_ARG before any device work.  The workspace is about 4 MiB
+ * of static device memory that every GPU loading this library holds until
+ * the process exits.  All calls share it and it keeps the last call's
+ * contents (each call clears what must start at zero), so calls that
+ * overlap on the GPU (different streams or threads without ordering) race:
+ * order them on one stream.  The first call on a device looks up the
+ * workspace's device address (cudaGetSymbolAddress); make that first call
+ * outside any stream capture.  Never calls cudaMalloc, cudaFree or an
+ * allocating library routine.  Asynchronous on `stream`. */
+aica_status aica_sort_by_cell_noalloc(const int32_t *cell_of, int64_t n, int64_t n_cells, int32_t *order,
+                                      int32_t *cell_off, void *stream);
+
 /* With deferred != 0, aica_bin_molecules and aica_forces do not synchronize
  * to check device-side error flags; errors are reported by
  * aica_check_status (which synchronizes `stream`). */

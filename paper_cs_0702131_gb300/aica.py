@@ -72,6 +72,8 @@ SIGNATURES = {
     "aica_set_kernel_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "aica_take_kernel_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                               ctypes.POINTER(ctypes.c_int64)]),
+    "aica_sort_by_cell_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
+                                                 ctypes.c_void_p, ctypes.c_void_p]),
     "aica_last_error": (ctypes.c_char_p, []),
     "aica_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -190,6 +192,15 @@ def aica_forces_backward(h, eps, sigma, prec, grad_force, grad_pos, grad_eps=Non
     lj = _lj(eps, sigma, False)
     _check(lib().aica_forces_backward(h, ctypes.byref(lj), int(prec), _ptr(grad_force), _ptr(grad_pos),
                                       _ptr(grad_eps), _ptr(grad_sigma), _stream()))
+
+
+def aica_sort_by_cell_noalloc(cell_of, n_cells, order, cell_off):
+    """Counting sort by cell with no device allocation (see include/aica.h)."""
+    n = cell_of.shape[0]
+    _dev(cell_of, torch.int32, (n,), "cell_of")
+    _dev(order, torch.int32, (n,), "order")
+    _dev(cell_off, torch.int32, (int(n_cells) + 1,), "cell_off")
+    _check(lib().aica_sort_by_cell_noalloc(_ptr(cell_of), n, int(n_cells), _ptr(order), _ptr(cell_off), _stream()))
 
 
 def aica_set_deferred_checks(h, deferred):

@@ -397,3 +397,58 @@ extern "C" aica_status aica_bin_molecules(aica_mesh *m, const double *pos, const
     }
     return AICA_OK;
 }
+
+// ------------------------------------------------------------ no allocation
+// Workspace of aica_sort_by_cell_noalloc: per-cell counters (reused as slot
+// fill counters after the prefix sum) and the prefix-sum tile totals.  A
+// file-scope device array: host code must not take its address directly (the
+// host-side name is not a device address); each device's address is looked
+// up once with cudaGetSymbolAddress.
+namespace {
+constexpr int64_t kNoAllocMaxCells = 1 << 20;
+constexpr int64_t kNoAllocWords = (kNoAllocMaxCells + 1) + (kNoAllocMaxCells + 1 + aica::kScanTile - 1) / aica::kScanTile + 8;
+constexpr int kNoAllocMaxDevices = 64;
+int *g_noalloc_dev[kNoAllocMaxDevices];   // device address of the workspace, per device
+}  // namespace
+
+static __device__ __align__(256) int g_noalloc_scratch[kNoAllocWords];
+
+extern "C" aica_status aica_sort_by_cell_noalloc(const int32_t *cell_of, int64_t n, int64_t n_cells, int32_t *order,
+                                                 int32_t *cell_off, void *stream) {
+    if (n < 0 || n > (int64_t(1) << 30) || n_cells < 1 || !cell_off || (n > 0 && (!cell_of || !order))) {
+        set_error("aica_sort_by_cell_noalloc: bad arguments (n = %lld, n_cells = %lld)", (long long)n,
+                  (long long)n_cells);
+        return AICA_ERR_INVALID_ARG;
+    }
+    if (n_cells > kNoAllocMaxCells) {
+        set_error("aica_sort_by_cell_noalloc: %lld cells exceed the fixed workspace (at most %lld)",
+                  (long long)n_cells, (long long)kNoAllocMaxCells);
+        return AICA_ERR_CAPACITY;
+    }
+    int dev = 0;
+    AICA_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) {
+        set_error("aica_sort_by_cell_noalloc: device %d beyond %d", dev, kNoAllocMaxDevices);
+        return AICA_ERR_INVALID_ARG;
+    }
+    if (!g_noalloc_dev[dev]) {    // once per device, with that device current
+        void *p = nullptr;
+        AICA_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_dev[dev] = static_cast<int *>(p);
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int C = (int)n_cells;
+    int *cnt = g_noalloc_dev[dev];
+    int *work = cnt + (kNoAllocMaxCells + 1);
+    AICA_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (C + 1), st));
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    if (n > 0) bin_count<<<nb, 256, 0, st>>>(cell_of, n, cnt);
+    exclusive_scan<int, int>(cnt, C, cell_off, work, st);
+    AICA_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (C + 1), st));
+    if (n > 0) {
+        bin_scatter<<<nb, 256, 0, st>>>(cell_of, n, cell_off, cnt, order);
+        bin_fixup<<<(C + 255) / 256, 256, 0, st>>>(cell_off, C, order);
+    }
+    AICA_CUDA(cudaGetLastError());
+    return AICA_OK;
+}
