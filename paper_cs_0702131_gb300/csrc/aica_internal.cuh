@@ -105,7 +105,7 @@ struct aica_mesh {
     double rc = 0, skin = 0;
     int64_t n_dil = 0, n_ref = 0, n_ref_ids = 0, n_ties = 0, n_work = 0;
     aica::DevBuf dil_off, dil_ids, ref_src, ref_n, ref_off, ref_ids;   // int32 (ref_n: 3 int32)
-    aica::DevBuf work_off, work, work_d32;   // [C+1] int32 (index of first DIL entry), WorkEntry, float4 shift
+    aica::DevBuf work_off, work;             // [C+1] int32 first entry of each cell; WorkEntry (partner, image)
     aica::DevBuf work_split;                 // [C] int32: first periodic-image entry of each cell
     aica::DevBuf proc_order;                 // [C] int32: cell processing order (spatially local)
 

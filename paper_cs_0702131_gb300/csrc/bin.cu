@@ -171,24 +171,62 @@ __global__ void __launch_bounds__(256) bin_locate_hint(BinArgs a) {
     if (miss) a.miss[1 + base + __popc(bal & ((1u << lane) - 1u))] = (int)k;
 }
 
-// Molecules that left their previous cell: its face neighbours, then the grid.
+// Molecules that left their previous cell: one warp per molecule, lanes test
+// the previous cell's face neighbours in parallel, then the cells of the
+// molecule's bucket.  Exact predicates make at most one cell hold the point.
 __global__ void __launch_bounds__(256) bin_locate_miss(BinArgs a) {
+    const int lane = threadIdx.x & 31;
     const int nm = a.miss[0];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nm; i += gridDim.x * blockDim.x) {
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nm; i += nw) {
         const int k = a.miss[1 + i];
         double p[3];
         bool ok;
         wrapped_position(a, k, p, ok);
         const int h = a.hint[k];
         int found = -1;
-        if (h >= 0)
-            for (int j = a.nbr_off[h]; j < a.nbr_off[h + 1] && found < 0; ++j) {
-                const int c = a.nbr[j];
-                if (cell_contains(a, c, local_to(a, p, c), p)) found = c;
+        if (h >= 0) {
+            const int j1 = a.nbr_off[h + 1];
+            for (int j0 = a.nbr_off[h]; j0 < j1; j0 += 32) {
+                const int j = j0 + lane;
+                int c = -1;
+                bool hit = false;
+                if (j < j1) {
+                    c = a.nbr[j];
+                    hit = cell_contains(a, c, local_to(a, p, c), p);
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, hit);
+                if (bal) {
+                    found = __shfl_sync(0xffffffffu, c, __ffs(bal) - 1);
+                    break;
+                }
             }
-        if (found < 0) found = grid_search(a, p, h);
-        a.cell_of[k] = found;
-        if (found < 0) atomicOr(a.flags, kFlagOutside);
+        }
+        if (found < 0) {
+            int ib[3];
+            for (int d = 0; d < 3; ++d)
+                ib[d] = min(max((int)floorf((float)(p[d] - a.glo[d]) * a.inv_gh_f[d]), 0), a.G[d] - 1);
+            const int b = (ib[0] * a.G[1] + ib[1]) * a.G[2] + ib[2];
+            const int i1 = a.bkt_off[b + 1];
+            for (int i0 = a.bkt_off[b]; i0 < i1; i0 += 32) {
+                const int ii = i0 + lane;
+                int c = -1;
+                bool hit = false;
+                if (ii < i1) {
+                    c = a.bkt_cells[ii];
+                    hit = c != h && cell_contains(a, c, local_to(a, p, c), p);
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, hit);
+                if (bal) {
+                    found = __shfl_sync(0xffffffffu, c, __ffs(bal) - 1);
+                    break;
+                }
+            }
+        }
+        if (lane == 0) {
+            a.cell_of[k] = found;
+            if (found < 0) atomicOr(a.flags, kFlagOutside);
+        }
     }
 }
 

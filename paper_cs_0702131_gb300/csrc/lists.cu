@@ -314,7 +314,6 @@ struct FillArgs {
     int *dil_ids, *ref_src, *ref_n, *ref_off, *ref_ids;
     int *work_off, *work_split;
     WorkEntry *work;
-    float4 *work_d32;
 };
 
 __global__ void lst_fill(FillArgs f) {
@@ -360,10 +359,6 @@ __global__ void lst_fill(FillArgs f) {
         // partner B seen from A: its molecules shifted by n = -n'
         int nx = -x, ny = -y, nz = -z;
         f.work[slot] = WorkEntry{B, pack_n(nx, ny, nz)};
-        double dx = (double)(f.orgk[3 * B] - f.orgk[3 * A]) * (1.0 / 1024.0) + nx * f.L[0];
-        double dy = (double)(f.orgk[3 * B + 1] - f.orgk[3 * A + 1]) * (1.0 / 1024.0) + ny * f.L[1];
-        double dz = (double)(f.orgk[3 * B + 2] - f.orgk[3 * A + 2]) * (1.0 / 1024.0) + nz * f.L[2];
-        f.work_d32[slot] = make_float4((float)dx, (float)dy, (float)dz, 0.f);
     }
 }
 
@@ -516,7 +511,6 @@ extern "C" aica_status aica_build_interaction_list(aica_mesh *m, double rc, doub
     CK(m->work_off.reserve(sizeof(int) * (C + 1)));
     CK(m->work_split.reserve(sizeof(int) * C));
     CK(m->work.reserve(sizeof(WorkEntry) * std::max<int64_t>(n_work, 1)));
-    CK(m->work_d32.reserve(sizeof(float4) * std::max<int64_t>(n_work, 1)));
     FillArgs f{};
     f.C = C;
     f.seg_off = a.seg_off;
@@ -535,7 +529,6 @@ extern "C" aica_status aica_build_interaction_list(aica_mesh *m, double rc, doub
     f.work_off = m->work_off.as<int>();
     f.work_split = m->work_split.as<int>();
     f.work = m->work.as<WorkEntry>();
-    f.work_d32 = m->work_d32.as<float4>();
     lst_fill<<<(C + 1 + 255) / 256, 256, 0, st>>>(f);
     m->launches += 1;
     CK(cudaGetLastError());

@@ -61,7 +61,8 @@ struct PairArgs {
     int C;
     const int *cell_off, *work_off;
     const WorkEntry *work;
-    const float4 *work_d32;
+    const int *orgk;             // cell origins in units of 2^-10
+    float Lhi[3], Llo[3];        // box lengths as float pairs (Lhi + Llo = L to ~1e-14)
     const float4 *xloc;
     const double *xs64;
     const float4 *sph;           // per-cell molecule bounding spheres (local frame)
@@ -140,6 +141,20 @@ __device__ void store_partials(double *part, int gwarp, const double (&dsum)[7],
 }
 
 // ------------------------------------------------------------------ FP32 path
+// Shift from cell I's frame to cell J's image n: (o_J - o_I) + n.L.  The
+// origin difference is a multiple of 2^-10 (exact in FP32); n.Lhi cancels
+// against it exactly for image pairs (Sterbenz), leaving one rounding for
+// the n.Llo term.
+__device__ __forceinline__ float3 cell_shift(const PairArgs &a, const int *oI, int J, int np) {
+    const int *oJ = a.orgk + 3 * J;
+    float3 d;
+    const float nx = (float)unpack_n(np, 0), ny = (float)unpack_n(np, 1), nz = (float)unpack_n(np, 2);
+    d.x = fmaf(nx, a.Lhi[0], (float)(oJ[0] - oI[0]) * (1.0f / 1024.0f)) + nx * a.Llo[0];
+    d.y = fmaf(ny, a.Lhi[1], (float)(oJ[1] - oI[1]) * (1.0f / 1024.0f)) + ny * a.Llo[1];
+    d.z = fmaf(nz, a.Lhi[2], (float)(oJ[2] - oI[2]) * (1.0f / 1024.0f)) + nz * a.Llo[2];
+    return d;
+}
+
 // Per-warp queue of partner molecules that survived culling: position in I's
 // frame (species bits in .w), binned index and image vector.
 constexpr int kQ = 64;
@@ -211,7 +226,8 @@ __device__ __forceinline__ unsigned eval_partner(const PairArgs &a, const float4
 // the warp queue, and evaluate them 32 at a time (lane = partner molecule).
 template <int NI_, bool MULTI, bool SHIFT>
 __device__ __forceinline__ void stream32(const PairArgs &a, const float4 *tab, IChunk<NI_> &c, Sums &sm, int e0,
-                                         int e1, float4 sI, float rcut, WarpQueue &q, int qn, int lane) {
+                                         int e1, WorkEntry we_next, const int *oI, float4 sI, float rcut,
+                                         WarpQueue &q, int qn, int lane) {
     const float cull_i = (rcut + sI.w) * (rcut + sI.w) * 1.00002f + 1e-5f;
     auto run = [&](int count) {
         bool valid = lane < count;
@@ -231,18 +247,19 @@ __device__ __forceinline__ void stream32(const PairArgs &a, const float4 *tab, I
         }
     };
     for (int eb = e0; eb < e1; eb += 32) {
-        int e = eb + lane;
+        const int e = eb + lane;
+        const WorkEntry we = we_next;            // loaded one batch ahead
+        if (eb + 32 + lane < e1) we_next = a.work[eb + 32 + lane];
         int js = 0, n = 0, np = 0;
-        float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
+        float3 d = make_float3(0.f, 0.f, 0.f);
         if (e < e1) {
-            WorkEntry we = a.work[e];
             js = a.cell_off[we.j];
             n = a.cell_off[we.j + 1] - js;
             np = we.n;
             if (n > 0) {
                 if (np != 0) sm.eval[2] += (unsigned)(n * c.ni);
                 else sm.eval[1] += (unsigned)(n * c.ni);
-                d = a.work_d32[e];
+                d = cell_shift(a, oI, we.j, np);
                 float4 sJ = a.sph[we.j];
                 float dx = sJ.x + d.x - sI.x, dy = sJ.y + d.y - sI.y, dz = sJ.z + d.z - sI.z;
                 float R = rcut + sI.w + sJ.w;
@@ -330,6 +347,8 @@ __global__ void __launch_bounds__(kPairThreads, NI_ <= 4 ? 3 : 2) pair_fwd32(Pai
         if (nI == 0) continue;
         const int e0 = a.work_off[I], e1 = a.work_off[I + 1];
         const float4 sph = a.sph[I];
+        const WorkEntry first = e0 + lane < e1 ? a.work[e0 + lane] : WorkEntry{0, 0};
+        const int *oI = a.orgk + 3 * I;
         for (int i0 = 0; i0 < nI; i0 += NI_) {
             IChunk<NI_> c;
             c.k0 = sI + i0;
@@ -353,10 +372,10 @@ __global__ void __launch_bounds__(kPairThreads, NI_ <= 4 ? 3 : 2) pair_fwd32(Pai
                 __syncwarp();
                 if (qn >= 32) {          // only for cells of more than 33 molecules
                     qn = 0;
-                    stream32<NI_, MULTI, SHIFT>(a, tab, c, sm, 0, 0, sph, rcut, q, 32, lane);
+                    stream32<NI_, MULTI, SHIFT>(a, tab, c, sm, 0, 0, first, oI, sph, rcut, q, 32, lane);
                 }
             }
-            stream32<NI_, MULTI, SHIFT>(a, tab, c, sm, e0, e1, sph, rcut, q, qn, lane);
+            stream32<NI_, MULTI, SHIFT>(a, tab, c, sm, e0, e1, first, oI, sph, rcut, q, qn, lane);
             // forces on the chunk's molecules: warp sums, one vector atomic each, k-side virial
 #pragma unroll
             for (int t = 0; t < NI_; ++t) {
@@ -526,7 +545,8 @@ __global__ void __launch_bounds__(kPairThreads) pair_fwd64(PairArgs a) {
                     if (n > 0) {
                         if (np != 0) eval[2] += (unsigned)(n * ni);
                         else eval[1] += (unsigned)(n * ni);
-                        d = a.work_d32[e];
+                        const float3 s3 = cell_shift(a, a.orgk + 3 * I, we.j, np);
+                        d = make_float4(s3.x, s3.y, s3.z, 0.f);
                         float4 sJ = a.sph[we.j];
                         float dx = sJ.x + d.x - sI4.x, dy = sJ.y + d.y - sI4.y, dz = sJ.z + d.z - sI4.z;
                         float R = rcut + sI4.w + sJ.w;
@@ -768,7 +788,8 @@ __global__ void __launch_bounds__(kPairThreads) pair_bwd(BwdArgs b) {
                 WorkEntry we = a.work[e];
                 J = we.j;
                 np = we.n;
-                d = a.work_d32[e];
+                const float3 s3 = cell_shift(a, a.orgk + 3 * I, J, np);
+                d = make_float4(s3.x, s3.y, s3.z, 0.f);
             }
             const int sJ = a.cell_off[J], nJ = a.cell_off[J + 1] - sJ;
             const int npairs = nI * nJ;
@@ -876,7 +897,12 @@ void fill_common(aica_mesh *m, PairArgs &a) {
     a.cell_off = m->cell_off.as<int>();
     a.work_off = m->work_off.as<int>();
     a.work = m->work.as<WorkEntry>();
-    a.work_d32 = m->work_d32.as<float4>();
+    a.orgk = m->orgk.as<int>();
+    for (int d = 0; d < 3; ++d) {
+        double L = m->box.periodic[d] ? m->box.L[d] : 0.0;
+        a.Lhi[d] = (float)L;
+        a.Llo[d] = (float)(L - (double)a.Lhi[d]);
+    }
     a.xloc = m->xloc.as<float4>();
     a.xs64 = m->xs64.as<double>();
     a.sph = m->sph.as<float4>();
