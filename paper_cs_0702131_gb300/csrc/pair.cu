@@ -74,6 +74,7 @@ struct PairArgs {
     const void *vs;              // backward: grad_force in binned order (float4 / double4)
     double *acc;                 // [0..6] U, W; [8..15] counters (as unsigned long long); [16..] grads
     double *part;                // per-warp partial sums [warps][kParts]
+    unsigned *next_cell;         // FP32 kernel: next unclaimed cell (zero at launch)
     SpeciesTab tab;
 };
 
@@ -181,233 +182,275 @@ __device__ __forceinline__ void lj32(const float4 *tab, float4 t0, int spi, int 
     if (SHIFT) u -= t.w;
 }
 
-// The molecules of I's current chunk (registers) and their accumulated forces.
+// FP32 kernel: persistent grid of 4-warp blocks; warps claim cells from a
+// global counter.  Per warp, shared memory holds the partner ring, the live
+// schedule entries of the current batch and the chunk's molecules.
+constexpr int kThreads32 = 128;
+constexpr int kWarps32 = kThreads32 / 32;
+constexpr int kRing = 64;            // partner ring (power of two, >= 2 x 32)
+constexpr int kGrab = 2;             // cells claimed per counter update
+
 template <int NI_>
-struct IChunk {
-    float4 x[NI_];
-    R3<float> f[NI_];
-    int k0, ni;
+struct Warp32 {
+    float4 qx[kRing];    // queued partners: position in I's frame (.w species bits)
+    int2 ql[kRing];      // queued partners: binned index, image code (kSameCell: same cell)
+    float4 ed[32];       // live entries of the batch, compacted: shift (xyz), image code (.w bits)
+    int eb[32];          // ... and binned index minus candidate position
+    float4 xi[NI_];      // molecules of the current chunk
+    unsigned cnt[5];     // evaluated same / DIL / image, pair tests, sphere tests
 };
 
-// One lane's partner molecule xj against the chunk: every pair with
+// One lane's partner xj against the chunk's ni molecules: every pair with
 // r^2 < rc^2 (FP32, with the FP64 re-decision near the cut) adds f to the
-// chunk's molecule and -f to the partner's reaction.  Returns the number of
-// pairs within rc.  Only chunk molecules k < lmax_k take part.
+// chunk molecule's sum and -f to the partner's.  Only chunk molecules of
+// binned index below lmax_k take part.  Returns the pairs within rc.
 template <int NI_, bool MULTI, bool SHIFT>
-__device__ __forceinline__ unsigned eval_partner(const PairArgs &a, const float4 *tab, IChunk<NI_> &c, float4 xj,
-                                                 int l, int np, int lmax_k, R3<float> &fj, float &u_acc) {
+__device__ __forceinline__ unsigned eval_partner(const PairArgs &a, const float4 *tab, const float4 *xi, int ni,
+                                                 int k0, float4 xj, int l, int np, int lmax_k, float (&fi)[3 * NI_],
+                                                 R3<float> &fj, float &u_acc) {
     unsigned nin = 0;
     const float4 t0 = tab[0];
 #pragma unroll
     for (int t = 0; t < NI_; ++t) {
-        if (t < c.ni) {
-            float rx = c.x[t].x - xj.x, ry = c.x[t].y - xj.y, rz = c.x[t].z - xj.z;
+        if (t < ni) {
+            const float4 x = xi[t];
+            float rx = x.x - xj.x, ry = x.y - xj.y, rz = x.z - xj.z;
             float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
-            bool ok = c.k0 + t < lmax_k;
+            bool ok = k0 + t < lmax_k;
             bool in = ok && r2 < a.rc2_lo;
             bool band = ok && r2 >= a.rc2_lo && r2 < a.rc2_hi;
             if (__any_sync(0xffffffffu, band))
-                if (band) in = band_in(a, c.k0 + t, l, np);
+                if (band) in = band_in(a, k0 + t, l, np);
             float fs, u;
-            lj32<MULTI, SHIFT>(tab, t0, __float_as_int(c.x[t].w), __float_as_int(xj.w), r2, fs, u);
+            lj32<MULTI, SHIFT>(tab, t0, __float_as_int(x.w), __float_as_int(xj.w), r2, fs, u);
             fs = in ? fs : 0.f;
             u_acc += in ? u : 0.f;
             nin += in;
             float fx = fs * rx, fy = fs * ry, fz = fs * rz;
-            c.f[t].x += fx; c.f[t].y += fy; c.f[t].z += fz;
+            fi[3 * t] += fx; fi[3 * t + 1] += fy; fi[3 * t + 2] += fz;
             fj.x -= fx; fj.y -= fy; fj.z -= fz;
         }
     }
     return nin;
 }
 
-// Stream the molecules of the partner cells of entries [e0, e1) against the
-// chunk: cull cells and molecules against I's sphere, compact survivors into
-// the warp queue, and evaluate them 32 at a time (lane = partner molecule).
-template <int NI_, bool MULTI, bool SHIFT>
-__device__ __forceinline__ void stream32(const PairArgs &a, const float4 *tab, IChunk<NI_> &c, Sums &sm, int e0,
-                                         int e1, WorkEntry we_next, const int *oI, float4 sI, float rcut,
-                                         WarpQueue &q, int qn, int lane) {
-    const float cull_i = (rcut + sI.w) * (rcut + sI.w) * 1.00002f + 1e-5f;
-    auto run = [&](int count) {
-        bool valid = lane < count;
-        float4 xj = valid ? q.x[lane] : make_float4(1e18f, 1e18f, 1e18f, 0.f);
-        int l = valid ? q.l[lane] : 0, np = valid ? q.np[lane] : 0;
-        if (lane == 0) sm.tests += (unsigned)(count * c.ni);
-        R3<float> fj = {0.f, 0.f, 0.f};
-        const bool same = np == kSameCell;
-        unsigned nin = eval_partner<NI_, MULTI, SHIFT>(a, tab, c, xj, l, same ? 0 : np, same ? l : 0x7fffffff, fj,
-                                                       sm.v[0]);
-        if (same) sm.within[0] += nin;
-        else if (np != 0) sm.within[2] += nin;
-        else sm.within[1] += nin;
-        if (nin) {
-            atomicAdd((float4 *)a.facc + l, make_float4(fj.x, fj.y, fj.z, 0.f));
-            sm.outer(xj.x, xj.y, xj.z, fj.x, fj.y, fj.z);
-        }
-    };
-    for (int eb = e0; eb < e1; eb += 32) {
-        const int e = eb + lane;
-        const WorkEntry we = we_next;            // loaded one batch ahead
-        if (eb + 32 + lane < e1) we_next = a.work[eb + 32 + lane];
-        int js = 0, n = 0, np = 0;
-        float3 d = make_float3(0.f, 0.f, 0.f);
-        if (e < e1) {
-            js = a.cell_off[we.j];
-            n = a.cell_off[we.j + 1] - js;
-            np = we.n;
-            if (n > 0) {
-                if (np != 0) sm.eval[2] += (unsigned)(n * c.ni);
-                else sm.eval[1] += (unsigned)(n * c.ni);
-                d = cell_shift(a, oI, we.j, np);
-                float4 sJ = a.sph[we.j];
-                float dx = sJ.x + d.x - sI.x, dy = sJ.y + d.y - sI.y, dz = sJ.z + d.z - sI.z;
-                float R = rcut + sI.w + sJ.w;
-                sm.culls++;
-                if (dx * dx + dy * dy + dz * dz > R * R * 1.00002f + 1e-5f) n = 0;
-            }
-        }
-        int inc = n;
+// Sum v[0..3 NI_) over the warp by recursive halving: on return the lanes
+// t * (32 / NI_) .. (t + 1) * (32 / NI_) - 1 hold the totals of v[3t..3t+3)
+// in v[0..3).
+template <int N>
+__device__ __forceinline__ void halve(float *v, int lane, int o) {
+    const bool up = lane & o;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += y;
-        }
-        const int total = __shfl_sync(0xffffffffu, inc, 31);
-        const int exc = inc - n;
-        for (int p0 = 0; p0 < total; p0 += 32) {
-            int p = p0 + lane;
-            int o = 0;
-#pragma unroll
-            for (int step = 16; step > 0; step >>= 1)
-                if (__shfl_sync(0xffffffffu, inc, o + step - 1) <= p) o += step;
-            int jsl = __shfl_sync(0xffffffffu, js, o);
-            int exl = __shfl_sync(0xffffffffu, exc, o);
-            float dx = __shfl_sync(0xffffffffu, d.x, o);
-            float dy = __shfl_sync(0xffffffffu, d.y, o);
-            float dz = __shfl_sync(0xffffffffu, d.z, o);
-            int npl = __shfl_sync(0xffffffffu, np, o);
-            bool alive = false;
-            int l = jsl + (p - exl);
-            float4 xj;
-            if (p < total) {
-                float4 xl = a.xloc[l];
-                xj = make_float4(xl.x + dx, xl.y + dy, xl.z + dz, xl.w);
-                float cx = xj.x - sI.x, cy = xj.y - sI.y, cz = xj.z - sI.z;
-                alive = cx * cx + cy * cy + cz * cz <= cull_i;
-                sm.culls++;
-            }
-            unsigned bal = __ballot_sync(0xffffffffu, alive);
-            if (alive) {
-                int s = qn + __popc(bal & ((1u << lane) - 1u));
-                q.x[s] = xj;
-                q.l[s] = l;
-                q.np[s] = npl;
-            }
-            qn += __popc(bal);
-            __syncwarp();
-            if (qn >= 32) {
-                run(32);
-                __syncwarp();
-                qn -= 32;
-                if (lane < qn) {
-                    q.x[lane] = q.x[32 + lane];
-                    q.l[lane] = q.l[32 + lane];
-                    q.np[lane] = q.np[32 + lane];
-                }
-                __syncwarp();
-            }
-        }
-    }
-    if (qn > 0) {
-        run(qn);
-        __syncwarp();
+    for (int i = 0; i < N / 2; ++i) {
+        const float send = up ? v[i] : v[i + N / 2];
+        const float keep = up ? v[i + N / 2] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
     }
 }
+template <int NI_>
+__device__ __forceinline__ void chunk_reduce(float (&v)[3 * NI_], int lane) {
+    if (NI_ >= 2) halve<3 * NI_>(v, lane, 16);
+    if (NI_ >= 4) halve<3 * NI_ / 2>(v, lane, 8);
+    if (NI_ >= 8) halve<3 * NI_ / 4>(v, lane, 4);
+#pragma unroll
+    for (int o = 16 / NI_; o > 0; o >>= 1)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+}
 
-template <int NI_, bool MULTI, bool SHIFT>
-__global__ void __launch_bounds__(kPairThreads, NI_ <= 4 ? 3 : 2) pair_fwd32(PairArgs a) {
+__device__ __forceinline__ void outer7(float (&v)[7], float ax, float ay, float az, float bx, float by, float bz) {
+    v[1] = fmaf(ax, bx, v[1]);
+    v[2] = fmaf(ay, by, v[2]);
+    v[3] = fmaf(az, bz, v[3]);
+    v[4] = fmaf(ax, by, v[4]);
+    v[5] = fmaf(ax, bz, v[5]);
+    v[6] = fmaf(ay, bz, v[6]);
+}
+
+template <int NI_, bool MULTI, bool SHIFT, int MINB>
+__global__ void __launch_bounds__(kThreads32, MINB) pair_fwd32(PairArgs a) {
     __shared__ float4 tab[kMaxSpecies * kMaxSpecies];
-    __shared__ WarpQueue queues[kWarps];
-    __shared__ double dsums[kWarps][8];
+    __shared__ Warp32<NI_> wsh[kWarps32];
+    __shared__ double dsums[kWarps32][8];
     for (int i = threadIdx.x; i < kMaxSpecies * kMaxSpecies; i += blockDim.x) tab[i] = a.tab.f[i];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    Warp32<NI_> &w = wsh[wib];
     if (lane < 8) dsums[wib][lane] = 0.0;
+    if (lane < 5) w.cnt[lane] = 0;
     __syncthreads();
-    const int gwarp = blockIdx.x * kWarps + wib;
-    const int nwarps = gridDim.x * kWarps;
-    WarpQueue &q = queues[wib];
-    double *dsum = dsums[wib];
+    const unsigned FULL = 0xffffffffu, lt = (1u << lane) - 1u, le = FULL >> (31 - lane);
+    const float4 far = make_float4(1e18f, 1e18f, 1e18f, 0.f);
     const float rcut = sqrtf(a.rc2_hi);
-    Sums sm;
-    sm.zero();
+    double *dsum = dsums[wib];
+    float v[7];
+#pragma unroll
+    for (int i = 0; i < 7; ++i) v[i] = 0.f;
+    unsigned within[3] = {0, 0, 0};
     int ncell = 0;
-    for (int I = gwarp; I < a.C; I += nwarps) {
-        const int sI = a.cell_off[I], nI = a.cell_off[I + 1] - sI;
-        if (nI == 0) continue;
-        const int e0 = a.work_off[I], e1 = a.work_off[I + 1];
-        const float4 sph = a.sph[I];
-        const WorkEntry first = e0 + lane < e1 ? a.work[e0 + lane] : WorkEntry{0, 0};
-        const int *oI = a.orgk + 3 * I;
-        for (int i0 = 0; i0 < nI; i0 += NI_) {
-            IChunk<NI_> c;
-            c.k0 = sI + i0;
-            c.ni = min(NI_, nI - i0);
-#pragma unroll
-            for (int t = 0; t < NI_; ++t) {
-                c.x[t] = t < c.ni ? a.xloc[c.k0 + t] : make_float4(1e18f, 1e18f, 1e18f, 0.f);
-                c.f[t] = {0.f, 0.f, 0.f};
-            }
-            // same-cell pairs k' > k (sorted order): I's later molecules enter
-            // the queue first, marked so they pair only with lower indices
-            int qn = 0;
-            for (int lb = i0 + 1; lb < nI; lb += 32) {
-                const int li = lb + lane;
-                if (li < nI) {
-                    q.x[qn + lane] = a.xloc[sI + li];
-                    q.l[qn + lane] = sI + li;
-                    q.np[qn + lane] = kSameCell;
-                }
-                qn += min(32, nI - lb);
+    int I0 = lane == 0 ? (int)atomicAdd(a.next_cell, (unsigned)kGrab) : 0;
+    I0 = __shfl_sync(FULL, I0, 0);
+    while (I0 < a.C) {
+        const int Inext = lane == 0 ? (int)atomicAdd(a.next_cell, (unsigned)kGrab) : 0;
+        const int Iend = min(I0 + kGrab, a.C);
+        for (int I = I0; I < Iend; ++I) {
+            const int s0 = a.cell_off[I], nI = a.cell_off[I + 1] - s0;
+            if (nI == 0) continue;
+            const int e0 = a.work_off[I], e1 = a.work_off[I + 1];
+            const float4 sI = a.sph[I];
+            const int *oI = a.orgk + 3 * I;
+            const float cull_i = (rcut + sI.w) * (rcut + sI.w) * 1.00002f + 1e-5f;
+            for (int i0 = 0; i0 < nI; i0 += NI_) {
+                const int ni = min(NI_, nI - i0), k0 = s0 + i0;
                 __syncwarp();
-                if (qn >= 32) {          // only for cells of more than 33 molecules
-                    qn = 0;
-                    stream32<NI_, MULTI, SHIFT>(a, tab, c, sm, 0, 0, first, oI, sph, rcut, q, 32, lane);
-                }
-            }
-            stream32<NI_, MULTI, SHIFT>(a, tab, c, sm, e0, e1, first, oI, sph, rcut, q, qn, lane);
-            // forces on the chunk's molecules: warp sums, one vector atomic each, k-side virial
+                if (lane < ni) w.xi[lane] = a.xloc[k0 + lane];
+                float fi[3 * NI_];
 #pragma unroll
-            for (int t = 0; t < NI_; ++t) {
-                if (t < c.ni) {
-                    float x = warp_sum(c.f[t].x), y = warp_sum(c.f[t].y), z = warp_sum(c.f[t].z);
-                    if (lane == t) {
-                        atomicAdd((float4 *)a.facc + c.k0 + t, make_float4(x, y, z, 0.f));
-                        sm.outer(c.x[t].x, c.x[t].y, c.x[t].z, x, y, z);
+                for (int i = 0; i < 3 * NI_; ++i) fi[i] = 0.f;
+                int head = 0, qn = 0;
+                __syncwarp();
+                // evaluate the `count` partners at the ring's head (lane = partner)
+                auto run = [&](int count) {
+                    const int s = (head + lane) & (kRing - 1);
+                    const bool valid = lane < count;
+                    const float4 xj = valid ? w.qx[s] : far;
+                    const int2 q = valid ? w.ql[s] : make_int2(0, 0);
+                    if (lane == 0) w.cnt[3] += (unsigned)(count * ni);
+                    R3<float> fj = {0.f, 0.f, 0.f};
+                    const bool same = q.y == kSameCell;
+                    const unsigned nin = eval_partner<NI_, MULTI, SHIFT>(a, tab, w.xi, ni, k0, xj, q.x, same ? 0 : q.y,
+                                                                         same ? q.x : 0x7fffffff, fi, fj, v[0]);
+                    if (same) within[0] += nin;
+                    else if (q.y != 0) within[2] += nin;
+                    else within[1] += nin;
+                    if (nin) {
+                        atomicAdd((float4 *)a.facc + q.x, make_float4(fj.x, fj.y, fj.z, 0.f));
+                        outer7(v, xj.x, xj.y, xj.z, fj.x, fj.y, fj.z);
                     }
+                    head = (head + count) & (kRing - 1);
+                    __syncwarp();
+                };
+                // append the live lanes' partners to the ring; evaluate each full 32
+                auto push = [&](bool alive, float4 xj, int l, int np) {
+                    const unsigned bal = __ballot_sync(FULL, alive);
+                    if (alive) {
+                        const int s = (head + qn + __popc(bal & lt)) & (kRing - 1);
+                        w.qx[s] = xj;
+                        w.ql[s] = make_int2(l, np);
+                    }
+                    qn += __popc(bal);
+                    __syncwarp();
+                    if (qn >= 32) {
+                        run(32);
+                        qn -= 32;
+                    }
+                };
+                // same-cell partners (k' > k, §2.3): I's molecules after the chunk's first
+                for (int lb = i0 + 1; lb < nI; lb += 32) {
+                    const int li = lb + lane;
+                    const bool alive = li < nI;
+                    push(alive, alive ? a.xloc[s0 + li] : far, s0 + li, kSameCell);
+                }
+                // schedule entries, 32 per batch
+                WorkEntry we = e0 + lane < e1 ? a.work[e0 + lane] : WorkEntry{0, 0};
+                for (int eb = e0; eb < e1; eb += 32) {
+                    const WorkEntry cur = we;
+                    const bool has = eb + lane < e1;
+                    if (eb + 32 + lane < e1) we = a.work[eb + 32 + lane];
+                    int js = 0, n = 0, nall = 0;
+                    float3 d = make_float3(0.f, 0.f, 0.f);
+                    if (has) {
+                        js = a.cell_off[cur.j];
+                        nall = n = a.cell_off[cur.j + 1] - js;
+                        if (n > 0) {
+                            d = cell_shift(a, oI, cur.j, cur.n);
+                            const float4 sJ = a.sph[cur.j];
+                            const float dx = sJ.x + d.x - sI.x, dy = sJ.y + d.y - sI.y, dz = sJ.z + d.z - sI.z;
+                            const float R = rcut + sI.w + sJ.w;
+                            if (dx * dx + dy * dy + dz * dz > R * R * 1.00002f + 1e-5f) n = 0;
+                        }
+                    }
+                    const unsigned ev_d = __reduce_add_sync(FULL, cur.n == 0 ? (unsigned)(nall * ni) : 0u);
+                    const unsigned ev_r = __reduce_add_sync(FULL, cur.n != 0 ? (unsigned)(nall * ni) : 0u);
+                    const unsigned ncull = __popc(__ballot_sync(FULL, nall > 0));
+                    int inc = n;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int y = __shfl_up_sync(FULL, inc, o);
+                        if (lane >= o) inc += y;
+                    }
+                    const int total = __shfl_sync(FULL, inc, 31);
+                    const bool live = n > 0;
+                    const unsigned lbal = __ballot_sync(FULL, live);
+                    if (live) {
+                        const int s = __popc(lbal & lt);
+                        w.ed[s] = make_float4(d.x, d.y, d.z, __int_as_float(cur.n));
+                        w.eb[s] = js - (inc - n);
+                    }
+                    if (lane == 0) {
+                        w.cnt[1] += ev_d;
+                        w.cnt[2] += ev_r;
+                        w.cnt[4] += ncull + (unsigned)total;
+                    }
+                    __syncwarp();
+                    for (int p0 = 0; p0 < total; p0 += 32) {
+                        // entry holding candidate p = p0 + lane: the live entries ending at or before p
+                        const int b = inc - p0;
+                        const int base = __popc(__ballot_sync(FULL, live && b <= 0));
+                        const unsigned M = __reduce_or_sync(FULL, (live && b > 0 && b < 32) ? (1u << b) : 0u);
+                        const int p = p0 + lane;
+                        bool alive = false;
+                        float4 xj = far;
+                        int l = 0, npl = 0;
+                        if (p < total) {
+                            const int o = base + __popc(M & le);
+                            const float4 e = w.ed[o];
+                            l = p + w.eb[o];
+                            npl = __float_as_int(e.w);
+                            const float4 xl = a.xloc[l];
+                            xj = make_float4(xl.x + e.x, xl.y + e.y, xl.z + e.z, xl.w);
+                            const float cx = xj.x - sI.x, cy = xj.y - sI.y, cz = xj.z - sI.z;
+                            alive = cx * cx + cy * cy + cz * cz <= cull_i;
+                        }
+                        push(alive, xj, l, npl);
+                    }
+                    __syncwarp();
+                }
+                if (qn > 0) run(qn);
+                // forces on the chunk's molecules: transposed warp sum, one vector atomic each, k-side virial
+                chunk_reduce<NI_>(fi, lane);
+                const int t = lane / (32 / NI_);
+                if ((lane & (32 / NI_ - 1)) == 0 && t < ni) {
+                    atomicAdd((float4 *)a.facc + k0 + t, make_float4(fi[0], fi[1], fi[2], 0.f));
+                    const float4 x = w.xi[t];
+                    outer7(v, x.x, x.y, x.z, fi[0], fi[1], fi[2]);
+                }
+            }
+            if (lane == 0) w.cnt[0] += (unsigned)(nI * (nI - 1) / 2);
+            if (++ncell == 4) {          // flush the FP32 running sums to FP64
+                ncell = 0;
+#pragma unroll
+                for (int i = 0; i < 7; ++i) {
+                    const float s = warp_sum(v[i]);
+                    if (lane == 0) dsum[i] += (double)s;
+                    v[i] = 0.f;
                 }
             }
         }
-        if (lane == 0) sm.eval[0] += (unsigned)(nI * (nI - 1) / 2);
-        if (++ncell == 4) {          // flush the FP32 running sums to FP64
-            ncell = 0;
-#pragma unroll
-            for (int i = 0; i < 7; ++i) {
-                float s = warp_sum(sm.v[i]);
-                if (lane == 0) dsum[i] += (double)s;
-                sm.v[i] = 0.f;
-            }
-        }
+        I0 = __shfl_sync(FULL, Inext, 0);
     }
     double fin[7];
 #pragma unroll
     for (int i = 0; i < 7; ++i) {
-        float s = warp_sum(sm.v[i]);
+        const float s = warp_sum(v[i]);
         fin[i] = dsum[i] + (double)s;
     }
-    unsigned cv[8] = {sm.eval[0], sm.eval[1], sm.eval[2], sm.within[0], sm.within[1], sm.within[2], sm.tests,
-                      sm.culls};
-    store_partials<float>(a.part, gwarp, fin, cv, lane);
+    __syncwarp();
+    unsigned cv[8] = {w.cnt[0], w.cnt[1], w.cnt[2], within[0], within[1], within[2], w.cnt[3], w.cnt[4]};
+    for (int i = 0; i < 3; ++i) cv[i] = __shfl_sync(FULL, cv[i], 0);
+    cv[6] = __shfl_sync(FULL, cv[6], 0);
+    cv[7] = __shfl_sync(FULL, cv[7], 0);
+    if (lane != 0) cv[0] = cv[1] = cv[2] = cv[6] = cv[7] = 0;
+    store_partials<float>(a.part, blockIdx.x * kWarps32 + wib, fin, cv, lane);
 }
 
 // ------------------------------------------------------------------ FP64 path
@@ -926,15 +969,34 @@ aica_status check_flags(aica_mesh *m, cudaStream_t st) {
     return AICA_OK;
 }
 
-template <int NI_>
-void launch_fwd32(const PairArgs &a, bool multi, bool shift, int grid, cudaStream_t st) {
-    if (multi) {
-        if (shift) pair_fwd32<NI_, true, true><<<grid, kPairThreads, 0, st>>>(a);
-        else pair_fwd32<NI_, true, false><<<grid, kPairThreads, 0, st>>>(a);
-    } else {
-        if (shift) pair_fwd32<NI_, false, true><<<grid, kPairThreads, 0, st>>>(a);
-        else pair_fwd32<NI_, false, false><<<grid, kPairThreads, 0, st>>>(a);
+// Blocks of the persistent FP32 kernel: every SM filled to its occupancy.
+template <int NI_, bool MULTI, bool SHIFT, int MINB>
+int fwd32_grid() {
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    if (!cache[dev]) {
+        int sms = 0, per = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pair_fwd32<NI_, MULTI, SHIFT, MINB>, kThreads32, 0);
+        cache[dev] = std::max(1, sms * std::max(1, per));
     }
+    return cache[dev];
+}
+
+template <int NI_, bool MULTI, bool SHIFT>
+int launch_fwd32_t(const PairArgs &a, cudaStream_t st) {
+    constexpr int MINB = NI_ <= 4 ? 7 : 5;
+    const int grid = std::min(fwd32_grid<NI_, MULTI, SHIFT, MINB>(), std::max(1, (a.C + kWarps32 - 1) / kWarps32));
+    pair_fwd32<NI_, MULTI, SHIFT, MINB><<<grid, kThreads32, 0, st>>>(a);
+    return grid * kWarps32;
+}
+
+// Launch the FP32 kernel; returns the number of warps (partial-sum rows).
+template <int NI_>
+int launch_fwd32(const PairArgs &a, bool multi, bool shift, cudaStream_t st) {
+    if (multi) return shift ? launch_fwd32_t<NI_, true, true>(a, st) : launch_fwd32_t<NI_, true, false>(a, st);
+    return shift ? launch_fwd32_t<NI_, false, true>(a, st) : launch_fwd32_t<NI_, false, false>(a, st);
 }
 
 }  // namespace
@@ -952,20 +1014,27 @@ extern "C" aica_status aica_forces(aica_mesh *m, const aica_lj *lj, aica_precisi
     aica_status s = fill_params(m, lj, kMaxSpecies, a);
     if (s != AICA_OK) return s;
     const int grid = pair_grid((int)m->n_cells);
-    AICA_CUDA(m->part.reserve(sizeof(double) * kParts * grid * kWarps));
+    int dev = 0, sms = 0;
+    AICA_CUDA(cudaGetDevice(&dev));
+    AICA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    // rows: FP64 grid, or the persistent FP32 grid (at most 16 blocks of 4 warps per SM)
+    const int rows_max = std::max(grid * kWarps, sms * 16 * kWarps32);
+    AICA_CUDA(m->part.reserve(sizeof(double) * kParts * rows_max));
     fill_common(m, a);
+    a.next_cell = (unsigned *)(m->acc.as<double>() + 24);
     m->launches = 0;
     const int64_t n = m->n_mol;
     const bool f64 = prec == AICA_FP64;
     if (n > 0) AICA_CUDA(cudaMemsetAsync(m->facc.p, 0, (f64 ? 4 * sizeof(double) : sizeof(float4)) * n, st));
-    AICA_CUDA(cudaMemsetAsync(m->acc.p, 0, 16 * sizeof(double), st));
+    AICA_CUDA(cudaMemsetAsync(m->acc.p, 0, 32 * sizeof(double), st));
     const bool multi = a.S > 1, shift = lj->shift != 0;
     cudaEvent_t tstop;
     AICA_CUDA(timing_begin(m, st, &tstop));
+    int rows = grid * kWarps;
     if (!f64) {
         // i-chunk width: 4 for cells of a few molecules (tetrahedra), 8 otherwise
-        if ((double)n < 5.0 * (double)a.C) launch_fwd32<4>(a, multi, shift, grid, st);
-        else launch_fwd32<8>(a, multi, shift, grid, st);
+        if ((double)n < 5.0 * (double)a.C) rows = launch_fwd32<4>(a, multi, shift, st);
+        else rows = launch_fwd32<8>(a, multi, shift, st);
     } else {
         if (multi) {
             if (shift) pair_fwd64<true, true><<<grid, kPairThreads, 0, st>>>(a);
@@ -976,7 +1045,7 @@ extern "C" aica_status aica_forces(aica_mesh *m, const aica_lj *lj, aica_precisi
         }
     }
     AICA_CUDA(timing_end(tstop, st));
-    finalize_partials<<<(grid * kWarps + 255) / 256, 256, 0, st>>>(a.part, grid * kWarps, a.acc);
+    finalize_partials<<<(rows + 255) / 256, 256, 0, st>>>(a.part, rows, a.acc);
     m->launches = 2;
     if (n > 0) {
         if (f64) unsort_forces<double><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m->inv.as<int>(), n, m->facc.p, (double *)force_out, 1);
