@@ -200,35 +200,61 @@ struct Warp32 {
     unsigned cnt[5];     // evaluated same / DIL / image, pair tests, sphere tests
 };
 
+// One pair's force and energy (FP32 body, branch-free): f is added to fi3
+// and subtracted from fj when `in`, u to u_acc.
+template <bool MULTI, bool SHIFT>
+__device__ __forceinline__ void pair32(const float4 *tab, float4 t0, int spi, int spj, float rx, float ry, float rz,
+                                       float r2, bool in, float *fi3, R3<float> &fj, float &u_acc) {
+    float fs, u;
+    lj32<MULTI, SHIFT>(tab, t0, spi, spj, r2, fs, u);
+    fs = in ? fs : 0.f;
+    u_acc += in ? u : 0.f;
+    fi3[0] = fmaf(fs, rx, fi3[0]);
+    fi3[1] = fmaf(fs, ry, fi3[1]);
+    fi3[2] = fmaf(fs, rz, fi3[2]);
+    fj.x = fmaf(-fs, rx, fj.x);
+    fj.y = fmaf(-fs, ry, fj.y);
+    fj.z = fmaf(-fs, rz, fj.z);
+}
+
 // One lane's partner xj against the chunk's ni molecules: every pair with
-// r^2 < rc^2 (FP32, with the FP64 re-decision near the cut) adds f to the
-// chunk molecule's sum and -f to the partner's.  Only chunk molecules of
-// binned index below lmax_k take part.  Returns the pairs within rc.
-template <int NI_, bool MULTI, bool SHIFT>
+// r^2 < rc^2 adds f to the chunk molecule's sum and -f to the partner's.
+// FP32 r^2 within 1e-5 rc^2 of the cut-off is re-decided in FP64 after the
+// pass (one vote per batch).  With SAME, only chunk molecules of binned
+// index below lmax_k take part.  Returns the pairs within rc.
+template <int NI_, bool MULTI, bool SHIFT, bool SAME>
 __device__ __forceinline__ unsigned eval_partner(const PairArgs &a, const float4 *tab, const float4 *xi, int ni,
                                                  int k0, float4 xj, int l, int np, int lmax_k, float (&fi)[3 * NI_],
                                                  R3<float> &fj, float &u_acc) {
-    unsigned nin = 0;
+    unsigned nin = 0, bm = 0;
     const float4 t0 = tab[0];
 #pragma unroll
     for (int t = 0; t < NI_; ++t) {
         if (t < ni) {
             const float4 x = xi[t];
-            float rx = x.x - xj.x, ry = x.y - xj.y, rz = x.z - xj.z;
-            float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
-            bool ok = k0 + t < lmax_k;
-            bool in = ok && r2 < a.rc2_lo;
-            bool band = ok && r2 >= a.rc2_lo && r2 < a.rc2_hi;
-            if (__any_sync(0xffffffffu, band))
-                if (band) in = band_in(a, k0 + t, l, np);
-            float fs, u;
-            lj32<MULTI, SHIFT>(tab, t0, __float_as_int(x.w), __float_as_int(xj.w), r2, fs, u);
-            fs = in ? fs : 0.f;
-            u_acc += in ? u : 0.f;
+            const float rx = x.x - xj.x, ry = x.y - xj.y, rz = x.z - xj.z;
+            const float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
+            const bool ok = !SAME || k0 + t < lmax_k;
+            const bool in = ok && r2 < a.rc2_lo;
+            if (ok && !in && r2 < a.rc2_hi) bm |= 1u << t;
+            pair32<MULTI, SHIFT>(tab, t0, __float_as_int(x.w), __float_as_int(xj.w), rx, ry, rz, r2, in, &fi[3 * t],
+                                 fj, u_acc);
             nin += in;
-            float fx = fs * rx, fy = fs * ry, fz = fs * rz;
-            fi[3 * t] += fx; fi[3 * t + 1] += fy; fi[3 * t + 2] += fz;
-            fj.x -= fx; fj.y -= fy; fj.z -= fz;
+        }
+    }
+    if (__any_sync(0xffffffffu, bm != 0)) {
+#pragma unroll
+        for (int t = 0; t < NI_; ++t) {
+            if ((bm >> t) & 1u) {
+                if (band_in(a, k0 + t, l, np)) {
+                    const float4 x = xi[t];
+                    const float rx = x.x - xj.x, ry = x.y - xj.y, rz = x.z - xj.z;
+                    const float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
+                    pair32<MULTI, SHIFT>(tab, t0, __float_as_int(x.w), __float_as_int(xj.w), rx, ry, rz, r2, true,
+                                         &fi[3 * t], fj, u_acc);
+                    nin++;
+                }
+            }
         }
     }
     return nin;
@@ -317,8 +343,11 @@ __global__ void __launch_bounds__(kThreads32, MINB) pair_fwd32(PairArgs a) {
                     if (lane == 0) w.cnt[3] += (unsigned)(count * ni);
                     R3<float> fj = {0.f, 0.f, 0.f};
                     const bool same = q.y == kSameCell;
-                    const unsigned nin = eval_partner<NI_, MULTI, SHIFT>(a, tab, w.xi, ni, k0, xj, q.x, same ? 0 : q.y,
-                                                                         same ? q.x : 0x7fffffff, fi, fj, v[0]);
+                    const unsigned nin =
+                        __any_sync(FULL, same)
+                            ? eval_partner<NI_, MULTI, SHIFT, true>(a, tab, w.xi, ni, k0, xj, q.x, same ? 0 : q.y,
+                                                                    same ? q.x : 0x7fffffff, fi, fj, v[0])
+                            : eval_partner<NI_, MULTI, SHIFT, false>(a, tab, w.xi, ni, k0, xj, q.x, q.y, 0, fi, fj, v[0]);
                     if (same) within[0] += nin;
                     else if (q.y != 0) within[2] += nin;
                     else within[1] += nin;
@@ -986,7 +1015,7 @@ int fwd32_grid() {
 
 template <int NI_, bool MULTI, bool SHIFT>
 int launch_fwd32_t(const PairArgs &a, cudaStream_t st) {
-    constexpr int MINB = NI_ <= 4 ? 7 : 5;
+    constexpr int MINB = NI_ <= 4 ? 7 : 6;
     const int grid = std::min(fwd32_grid<NI_, MULTI, SHIFT, MINB>(), std::max(1, (a.C + kWarps32 - 1) / kWarps32));
     pair_fwd32<NI_, MULTI, SHIFT, MINB><<<grid, kThreads32, 0, st>>>(a);
     return grid * kWarps32;
