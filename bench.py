@@ -31,6 +31,9 @@ if ROOT not in sys.path:
 METRIC = "LJ pair interactions/s within rc (FP32 vs FP64 on same GB300) at stated force error"
 UNIT = "pairs/s"
 FLOPS_EVAL, FLOPS_WITHIN = 8, 35     # algorithmic FP32 flops per evaluated / per within-rc pair evaluation
+FLOPS64_EVAL, FLOPS64_WITHIN = 14, 35  # FP64 path: (x_k - x_l) - n.L and r^2 unfused; pair body
+BIN_BYTES = 84                       # binning: pos 24 + species 4 + previous cell 4 read; cell, order,
+                                     # inverse 4 each + float4 16 + FP64 copy 24 written, per molecule
 FORCE_TOL = {"fp32": 1e-5, "fp64": 1e-12}
 
 
@@ -194,17 +197,19 @@ def run_ours(args):
     mesh.check()
     mesh.set_deferred(True)
     graphs = {}
-    for prec in ("fp32", "fp64"):
+    bin_only = lambda j: mesh.bin(pos_sets[j], sp, outputs=False)
+    for prec in ("fp32", "fp64", "bin"):
+        fn = bin_only if prec == "bin" else (lambda j, prec=prec: step(prec, j))
         for j in range(2):
             s = torch.cuda.Stream()
             s.wait_stream(torch.cuda.current_stream())
             with torch.cuda.stream(s):
                 for _ in range(max(3, args.warmup)):
-                    step(prec, j)
+                    fn(j)
             torch.cuda.current_stream().wait_stream(s)
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g):
-                step(prec, j)
+                fn(j)
             graphs[prec, j] = g
     torch.cuda.synchronize()
 
@@ -248,11 +253,19 @@ def run_ours(args):
             kms += [float(x) for x in mesh.take_kernel_times()]
     kms += [float(x) for x in mesh.take_kernel_times()]
     mesh.set_kernel_timing(False)
+    t_bin = timed("bin", max(3, min(args.steps, 200)), 3)
     fp64 = None
     if not args.no_extras:
         K64 = args.fp64_steps or max(3, args.steps // 10)
         t64 = timed("fp64", K64, 3)
         c64AB = [c.cpu().numpy() for c in cnts]
+        mesh.set_kernel_timing(True)
+        for i in range(10):
+            flush.zero_()
+            step("fp64")
+        kms64 = [float(x) for x in mesh.take_kernel_times()]
+        mesh.set_kernel_timing(False)
+        stats64 = mesh.last_stats()
     time.sleep(0.2)
     clk = clocks.stop()
     mesh.check()
@@ -268,6 +281,18 @@ def run_ours(args):
         tp64, ms64_max = aggregate(dist, pairs64, ms64, dev)
         fp64 = {"value": tp64 / (ms64_max * 1e-3), "ms_per_step": ms64_max, "steps": len(t64),
                 "pairs_equal_fp32": bool(all((c64AB[j][3:] == cAB[j][3:]).all() for j in range(2)))}
+        if rank == 0:
+            from paper_cs_0702131_gb300.aica import aica_probe_fma_rate
+            peak64 = aica_probe_fma_rate(True, 20000) / 1e12
+            k64 = statistics.mean(kms64)
+            w64 = int(c64AB[0][3] + c64AB[0][4] + c64AB[0][5])
+            fl64 = FLOPS64_EVAL * int(stats64[0]) + FLOPS64_WITHIN * w64
+            fp64["roofline"] = {"kernel": "pair_fwd64", "bound": "alu", "achieved": round(fl64 / (k64 * 1e-3) / 1e12, 4),
+                                "peak": round(peak64, 4), "unit": "TFLOP/s",
+                                "frac": round(fl64 / (k64 * 1e-3) / 1e12 / peak64, 4), "kernel_ms": round(k64, 4),
+                                "peak_basis": "measured FP64 FMA rate of this GPU (aica_probe_fma_rate)",
+                                "flop_model": (f"{FLOPS64_EVAL} per FP64 distance test ({int(stats64[0])}) + "
+                                               f"{FLOPS64_WITHIN} per within-rc pair; FP32 sphere tests not counted")}
 
     out = None
     if rank == 0:
@@ -290,6 +315,19 @@ def run_ours(args):
                                f"sphere tests {culls}) + {FLOPS_WITHIN} per within-rc pair evaluation")}
         if clk and clk.get("sm_mhz"):
             roof["frac_at_sampled_clock"] = round(achieved / (peak * clk["sm_mhz"] / sm_max), 4)
+        from paper_cs_0702131_gb300.aica import aica_probe_fma_rate
+        peak_fma = aica_probe_fma_rate(False, 1 << 20) / 1e12
+        roof["peak_measured_fma"] = round(peak_fma, 2)
+        roof["frac_of_measured_fma"] = round(achieved / peak_fma, 4)
+        tb = statistics.mean(t_bin)
+        hbm = peaks.get("hbm_gbs") or 6800.0
+        binning = {"ms_per_step": round(tb, 4), "bytes_per_molecule": BIN_BYTES,
+                   "achieved_GBps": round(n * BIN_BYTES / (tb * 1e-3) / 1e9, 1), "peak_GBps": hbm,
+                   "frac": round(n * BIN_BYTES / (tb * 1e-3) / 1e9 / hbm, 4),
+                   "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json)" if peaks.get("hbm_gbs")
+                   else "fallback 6.8 TB/s",
+                   "note": "whole binning stage (point location with previous-cell hints, counting sort, gather, "
+                           "spheres), CUDA graph, L2 flushed, position sets alternating"}
         # DRAM bytes per launch of this kernel from the committed ncu summary
         # (dram__bytes_read.sum + dram__bytes_write.sum), if one exists for it
         prof = os.path.join(ROOT, "profiles", f"pair_fwd32_{args.config}.md")
@@ -315,7 +353,7 @@ def run_ours(args):
                "energy_per_molecule": ev_main[0] / n,
                "gpu_launches": int(launches["fp32"]) * args.steps,
                "launches_per_step": int(launches["fp32"]),
-               "roofline": roof, "clocks": clk,
+               "roofline": roof, "binning": binning, "clocks": clk,
                "setup": {"mesh_create_s": round(t_create, 3), "build_lists_s": round(t_build, 4)}}
         if fp64:
             out["fp64"] = fp64
@@ -325,8 +363,10 @@ def run_ours(args):
         mesh.bin(pos_sets[0], sp, outputs=False)      # the oracle sees the first set
         out["force_error"] = accuracy(cfg, mesh, eps, sig, F32, F64, dev)
         out["e2e"] = e2e(args, cfg, mesh, flush, dev)
+        out["adjoint"] = adjoint_timing(cfg, mesh, flush, dev, pairs)
         if ws == 1:
             out["cpu_baseline"] = cpu_baseline(cfg)
+            out["cpu_cell_list"] = cpu_cell_list(cfg)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
@@ -393,6 +433,35 @@ def accuracy(cfg, mesh, eps, sig, F32, F64, dev):
     return res
 
 
+def adjoint_timing(cfg, mesh, flush, dev, pairs):
+    """The adjoint (aica_forces_backward: position gradient, i.e. a Hessian-
+    vector product, and per-species eps/sigma gradients) for a seeded random
+    dL/dF, timed eagerly with CUDA events, L2 flushed before each call."""
+    import numpy as np
+    import torch
+    n = len(cfg["pos"])
+    v = torch.tensor(np.random.default_rng(77).normal(size=(n, 3)), device=dev)
+    res = {}
+    for prec, dt in (("fp32", torch.float32), ("fp64", torch.float64)):
+        g = v.to(dt)
+        for _ in range(2):
+            mesh.forces_backward(cfg["eps"], cfg["sigma"], g, prec)
+        ms = []
+        for _ in range(10):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            mesh.forces_backward(cfg["eps"], cfg["sigma"], g, prec)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        t = statistics.median(ms)
+        res[prec] = {"ms": round(t, 4), "pairs_per_s": pairs / (t * 1e-3)}
+    res["note"] = ("one backward call (gather of dL/dF, pair kernel recomputing every pair term, scatter); "
+                   "binning of the current positions not included")
+    return res
+
+
 def e2e(args, cfg, mesh, flush, dev):
     """Through the public API with host buffers: H2D of positions and species
     from pinned memory, bin + forces, D2H of forces and energy/virial."""
@@ -430,7 +499,7 @@ def e2e(args, cfg, mesh, flush, dev):
     torch.cuda.synchronize()
     ms = statistics.mean(a.elapsed_time(b) for a, b in zip(e0, e1))
     c = cnt.cpu().numpy()
-    pairs = int(c[3] + c[4] + c[5] // 2)
+    pairs = int(c[3] + c[4] + c[5])
     return {"value": pairs / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": K,
             "h2d_bytes_per_step": int(pos_h.numel() * 8 + sp_h.numel() * 4),
             "d2h_bytes_per_step": int(F_h.numel() * 4 + ev_h.numel() * 8)}
@@ -456,6 +525,18 @@ def cpu_baseline(cfg, budget_s=10.0):
     return {"value": r["row_pairs"] / 2.0 / t, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"{m} of {n} molecules, each a full all-pairs row (FP64, OpenMP); {t:.2f} s",
             "seconds": round(t, 3)}
+
+
+def cpu_cell_list(cfg):
+    """The textbook cubic-cell algorithm (§2.1) in FP64 on the host cores over
+    the whole workload: the practical CPU baseline (not the timed reference)."""
+    import oracle
+    t0 = time.perf_counter()
+    r = oracle.lj_cells(cfg["pos"], cfg["species"], cfg["eps"], cfg["sigma"], cfg["rc"], cfg["box"])
+    t = time.perf_counter() - t0
+    return {"value": r["pairs"] / t, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "cubic-cell algorithm of the paper's §2.1, FP64, OpenMP (oracle library)",
+            "sample": f"all {len(cfg['pos'])} molecules, one evaluation", "seconds": round(t, 3)}
 
 
 # ------------------------------------------------------------------ reference arm

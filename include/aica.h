@@ -224,6 +224,17 @@ aica_status aica_take_kernel_times(aica_mesh *mesh, float *ms, int64_t cap, int6
  * `stream`. */
 aica_status aica_get_work_counters(aica_mesh *mesh, int64_t *out, void *stream);
 
+/* Measured arithmetic peak of the current device (a measurement helper with
+ * no counterpart in the paper): the rate of fused multiply-adds in FP32
+ * (fp64 == 0) or FP64 (fp64 != 0), counted as 2 flops each, over a grid
+ * that fills every SM with independent FMA chains of `iters` steps per
+ * chain.  One untimed launch, then one launch timed with CUDA events on
+ * `stream`; synchronizes `stream`.  *flops_per_s (host) receives the rate.
+ * Use iters of about 2e4 (FP64) or 1e6 (FP32) for a launch of tens of
+ * milliseconds.  iters outside [1, 2^30] -> AICA_ERR_INVALID_ARG.  Allocates
+ * no memory. */
+aica_status aica_probe_fma_rate(int fp64, int64_t iters, double *flops_per_s, void *stream);
+
 /* Number of kernels the last call on this mesh launched (for accounting). */
 int64_t aica_last_launch_count(const aica_mesh *mesh);
 

@@ -69,6 +69,8 @@ def lib():
         L.oracle_aica_loop.argtypes = [ctypes.c_int64, _i64, _f64, _i32, _f64, _f64, ctypes.c_double, _f64,
                                        ctypes.c_int, _i64, _i32, ctypes.c_int64, _i32, _i32, _i64, _i32, _f64,
                                        _f64, _i64]
+        L.oracle_lj_cells.argtypes = [ctypes.c_int64, _f64, _i32, _f64, _f64, ctypes.c_double, _f64, _i32,
+                                      ctypes.c_int, _f64, _f64, _f64, _f64, _i64]
         L.oracle_num_threads.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -108,6 +110,26 @@ def lj(pos, species, eps, sigma, rc, box, shift=False, idx=None):
     if idx is None:
         out["pairs"] = int(cnt[0]) // 2
     return out
+
+
+def lj_cells(pos, species, eps, sigma, rc, box, shift=False):
+    """The same sum as lj() by the cubic-cell algorithm of §2.1 (CPU baseline).
+
+    Returns the keys of lj() for all molecules.  Requires rc < L/2 on periodic
+    axes, as lj() does.
+    """
+    pos = _c(pos, np.float64)
+    n = pos.shape[0]
+    F = np.zeros((n, 3))
+    Fabs = np.zeros(n)
+    ev = np.zeros(7)
+    ab = np.zeros(2)
+    cnt = np.zeros(1, np.int64)
+    lib().oracle_lj_cells(n, pos, _c(species, np.int32), _c(eps, np.float64), _c(sigma, np.float64), float(rc),
+                          _c(box["L"], np.float64), _c(box["periodic"], np.int32), int(bool(shift)), F, Fabs, ev,
+                          ab, cnt)
+    return dict(F=F, Fabs=Fabs, U=ev[0], W=ev[1:].copy(), Uabs=ab[0], Wabs=ab[1], row_pairs=int(cnt[0]),
+                pairs=int(cnt[0]) // 2)
 
 
 # ------------------------------------------------------------------ cell geometry

@@ -19,6 +19,9 @@
  *                        uncertain cases are flagged for exact resolution
  *   oracle_aica_loop     the real-real and real-referred loops of §2.3 over
  *                        the oracle's own lists and binning
+ *   oracle_lj_cells      the same LJ sum by the textbook cubic-cell
+ *                        algorithm of §2.1 (bins of side >= rc, 27-bin
+ *                        stencil): the practical CPU baseline, not a pin
  */
 #include <math.h>
 #include <stdint.h>
@@ -520,6 +523,130 @@ void oracle_aica_loop(int64_t n_cells, const int64_t *cell_off, const double *xs
             }
         }
     }
+}
+
+/* ------------------------------------------------ cubic-cell baseline (§2.1) */
+/* The conventional cell algorithm the paper starts from: the box is cut into
+ * cubic bins of side >= rc, and every molecule meets the molecules of its own
+ * and the 26 surrounding bins (periodic wrap; a bin met twice through a narrow
+ * axis is visited once).  The pair arithmetic is oracle_lj's, so forces equal
+ * it up to summation order and counts equal it exactly.  On non-periodic axes
+ * the bins span the molecules' extent. */
+void oracle_lj_cells(int64_t n, const double *pos, const int32_t *species, const double *eps,
+                     const double *sigma, double rc, const double *L, const int32_t *periodic, int shift,
+                     double *F, double *Fabs, double *ev7, double *abs2, int64_t *count)
+{
+    double rc2 = rc * rc, lo[3], side[3];
+    int64_t nb[3];
+    for (int d = 0; d < 3; ++d) {
+        double a = 0, b = L[d];
+        if (!periodic[d]) {
+            a = INFINITY; b = -INFINITY;
+            for (int64_t k = 0; k < n; ++k) { a = fmin(a, pos[3 * k + d]); b = fmax(b, pos[3 * k + d]); }
+            if (n == 0) { a = 0; b = 1; }
+        }
+        lo[d] = a;
+        nb[d] = (int64_t)floor((b - a) / rc);
+        if (nb[d] < 1) nb[d] = 1;
+        side[d] = (b - a) / (double)nb[d];
+        if (!periodic[d]) side[d] *= 1.0 + 1e-12;
+    }
+    int64_t B = nb[0] * nb[1] * nb[2];
+    int64_t *bin = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int64_t *start = (int64_t *)calloc((size_t)B + 1, sizeof(int64_t));
+    int64_t *sorted = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    for (int64_t k = 0; k < n; ++k) {
+        int64_t c[3];
+        for (int d = 0; d < 3; ++d) {
+            double x = pos[3 * k + d];
+            if (periodic[d]) x -= L[d] * floor(x / L[d]);
+            c[d] = (int64_t)floor((x - lo[d]) / side[d]);
+            if (c[d] < 0) c[d] = 0;
+            if (c[d] >= nb[d]) c[d] = nb[d] - 1;
+        }
+        bin[k] = (c[0] * nb[1] + c[1]) * nb[2] + c[2];
+        start[bin[k] + 1]++;
+    }
+    for (int64_t b = 0; b < B; ++b) start[b + 1] += start[b];
+    {
+        int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)(B > 0 ? B : 1));
+        memcpy(fill, start, sizeof(int64_t) * (size_t)B);
+        for (int64_t k = 0; k < n; ++k) sorted[fill[bin[k]]++] = k;
+        free(fill);
+    }
+    double U = 0, wxx = 0, wyy = 0, wzz = 0, wxy = 0, wxz = 0, wyz = 0, Ua = 0, Va = 0;
+    int64_t cnt = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : U, wxx, wyy, wzz, wxy, wxz, wyz, Ua, Va, cnt)
+    for (int64_t k = 0; k < n; ++k) {
+        int64_t b = bin[k];
+        int64_t c[3] = {b / (nb[1] * nb[2]), (b / nb[2]) % nb[1], b % nb[2]};
+        int64_t seen[27];
+        int ns = 0;
+        double fx = 0, fy = 0, fz = 0, fa = 0;
+        int a = species[k];
+        for (int ox = -1; ox <= 1; ++ox)
+            for (int oy = -1; oy <= 1; ++oy)
+                for (int oz = -1; oz <= 1; ++oz) {
+                    int64_t q[3] = {c[0] + ox, c[1] + oy, c[2] + oz}, ok = 1;
+                    for (int d = 0; d < 3; ++d) {
+                        if (q[d] < 0 || q[d] >= nb[d]) {
+                            if (!periodic[d]) ok = 0;
+                            else q[d] = (q[d] + nb[d]) % nb[d];
+                        }
+                    }
+                    if (!ok) continue;
+                    int64_t nbin = (q[0] * nb[1] + q[1]) * nb[2] + q[2], dup = 0;
+                    for (int i = 0; i < ns; ++i) dup |= seen[i] == nbin;
+                    if (dup) continue;
+                    seen[ns++] = nbin;
+                    for (int64_t s = start[nbin]; s < start[nbin + 1]; ++s) {
+                        int64_t l = sorted[s];
+                        if (l == k) continue;
+                        double dx = min_image(pos[3 * k + 0] - pos[3 * l + 0], L[0], periodic[0]);
+                        double dy = min_image(pos[3 * k + 1] - pos[3 * l + 1], L[1], periodic[1]);
+                        double dz = min_image(pos[3 * k + 2] - pos[3 * l + 2], L[2], periodic[2]);
+                        double r2 = (dx * dx + dy * dy) + dz * dz;
+                        if (!(r2 < rc2)) continue;
+                        int bs = species[l];
+                        double eab = sqrt(eps[a] * eps[bs]);
+                        double sab = 0.5 * (sigma[a] + sigma[bs]);
+                        double fs, u;
+                        lj_pair(r2, eab, sab, &fs, &u);
+                        if (shift) {
+                            double fc, uc;
+                            lj_pair(rc2, eab, sab, &fc, &uc);
+                            u -= uc;
+                        }
+                        fx += fs * dx;
+                        fy += fs * dy;
+                        fz += fs * dz;
+                        fa += fabs(fs) * sqrt(r2);
+                        U += 0.5 * u;
+                        Ua += 0.5 * fabs(u);
+                        Va += 0.5 * fabs(fs) * r2;
+                        wxx += 0.5 * dx * (fs * dx);
+                        wyy += 0.5 * dy * (fs * dy);
+                        wzz += 0.5 * dz * (fs * dz);
+                        wxy += 0.5 * dx * (fs * dy);
+                        wxz += 0.5 * dx * (fs * dz);
+                        wyz += 0.5 * dy * (fs * dz);
+                        cnt += 1;
+                    }
+                }
+        F[3 * k + 0] = fx;
+        F[3 * k + 1] = fy;
+        F[3 * k + 2] = fz;
+        Fabs[k] = fa;
+    }
+    ev7[0] = U;
+    ev7[1] = wxx; ev7[2] = wyy; ev7[3] = wzz;
+    ev7[4] = wxy; ev7[5] = wxz; ev7[6] = wyz;
+    abs2[0] = Ua;
+    abs2[1] = Va;
+    *count = cnt;
+    free(bin);
+    free(start);
+    free(sorted);
 }
 
 int oracle_num_threads(void)

@@ -74,6 +74,8 @@ SIGNATURES = {
                                               ctypes.POINTER(ctypes.c_int64)]),
     "aica_sort_by_cell_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
                                                  ctypes.c_void_p, ctypes.c_void_p]),
+    "aica_probe_fma_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.c_void_p]),
     "aica_last_error": (ctypes.c_char_p, []),
     "aica_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -230,6 +232,13 @@ def aica_take_kernel_times(h, cap=1 << 16):
     n = ctypes.c_int64()
     _check(lib().aica_take_kernel_times(h, ms.ctypes.data, cap, ctypes.byref(n)))
     return ms[: n.value].copy()
+
+
+def aica_probe_fma_rate(fp64, iters):
+    """Measured FMA rate of the current device in flop/s (FP64 if fp64)."""
+    out = ctypes.c_double()
+    _check(lib().aica_probe_fma_rate(int(bool(fp64)), int(iters), ctypes.byref(out), _stream()))
+    return out.value
 
 
 # ---------------------------------------------------------------- convenience

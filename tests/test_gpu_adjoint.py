@@ -67,16 +67,22 @@ def test_force_matching_loss_c4():
         assert abs(fd - ge_g[s].item()) <= 1e-5 * abs(ge_g[s].item()) + 1e-6
         fd = (loss(c["eps"], c["sigma"] + d) - loss(c["eps"], c["sigma"] - d)) / (2 * h)
         assert abs(fd - gs_g[s].item()) <= 1e-5 * abs(gs_g[s].item()) + 1e-6
+    # position checks: the FP64 forces are summed with atomics, so the loss
+    # itself differs between repeated evaluations in its last bits; the
+    # difference quotient carries that noise divided by h (measured here)
+    L0 = loss(c["eps"], c["sigma"])
+    noise = max(abs(loss(c["eps"], c["sigma"]) - L0) for _ in range(4))
+    hx = 1e-5
     rng = np.random.default_rng(2)
-    for k in rng.choice(len(c["pos"]), 16, replace=False):
+    for k in rng.choice(len(c["pos"]), 64, replace=False):
         ax = int(rng.integers(3))
         p = pos.clone()
-        p[k, ax] += h
+        p[k, ax] += hx
         lp = loss(c["eps"], c["sigma"], p)
-        p[k, ax] -= 2 * h
+        p[k, ax] -= 2 * hx
         lm = loss(c["eps"], c["sigma"], p)
-        fd = (lp - lm) / (2 * h)
-        assert abs(fd - gp[k, ax].item()) <= 1e-4 * max(1.0, abs(gp[k, ax].item()))
+        fd = (lp - lm) / (2 * hx)
+        assert abs(fd - gp[k, ax].item()) <= 1e-4 * max(1.0, abs(gp[k, ax].item())) + 4 * noise / hx
     m.bin(pos, sp, outputs=False)
 
 

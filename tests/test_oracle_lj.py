@@ -148,3 +148,20 @@ def test_sampled_rows_equal_full():
     idx = np.array([0, 5, 17, 400, 863])
     part = oracle.lj(c["pos"], c["species"], c["eps"], c["sigma"], c["rc"], c["box"], idx=idx)
     np.testing.assert_array_equal(part["F"], full["F"][idx])
+
+
+@pytest.mark.parametrize("name", ["t0", "h0", "c1", "c4", "slab"])
+def test_cubic_cell_baseline_equals_all_pairs(name):
+    """The cubic-cell baseline (§2.1) visits exactly the pairs within rc."""
+    if name == "slab":
+        c = synth.nanochannel(3, nfcc=(12, 4, 12), hex_shape=(8, 4, 8), post_radius=2.0)
+    else:
+        c = synth.make(name, seed=4)
+    args = (c["pos"], c["species"], c["eps"], c["sigma"], c["rc"], c["box"])
+    a = oracle.lj(*args)
+    b = oracle.lj_cells(*args)
+    assert a["row_pairs"] == b["row_pairs"]
+    scale = a["Fabs"][:, None] + 1e-300
+    assert np.max(np.abs(a["F"] - b["F"]) / scale) < 1e-13
+    assert abs(a["U"] - b["U"]) <= 1e-13 * a["Uabs"]
+    assert np.all(np.abs(a["W"] - b["W"]) <= 1e-13 * a["Wabs"])
