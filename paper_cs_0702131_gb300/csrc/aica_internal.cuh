@@ -86,7 +86,8 @@ struct aica_mesh {
     // Geometry (device, FP64).  Triangles are oriented out of their cell.
     aica::DevBuf tri_off, tri, vtx_off, vtx, edg_off, edg;  // int32 offsets, double coords
     aica::DevBuf ctr, rad, lo, hi, org;                      // [C*3] vertex mean, [C] radius, AABB, origin
-    aica::DevBuf ntri;                                       // [C] int32 triangle counts
+    aica::DevBuf ntri;                                       // [C] int32 triangle count | convex << 16
+    aica::DevBuf box32;                                      // [C*6] float local AABB (lo, hi), rounded outward
     // FP32 copies local to each cell's dyadic origin org_c = orgk_c * 2^-10.
     aica::DevBuf orgk;                                       // [C*3] int32
     aica::DevBuf tri32, vtx32, edg32, ctr32;                 // float, minus org_c
@@ -115,7 +116,6 @@ struct aica_mesh {
     aica::DevBuf cell_of, order, cell_off, fill, xloc, xs64, scratch_i32, inv;
     int max_species = -1;                    // from the last checked binning, -1 if unknown
     aica::DevBuf sph;                        // [C] float4 molecule bounding sphere per cell (local frame)
-    aica::DevBuf part;                       // per-warp partial sums of the pair kernels
     aica::DevBuf miss;                       // molecules whose previous cell no longer holds them
     int64_t n_mol_prev = -1;                 // molecule count of the previous binning
     bool hint_valid = false;                 // cell_of holds that binning (a search hint)

@@ -4,22 +4,29 @@
 // Kernels
 //   bin_locate   thread per molecule: wrap periodic coordinates, look up the
 //                point-location bucket, test candidate cells until one holds
-//                p + (e, e^2, e^3): tetrahedra by their four face planes,
-//                other (star-shaped) cells by the cone from the vertex mean
+//                p + (e, e^2, e^3), and count the cell's molecules.  A cell
+//                holds the point if it lies behind every face plane; a convex
+//                cell (tetrahedra, and any cell checked convex at mesh
+//                creation) does not if it lies in front of one; other
+//                (star-shaped) cells take the cone from the vertex mean
 //                through each face triangle.  FP32 filter on cell-local
 //                coordinates, FP64 and exact slow paths (predicates.cuh).
 //   bin_locate_hint / bin_locate_miss   when the same molecules were binned
-//                before: test each molecule's previous cell, collect the
-//                ones that left it, then search those among the face
-//                neighbours of the previous cell and finally the grid.  The
-//                previous cell is only a search order: the test is exact.
-//   bin_count    warp-aggregated histogram of cells (match_any + one atomic)
-//   (scan)       cell offsets
-//   bin_scatter  warp-aggregated slot claims
-//   bin_fixup    per-cell insertion sort by original index: the binned order
-//                is the stable counting sort by (cell, original index)
-//   bin_gather   sorted FP64 positions and float4 cell-local coordinates with
-//                the species in .w (the pair kernels' input layout)
+//                before: test each molecule's previous cell with the FP32
+//                filter alone, collect the ones that left it (or that the
+//                filter could not decide), then search those exactly in the
+//                previous cell, its face neighbours and finally the grid.
+//                The previous cell is only a search order: the test is exact.
+//   (scan)       cell offsets from the counts
+//   bin_scatter_down  warp-aggregated slot claims, counting the counts down
+//   bin_cells    per cell (groups of 8 or 32 lanes): order the cell's slots by
+//                original index (the stable counting sort by (cell, original
+//                index)), gather FP64 positions and float4 cell-local
+//                coordinates with the species in .w (the pair kernels' input
+//                layout), the inverse permutation, and the cell's bounding
+//                sphere
+//   bin_count, bin_scatter, bin_fixup   the same sort for caller-given cells
+//                (aica_sort_by_cell_noalloc)
 #include <math.h>
 
 #include <algorithm>
@@ -45,12 +52,21 @@ struct BinArgs {
     double glo[3], gh[3], ghi[3];
     const int *bkt_off, *bkt_cells;
     const int *tri_off, *ntri, *orgk;
-    const float *tri32, *ctr32;
+    const float *tri32, *ctr32, *box32;
     const double *tri, *ctr;
     float max_local;
     int *cell_of;
+    int *cnt;              // molecules per cell (counted as they are located)
+    int *inv;              // original -> binned index; -1 for molecules in no cell
     unsigned *flags;
 };
+
+// Add one molecule to cell c's count (c < 0: none), aggregated over the warp's
+// lanes that located molecules in the same cell.  Every lane must call.
+__device__ __forceinline__ void count_located(const BinArgs &a, int c) {
+    const unsigned same = __match_any_sync(0xffffffffu, c);
+    if (c >= 0 && (int)(threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(a.cnt + c, __popc(same));
+}
 
 __device__ __forceinline__ double wrap_coord(double x, double L) {
     if (x >= 0.0 && x < L) return x;
@@ -61,25 +77,46 @@ __device__ __forceinline__ double wrap_coord(double x, double L) {
 
 __device__ __forceinline__ float3 ld3f(const float *p) { return make_float3(p[0], p[1], p[2]); }
 
-// sign of O(a, b, c, p + (e, e^2, e^3)); FP32 filter then exact slow path
+// sign of O(a, b, c, p + (e, e^2, e^3)): FP32 filter, then (EXACT) the FP64 and
+// exact stages; without EXACT an undecided filter returns 0
+template <bool EXACT>
 __device__ __forceinline__ int orient(float3 a, float3 b, float3 c, float3 q, float scale, const double *a64,
                                       const double *b64, const double *c64, const double *p64) {
     int s = orient_f32(a, b, c, q, scale);
-    if (s) return s;
-    return orient_sos_slow(a64, b64, c64, p64);
+    if (EXACT && !s) s = orient_sos_slow(a64, b64, c64, p64);
+    return s;
 }
 
-__device__ bool cell_contains(const BinArgs &a, int c, float3 q, const double *p64) {
-    int t0 = a.tri_off[c], nt = a.ntri[c];
-    float scale = fmaxf(a.max_local, fmaxf(fabsf(q.x), fmaxf(fabsf(q.y), fabsf(q.z))));
-    if (nt == 4) {   // tetrahedron: convex, inside iff behind all four faces
-        for (int t = t0; t < t0 + 4; ++t) {
-            const float *T = a.tri32 + 9 * t;
-            const double *D = a.tri + 9 * t;
-            if (orient(ld3f(T), ld3f(T + 3), ld3f(T + 6), q, scale, D, D + 3, D + 6, p64) > 0) return false;
+// q (p local to cell c) inside cell c with the SoS tie-break: 1 inside, 0
+// outside, -1 undecided (only without EXACT, when the FP32 filter cannot
+// decide; the caller then defers to an exact pass).  Behind every face plane
+// means inside for any closed cell star-shaped about its centre (the segment
+// from the centre to an outside point leaves through a face it ends in front
+// of); for a convex cell, in front of one face means outside.  Other cells
+// take the cone test: find the triangle whose cone from the centre holds q,
+// then q must lie behind that triangle.
+template <bool EXACT>
+__device__ int cell_test(const BinArgs &a, int c, float3 q, const double *p64) {
+    const float *B = a.box32 + 6 * c;
+    const float scale = fmaxf(a.max_local, fmaxf(fabsf(q.x), fmaxf(fabsf(q.y), fabsf(q.z))));
+    const float tol = 1e-5f * scale;
+    if (q.x < B[0] - tol || q.y < B[1] - tol || q.z < B[2] - tol || q.x > B[3] + tol || q.y > B[4] + tol ||
+        q.z > B[5] + tol)
+        return 0;
+    const int t0 = a.tri_off[c], code = a.ntri[c], nt = code & 0xffff;
+    bool behind = true;
+    for (int t = t0; t < t0 + nt; ++t) {
+        const float *T = a.tri32 + 9 * t;
+        const double *D = a.tri + 9 * t;
+        const int s = orient<EXACT>(ld3f(T), ld3f(T + 3), ld3f(T + 6), q, scale, D, D + 3, D + 6, p64);
+        if (!EXACT && s == 0) return -1;
+        if (s > 0) {
+            behind = false;
+            break;
         }
-        return true;
     }
+    if (behind) return 1;
+    if (code >> 16) return 0;
     float3 C = ld3f(a.ctr32 + 3 * c);
     const double *C64 = a.ctr + 3 * c;
     for (int t = t0; t < t0 + nt; ++t) {
@@ -87,12 +124,24 @@ __device__ bool cell_contains(const BinArgs &a, int c, float3 q, const double *p
         const double *D = a.tri + 9 * t;
         float3 x0 = ld3f(T), x1 = ld3f(T + 3), x2 = ld3f(T + 6);
         // p in the cone from C through triangle (x0, x1, x2)?
-        if (orient(C, x0, x1, q, scale, C64, D, D + 3, p64) < 0) continue;
-        if (orient(C, x1, x2, q, scale, C64, D + 3, D + 6, p64) < 0) continue;
-        if (orient(C, x2, x0, q, scale, C64, D + 6, D, p64) < 0) continue;
-        return orient(x0, x1, x2, q, scale, D, D + 3, D + 6, p64) < 0;
+        int s = orient<EXACT>(C, x0, x1, q, scale, C64, D, D + 3, p64);
+        if (!EXACT && s == 0) return -1;
+        if (s < 0) continue;
+        s = orient<EXACT>(C, x1, x2, q, scale, C64, D + 3, D + 6, p64);
+        if (!EXACT && s == 0) return -1;
+        if (s < 0) continue;
+        s = orient<EXACT>(C, x2, x0, q, scale, C64, D + 6, D, p64);
+        if (!EXACT && s == 0) return -1;
+        if (s < 0) continue;
+        s = orient<EXACT>(x0, x1, x2, q, scale, D, D + 3, D + 6, p64);
+        if (!EXACT && s == 0) return -1;
+        return s < 0 ? 1 : 0;
     }
-    return false;
+    return 0;
+}
+
+__device__ __forceinline__ bool cell_contains(const BinArgs &a, int c, float3 q, const double *p64) {
+    return cell_test<true>(a, c, q, p64) == 1;
 }
 
 // p relative to the dyadic origin c_k * 2^-10 of cell c, in FP32 (one rounding)
@@ -136,39 +185,52 @@ __device__ int grid_search(const BinArgs &a, const double *p, int skip) {
 // Full search for every molecule (no previous cells).
 __global__ void __launch_bounds__(256) bin_locate(BinArgs a) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= a.n) return;
-    double p[3];
-    bool ok;
-    wrapped_position(a, k, p, ok);
-    const int found = ok ? grid_search(a, p, -1) : -1;
-    a.cell_of[k] = found;
-    if (found < 0) atomicOr(a.flags, kFlagOutside);
+    int found = -1;
+    if (k < a.n) {
+        double p[3];
+        bool ok;
+        wrapped_position(a, k, p, ok);
+        found = ok ? grid_search(a, p, -1) : -1;
+        a.cell_of[k] = found;
+        if (found < 0) {
+            a.inv[k] = -1;
+            atomicOr(a.flags, kFlagOutside);
+        }
+    }
+    count_located(a, found);
 }
 
 // Previous cell first; molecules that left it go to the miss list.
 __global__ void __launch_bounds__(256) bin_locate_hint(BinArgs a) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    bool miss = false;
+    bool miss = false, undecided = false;
+    int located = -1;
     if (k < a.n) {
         double p[3];
         bool ok;
         wrapped_position(a, k, p, ok);
         const int h = a.hint[k];
-        if (ok && h >= 0 && cell_contains(a, h, local_to(a, p, h), p)) {
+        const int r = (ok && h >= 0) ? cell_test<false>(a, h, local_to(a, p, h), p) : 0;
+        if (r == 1) {
             a.cell_of[k] = h;
+            located = h;
         } else if (ok) {
             miss = true;
+            undecided = r < 0;
         } else {
             a.cell_of[k] = -1;
+            a.inv[k] = -1;
             atomicOr(a.flags, kFlagOutside);
         }
     }
+    count_located(a, located);
     const unsigned bal = __ballot_sync(0xffffffffu, miss);
     const int lane = threadIdx.x & 31;
     int base = 0;
     if (lane == 0 && bal) base = atomicAdd(a.miss, __popc(bal));
     base = __shfl_sync(0xffffffffu, base, 0);
-    if (miss) a.miss[1 + base + __popc(bal & ((1u << lane) - 1u))] = (int)k;
+    // the top bit marks molecules whose previous cell the FP32 filter could not decide
+    if (miss) a.miss[1 + base + __popc(bal & ((1u << lane) - 1u))] = (int)k | (undecided ? (int)0x80000000u : 0);
 }
 
 // Molecules that left their previous cell: one warp per molecule, lanes test
@@ -179,13 +241,19 @@ __global__ void __launch_bounds__(256) bin_locate_miss(BinArgs a) {
     const int nm = a.miss[0];
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nm; i += nw) {
-        const int k = a.miss[1 + i];
+        const int e = a.miss[1 + i];
+        const int k = e & 0x7fffffff;
         double p[3];
         bool ok;
         wrapped_position(a, k, p, ok);
         const int h = a.hint[k];
         int found = -1;
-        if (h >= 0) {
+        if (e < 0) {            // the previous cell, undecided by the FP32 filter: exactly, once
+            bool in = false;
+            if (lane == 0) in = cell_contains(a, h, local_to(a, p, h), p);
+            if (__shfl_sync(0xffffffffu, in, 0)) found = h;
+        }
+        if (h >= 0 && found < 0) {
             const int j1 = a.nbr_off[h + 1];
             for (int j0 = a.nbr_off[h]; j0 < j1; j0 += 32) {
                 const int j = j0 + lane;
@@ -225,7 +293,12 @@ __global__ void __launch_bounds__(256) bin_locate_miss(BinArgs a) {
         }
         if (lane == 0) {
             a.cell_of[k] = found;
-            if (found < 0) atomicOr(a.flags, kFlagOutside);
+            if (found >= 0) {
+                atomicAdd(a.cnt + found, 1);
+            } else {
+                a.inv[k] = -1;
+                atomicOr(a.flags, kFlagOutside);
+            }
         }
     }
 }
@@ -265,52 +338,125 @@ __global__ void __launch_bounds__(256) bin_fixup(const int *cell_off, int C, int
     }
 }
 
-__global__ void __launch_bounds__(256) bin_gather(BinArgs a, const int *order, const int *cell_off, int C,
-                                                  double *xs64, float4 *xloc, int *inv) {
-    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int sp = 0;
-    if (s < cell_off[C]) {
-        int k = order[s];
-        inv[k] = (int)s;
-        sp = a.species[k];
-    int c = a.cell_of[k];
-    double p[3];
-    for (int d = 0; d < 3; ++d) {
-        p[d] = a.pos[3 * (int64_t)k + d];
-        if (a.per[d]) p[d] = wrap_coord(p[d], a.L[d]);
-        xs64[3 * s + d] = p[d];
-    }
-    xloc[s] = make_float4((float)(p[0] - a.orgk[3 * c] * (1.0 / 1024.0)), (float)(p[1] - a.orgk[3 * c + 1] * (1.0 / 1024.0)),
-                          (float)(p[2] - a.orgk[3 * c + 2] * (1.0 / 1024.0)), __int_as_float(sp & (kMaxSpecies - 1)));
-    }
-    // largest species index (flags[1]) and out-of-range species (flags[0])
-    unsigned bad = (unsigned)sp >= (unsigned)kMaxSpecies;
-    int mx = __reduce_max_sync(0xffffffffu, sp < 0 ? kMaxSpecies : sp);
-    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(a.flags, kFlagSpecies);
-    if ((threadIdx.x & 31) == 0) atomicMax((int *)a.flags + 1, mx);
+// Slots of located molecules: cell c's count (from the locate kernels) is
+// counted down, so the counts are zero again afterwards.  Order within a
+// cell is fixed by bin_cells.
+__global__ void __launch_bounds__(256) bin_scatter_down(const int *cell_of, int64_t n, const int *cell_off, int *cnt,
+                                                        int *order) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = k < n ? cell_of[k] : -1;
+    const unsigned same = __match_any_sync(0xffffffffu, c);
+    const int lane = threadIdx.x & 31, leader = __ffs(same) - 1, m = __popc(same);
+    int top = 0;
+    if (c >= 0 && lane == leader) top = atomicSub(cnt + c, m);
+    top = __shfl_sync(0xffffffffu, top, leader);
+    if (c >= 0) order[cell_off[c] + top - m + __popc(same & ((1u << lane) - 1u))] = (int)k;
 }
 
-// Per-cell bounding sphere of its molecules in the cell's local frame:
-// centre = mean, radius = max distance, rounded up.  Used by the pair kernels
-// to skip cell pairs and partner molecules that cannot be within rc.
-__global__ void __launch_bounds__(256) bin_spheres(const int *cell_off, int C, const float4 *xloc, float4 *sph) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= C) return;
-    int s = cell_off[c], e = cell_off[c + 1];
-    float cx = 0.f, cy = 0.f, cz = 0.f;
-    for (int i = s; i < e; ++i) {
-        float4 x = xloc[i];
-        cx += x.x; cy += x.y; cz += x.z;
+// Per cell, by groups of G lanes: order the cell's molecules by original
+// index (the stable counting sort), gather FP64 positions and FP32
+// coordinates local to the cell's origin into binned order, record the
+// inverse permutation, and the cell's bounding sphere (centre = mean, radius
+// = largest distance, rounded up) that the pair kernels cull with.
+template <int G>
+__global__ void __launch_bounds__(256) bin_cells(BinArgs a, const int *cell_off, int C, int *order, double *xs64,
+                                                 float4 *xloc, float4 *sph) {
+    const int lane = threadIdx.x & 31, g = lane & (G - 1);
+    const int groups = (gridDim.x * blockDim.x) / G;
+    int spmax = 0;
+    bool bad = false;
+    // every lane runs the same number of rounds (shuffles below use the full warp)
+    const int rounds = (C + groups - 1) / groups;
+    for (int r = 0; r < rounds; ++r) {
+        const int c = r * groups + (int)((blockIdx.x * blockDim.x + threadIdx.x) / G);
+        const int s = c < C ? cell_off[c] : 0, m = c < C ? cell_off[c + 1] - s : 0;
+        const bool small = m <= G;
+        int k = (small && g < m) ? order[s + g] : 0x7fffffff;
+        int rank = 0;
+#pragma unroll
+        for (int j = 0; j < G; ++j) rank += __shfl_sync(0xffffffffu, k, j, G) < k;
+        __syncwarp();
+        float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+        const bool mine = small && g < m;
+        if (mine) {
+            const int slot = s + rank;
+            order[slot] = k;
+            a.inv[k] = slot;
+            const int sp = a.species[k];
+            spmax = max(spmax, sp < 0 ? kMaxSpecies : sp);
+            bad |= (unsigned)sp >= (unsigned)kMaxSpecies;
+            double p[3];
+            for (int d = 0; d < 3; ++d) {
+                p[d] = a.pos[3 * (int64_t)k + d];
+                if (a.per[d]) p[d] = wrap_coord(p[d], a.L[d]);
+                xs64[3 * (int64_t)slot + d] = p[d];
+            }
+            x = make_float4((float)(p[0] - a.orgk[3 * c] * (1.0 / 1024.0)), (float)(p[1] - a.orgk[3 * c + 1] * (1.0 / 1024.0)),
+                            (float)(p[2] - a.orgk[3 * c + 2] * (1.0 / 1024.0)), __int_as_float(sp & (kMaxSpecies - 1)));
+            xloc[slot] = x;
+        }
+        float cx = mine ? x.x : 0.f, cy = mine ? x.y : 0.f, cz = mine ? x.z : 0.f;
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            cx += __shfl_xor_sync(0xffffffffu, cx, o, G);
+            cy += __shfl_xor_sync(0xffffffffu, cy, o, G);
+            cz += __shfl_xor_sync(0xffffffffu, cz, o, G);
+        }
+        const float inv_m = m > 0 ? 1.f / (float)m : 0.f;
+        cx *= inv_m; cy *= inv_m; cz *= inv_m;
+        float r2 = 0.f;
+        if (mine) {
+            const float dx = x.x - cx, dy = x.y - cy, dz = x.z - cz;
+            r2 = dx * dx + dy * dy + dz * dz;
+        }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) r2 = fmaxf(r2, __shfl_xor_sync(0xffffffffu, r2, o, G));
+        if (small && c < C && g == 0) sph[c] = make_float4(cx, cy, cz, sqrtf(r2) * (1.f + 1e-5f) + 1e-5f);
+        if (!small && g == 0) {
+            // more molecules than lanes: one lane sorts, gathers and bounds the cell
+            for (int i = s + 1; i < s + m; ++i) {
+                const int v = order[i];
+                int j = i - 1;
+                while (j >= s && order[j] > v) {
+                    order[j + 1] = order[j];
+                    --j;
+                }
+                order[j + 1] = v;
+            }
+            float sx = 0.f, sy = 0.f, sz = 0.f;
+            for (int slot = s; slot < s + m; ++slot) {
+                const int kk = order[slot];
+                a.inv[kk] = slot;
+                const int sp = a.species[kk];
+                spmax = max(spmax, sp < 0 ? kMaxSpecies : sp);
+                bad |= (unsigned)sp >= (unsigned)kMaxSpecies;
+                double p[3];
+                for (int d = 0; d < 3; ++d) {
+                    p[d] = a.pos[3 * (int64_t)kk + d];
+                    if (a.per[d]) p[d] = wrap_coord(p[d], a.L[d]);
+                    xs64[3 * (int64_t)slot + d] = p[d];
+                }
+                const float4 y = make_float4((float)(p[0] - a.orgk[3 * c] * (1.0 / 1024.0)),
+                                             (float)(p[1] - a.orgk[3 * c + 1] * (1.0 / 1024.0)),
+                                             (float)(p[2] - a.orgk[3 * c + 2] * (1.0 / 1024.0)),
+                                             __int_as_float(sp & (kMaxSpecies - 1)));
+                xloc[slot] = y;
+                sx += y.x; sy += y.y; sz += y.z;
+            }
+            sx /= (float)m; sy /= (float)m; sz /= (float)m;
+            float rr = 0.f;
+            for (int slot = s; slot < s + m; ++slot) {
+                const float4 y = xloc[slot];
+                const float dx = y.x - sx, dy = y.y - sy, dz = y.z - sz;
+                rr = fmaxf(rr, dx * dx + dy * dy + dz * dz);
+            }
+            sph[c] = make_float4(sx, sy, sz, sqrtf(rr) * (1.f + 1e-5f) + 1e-5f);
+        }
     }
-    float inv = e > s ? 1.f / (float)(e - s) : 0.f;
-    cx *= inv; cy *= inv; cz *= inv;
-    float r2 = 0.f;
-    for (int i = s; i < e; ++i) {
-        float4 x = xloc[i];
-        float dx = x.x - cx, dy = x.y - cy, dz = x.z - cz;
-        r2 = fmaxf(r2, dx * dx + dy * dy + dz * dz);
-    }
-    sph[c] = make_float4(cx, cy, cz, sqrtf(r2) * (1.f + 1e-5f) + 1e-5f);
+    // largest species index (flags[1]) and out-of-range species (flags[0])
+    const int mx = __reduce_max_sync(0xffffffffu, spmax);
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.flags, kFlagSpecies);
+    if (lane == 0) atomicMax((int *)a.flags + 1, mx);
 }
 
 }  // namespace
@@ -366,6 +512,7 @@ extern "C" aica_status aica_bin_molecules(aica_mesh *m, const double *pos, const
     a.orgk = m->orgk.as<int>();
     a.tri32 = m->tri32.as<float>();
     a.ctr32 = m->ctr32.as<float>();
+    a.box32 = m->box32.as<float>();
     a.tri = m->tri.as<double>();
     a.ctr = m->ctr.as<double>();
     a.max_local = (float)(m->max_local * (1 + 1e-6));
@@ -383,10 +530,13 @@ extern "C" aica_status aica_bin_molecules(aica_mesh *m, const double *pos, const
     a.flags = m->flags.as<unsigned>();
     int *cnt = m->fill.as<int>();
     int *off = m->cell_off.as<int>();
+    a.cnt = cnt;
+    a.inv = m->inv.as<int>();
     AICA_CUDA(cudaMemsetAsync(m->flags.p, 0, 16, st));
     AICA_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (C + 1), st));
     unsigned nb = (unsigned)((n + 255) / 256);
     if (n > 0) {
+        // locate every molecule and count the cells' molecules
         if (a.hint) {
             AICA_CUDA(cudaMemsetAsync(m->miss.p, 0, sizeof(int), st));
             bin_locate_hint<<<nb, 256, 0, st>>>(a);
@@ -396,21 +546,21 @@ extern "C" aica_status aica_bin_molecules(aica_mesh *m, const double *pos, const
             bin_locate<<<nb, 256, 0, st>>>(a);
             m->launches += 1;
         }
-        bin_count<<<nb, 256, 0, st>>>(a.cell_of, n, cnt);
-        m->launches += 1;
     }
     m->launches += exclusive_scan<int, int>(cnt, C, off, m->scratch_i32.as<int>(), st);
-    AICA_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (C + 1), st));
     if (n > 0) {
-        bin_scatter<<<nb, 256, 0, st>>>(a.cell_of, n, off, cnt, m->order.as<int>());
-        bin_fixup<<<(C + 255) / 256, 256, 0, st>>>(off, C, m->order.as<int>());
-        AICA_CUDA(cudaMemsetAsync(m->inv.p, 0xff, sizeof(int) * n, st));
-        bin_gather<<<nb, 256, 0, st>>>(a, m->order.as<int>(), off, C, m->xs64.as<double>(), m->xloc.as<float4>(),
-                                       m->inv.as<int>());
-        m->launches += 3;
+        bin_scatter_down<<<nb, 256, 0, st>>>(a.cell_of, n, off, cnt, m->order.as<int>());
+        m->launches += 1;
     }
-    bin_spheres<<<(C + 255) / 256, 256, 0, st>>>(off, C, m->xloc.as<float4>(), m->sph.as<float4>());
-    m->launches += 1;
+    // per cell: order by original index, gather, bounding sphere (lane groups sized to the mean occupancy)
+    if (C > 0) {
+        const bool wide = (double)n > 6.0 * (double)C;
+        const int64_t lanes = (int64_t)C * (wide ? 32 : 8);
+        const unsigned gc = (unsigned)std::min<int64_t>((lanes + 255) / 256, 152 * 16);
+        if (wide) bin_cells<32><<<gc, 256, 0, st>>>(a, off, C, m->order.as<int>(), m->xs64.as<double>(), m->xloc.as<float4>(), m->sph.as<float4>());
+        else bin_cells<8><<<gc, 256, 0, st>>>(a, off, C, m->order.as<int>(), m->xs64.as<double>(), m->xloc.as<float4>(), m->sph.as<float4>());
+        m->launches += 1;
+    }
     m->n_mol_prev = n;
     m->hint_valid = true;
     AICA_CUDA(cudaGetLastError());

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "aica_internal.cuh"
+#include "predicates.cuh"
 
 namespace {
 
@@ -26,6 +27,24 @@ cudaError_t upload(aica::DevBuf &buf, const std::vector<T> &h) {
     return e;
 }
 
+}  // namespace
+
+namespace {
+// Sign of O(a, b, c, p) = ((b - a) x (c - a)) . (p - a), exactly: FP64 filter,
+// then the exact determinant.
+int orient_host(const double *a, const double *b, const double *c, const double *p) {
+    double u[3], v[3], w[3];
+    for (int d = 0; d < 3; ++d) { u[d] = a[d] - p[d]; v[d] = b[d] - p[d]; w[d] = c[d] - p[d]; }
+    double m0 = v[1] * w[2], m1 = v[2] * w[1], m2 = v[2] * w[0], m3 = v[0] * w[2], m4 = v[0] * w[1], m5 = v[1] * w[0];
+    double det = u[0] * (m0 - m1) + u[1] * (m2 - m3) + u[2] * (m4 - m5);
+    double perm = fabs(u[0]) * (fabs(m0) + fabs(m1)) + fabs(u[1]) * (fabs(m2) + fabs(m3)) +
+                  fabs(u[2]) * (fabs(m4) + fabs(m5));
+    int s;
+    if (det > 1e-14 * perm) s = 1;
+    else if (det < -1e-14 * perm) s = -1;
+    else s = aica::exact_det3_sign(a, b, c, p);
+    return -s;
+}
 }  // namespace
 
 extern "C" aica_status aica_mesh_create(const double *points, int64_t n_points, const int64_t *face_offsets,
@@ -182,11 +201,23 @@ extern "C" aica_status aica_mesh_create(const double *points, int64_t n_points, 
         h_tri_off[c + 1] = (int32_t)t1;
         h_vtx_off[c + 1] = h_vtx_off[c] + (int32_t)vs.size();
         h_edg_off[c + 1] = h_edg_off[c] + ne;
-        h_ntri[c] = nt;
+        // convex: no vertex in front of any face plane (exact).  Binning then
+        // decides "outside" at the first face a point is in front of.
+        bool convex = true;
+        if (nt != 4)
+            for (int64_t t = t0; t < t1 && convex; ++t) {
+                const double *a = points + 3 * tv[3 * t], *b = points + 3 * tv[3 * t + 1],
+                             *e = points + 3 * tv[3 * t + 2];
+                for (int64_t v : vs) {
+                    if (v == tv[3 * t] || v == tv[3 * t + 1] || v == tv[3 * t + 2]) continue;
+                    if (orient_host(a, b, e, points + 3 * v) > 0) { convex = false; break; }
+                }
+            }
+        h_ntri[c] = nt | (convex ? 1 << 16 : 0);
     }
     if (T > INT32_MAX / 2) { set_error("too many triangles"); return AICA_ERR_CAPACITY; }
     std::vector<float> h_tri32(9 * T), h_vtx32(h_vtx.size()), h_edg32(h_edg.size()), h_ctr32(3 * n_cells),
-        h_rad32(n_cells);
+        h_rad32(n_cells), h_box32(6 * n_cells);
     double max_local = 0;
     for (int64_t c = 0; c < n_cells; ++c) {
         for (int64_t i = 3 * (int64_t)h_tri_off[c]; i < 3 * (int64_t)h_tri_off[c + 1]; ++i)
@@ -200,6 +231,10 @@ extern "C" aica_status aica_mesh_create(const double *points, int64_t n_points, 
         for (int64_t i = 2 * (int64_t)h_edg_off[c]; i < 2 * (int64_t)h_edg_off[c + 1]; ++i)
             for (int d = 0; d < 3; ++d) h_edg32[3 * i + d] = (float)(h_edg[3 * i + d] - h_org[3 * c + d]);
         for (int d = 0; d < 3; ++d) h_ctr32[3 * c + d] = (float)(h_ctr[3 * c + d] - h_org[3 * c + d]);
+        for (int d = 0; d < 3; ++d) {
+            h_box32[6 * c + d] = nextafterf((float)(h_lo[3 * c + d] - h_org[3 * c + d]), -INFINITY);
+            h_box32[6 * c + 3 + d] = nextafterf((float)(h_hi[3 * c + d] - h_org[3 * c + d]), INFINITY);
+        }
         h_rad32[c] = (float)(h_rad[c] * (1 + 1e-6)) + 1e-6f;
     }
 
@@ -291,6 +326,7 @@ extern "C" aica_status aica_mesh_create(const double *points, int64_t n_points, 
     if (e == cudaSuccess) e = upload(m->tri_off, h_tri_off);
     if (e == cudaSuccess) e = upload(m->tri, h_tri);
     if (e == cudaSuccess) e = upload(m->ntri, h_ntri);
+    if (e == cudaSuccess) e = upload(m->box32, h_box32);
     if (e == cudaSuccess) e = upload(m->vtx_off, h_vtx_off);
     if (e == cudaSuccess) e = upload(m->vtx, h_vtx);
     if (e == cudaSuccess) e = upload(m->edg_off, h_edg_off);
@@ -312,7 +348,7 @@ extern "C" aica_status aica_mesh_create(const double *points, int64_t n_points, 
     if (e == cudaSuccess) e = upload(m->bkt_cells, h_bkt_cells);
     if (e == cudaSuccess) { e = m->flags.reserve(16); what = "flags"; }
     if (e == cudaSuccess) e = cudaMemset(m->flags.p, 0, 16);
-    if (e == cudaSuccess) { e = m->acc.reserve(256); what = "acc"; }
+    if (e == cudaSuccess) { e = m->acc.reserve(sizeof(double) * (64 + 64 * 16)); what = "acc"; }
     if (e != cudaSuccess) {
         aica_status s = e == cudaErrorMemoryAllocation ? AICA_ERR_OOM : AICA_ERR_CUDA;
         cuda_fail(e, what);
@@ -328,10 +364,10 @@ extern "C" aica_status aica_mesh_create(const double *points, int64_t n_points, 
 extern "C" void aica_mesh_destroy(aica_mesh *m) {
     if (!m) return;
     aica::DevBuf *bufs[] = {&m->tri_off, &m->tri, &m->vtx_off, &m->vtx, &m->edg_off, &m->edg, &m->ctr, &m->rad,
-                            &m->lo, &m->hi, &m->org, &m->ntri, &m->orgk, &m->tri32, &m->vtx32, &m->edg32, &m->ctr32, &m->rad32, &m->bkt_off, &m->bkt_cells, &m->nbr_off, &m->nbr, &m->dil_off,
+                            &m->lo, &m->hi, &m->org, &m->ntri, &m->orgk, &m->tri32, &m->vtx32, &m->edg32, &m->ctr32, &m->rad32, &m->box32, &m->bkt_off, &m->bkt_cells, &m->nbr_off, &m->nbr, &m->dil_off,
                             &m->dil_ids, &m->ref_src, &m->ref_n, &m->ref_off, &m->ref_ids, &m->work_off,
                             &m->work, &m->work_split, &m->proc_order, &m->cell_of, &m->order,
-                            &m->cell_off, &m->fill, &m->inv, &m->sph, &m->part, &m->xloc, &m->xs64, &m->scratch_i32, &m->facc,
+                            &m->cell_off, &m->fill, &m->inv, &m->sph, &m->xloc, &m->xs64, &m->scratch_i32, &m->facc,
                             &m->vsorted, &m->acc, &m->flags, &m->params, &m->tmp};
     for (auto *b : bufs) b->release();
     for (auto *v : {&m->tev, &m->tfree})

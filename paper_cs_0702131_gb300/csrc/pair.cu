@@ -49,7 +49,7 @@ namespace {
 
 constexpr int kPairThreads = 256;
 constexpr int kWarps = kPairThreads / 32;
-constexpr int kParts = 16;           // per-warp partial sums: U, W[6], counters[8]
+constexpr int kParts = 16;           // accumulator row: U, W[6], counters[8]
 constexpr int NI = 8;                // i-molecules per chunk in the FP64 kernel
 
 struct SpeciesTab {
@@ -73,7 +73,6 @@ struct PairArgs {
     void *facc;                  // float4 (FP32) or double4 (FP64), binned order
     const void *vs;              // backward: grad_force in binned order (float4 / double4)
     double *acc;                 // [0..6] U, W; [8..15] counters (as unsigned long long); [16..] grads
-    double *part;                // per-warp partial sums [warps][kParts]
     unsigned *next_cell;         // FP32 kernel: next unclaimed cell (zero at launch)
     SpeciesTab tab;
 };
@@ -107,38 +106,39 @@ __device__ __noinline__ bool band_in(const PairArgs &a, int k, int l, int np) {
     return r2 < a.rc2_d;
 }
 
-// Per-lane running sums: U and the six virial components (FP32, flushed to
-// FP64 every few cells) and counters.
-struct Sums {
-    float v[7];
-    unsigned eval[3], within[3], tests, culls;
-    __device__ void zero() {
-#pragma unroll
-        for (int i = 0; i < 7; ++i) v[i] = 0.f;
-        for (int i = 0; i < 3; ++i) eval[i] = within[i] = 0;
-        tests = culls = 0;
-    }
-    __device__ __forceinline__ void outer(float ax, float ay, float az, float bx, float by, float bz) {
-        v[1] = fmaf(ax, bx, v[1]);
-        v[2] = fmaf(ay, by, v[2]);
-        v[3] = fmaf(az, bz, v[3]);
-        v[4] = fmaf(ax, by, v[4]);
-        v[5] = fmaf(ax, bz, v[5]);
-        v[6] = fmaf(ay, bz, v[6]);
-    }
-};
+// Sums of the pair kernels.  Every warp adds its totals (FP64 sums identical
+// in all lanes; counters per lane) to one of kStripes rows of FP64
+// accumulators (row = warp index mod kStripes, so few warps share an
+// address); finish_sums adds the rows.  Row layout: [0..6] U and W,
+// [7..14] the counters, exactly representable in FP64.
+constexpr int kStripes = 64;
+constexpr int kAccStripes = 64;        // offset of the rows in acc (doubles)
 
-// Write the warp's partial sums (FP64) and counters to part[warp].
-template <class Flt>
-__device__ void store_partials(double *part, int gwarp, const double (&dsum)[7], const unsigned (&cv)[8], int lane) {
-    double *row = part + (size_t)gwarp * kParts;
+__device__ void warp_to_stripe(const PairArgs &a, int gwarp, const double (&dsum)[7], const unsigned (&cv)[8],
+                               int lane) {
+    double *row = a.acc + kAccStripes + (size_t)(gwarp % kStripes) * kParts;
     for (int i = 0; i < 8; ++i) {
-        unsigned s = __reduce_add_sync(0xffffffffu, cv[i]);
-        if (lane == 0) row[7 + i] = (double)s;
+        const unsigned s = __reduce_add_sync(0xffffffffu, cv[i]);
+        if (lane == 0 && s) atomicAdd(row + 7 + i, (double)s);
     }
-    if (lane == 0)
-        for (int i = 0; i < 7; ++i) row[i] = dsum[i];
-    if (lane == 0) row[15] = 0.0;
+    if (lane < 7) atomicAdd(row + lane, dsum[lane < 7 ? lane : 0]);
+}
+
+// Totals of the stripe rows into acc ([0..6] FP64, [8..15] counters as
+// unsigned 64-bit) and the caller's energy/virial [7] and pair counts [6].
+__global__ void finish_sums(double *acc, double *ev, long long *counts) {
+    const int i = threadIdx.x;
+    if (i >= 15) return;
+    double v = 0.0;
+    for (int r = 0; r < kStripes; ++r) v += acc[kAccStripes + r * kParts + i];
+    if (i < 7) {
+        acc[i] = v;
+        if (ev) ev[i] = v;
+    } else {
+        const unsigned long long c = (unsigned long long)llrint(v);
+        ((unsigned long long *)(acc + 8))[i - 7] = c;
+        if (counts && i < 13) counts[i - 7] = (long long)c;
+    }
 }
 
 // ------------------------------------------------------------------ FP32 path
@@ -479,7 +479,7 @@ __global__ void __launch_bounds__(kThreads32, MINB) pair_fwd32(PairArgs a) {
     cv[6] = __shfl_sync(FULL, cv[6], 0);
     cv[7] = __shfl_sync(FULL, cv[7], 0);
     if (lane != 0) cv[0] = cv[1] = cv[2] = cv[6] = cv[7] = 0;
-    store_partials<float>(a.part, blockIdx.x * kWarps32 + wib, fin, cv, lane);
+    warp_to_stripe(a, blockIdx.x * kWarps32 + wib, fin, cv, lane);
 }
 
 // ------------------------------------------------------------------ FP64 path
@@ -691,30 +691,7 @@ __global__ void __launch_bounds__(kPairThreads) pair_fwd64(PairArgs a) {
     double dsum[7];
     for (int i = 0; i < 7; ++i) dsum[i] = warp_sum(acc[i]);
     unsigned cv[8] = {eval[0], eval[1], eval[2], within[0], within[1], within[2], tests, culls};
-    store_partials<double>(a.part, gwarp, dsum, cv, lane);
-}
-
-// Sum the per-warp partials into acc[0..6] (FP64) and acc[8..15] (counters),
-// which must be zero on entry: one row per thread, block sums, one atomic per
-// value and block.
-__global__ void __launch_bounds__(256) finalize_partials(const double *part, int nwarps, double *acc) {
-    __shared__ double sh[256 / 32][kParts];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    double s[15];
-    for (int i = 0; i < 15; ++i) s[i] = 0;
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nwarps; r += gridDim.x * blockDim.x)
-        for (int i = 0; i < 15; ++i) s[i] += part[(size_t)r * kParts + i];
-    for (int i = 0; i < 15; ++i) {
-        double v = warp_sum(s[i]);
-        if (lane == 0) sh[w][i] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < 15) {
-        double v = 0;
-        for (int j = 0; j < 256 / 32; ++j) v += sh[j][threadIdx.x];
-        if (threadIdx.x < 7) atomicAdd(acc + threadIdx.x, v);
-        else atomicAdd((unsigned long long *)(acc + 8) + (threadIdx.x - 7), (unsigned long long)llrint(v));
-    }
+    warp_to_stripe(a, gwarp, dsum, cv, lane);
 }
 
 // ---------------------------------------------------------------- unsort
@@ -738,11 +715,6 @@ __global__ void __launch_bounds__(256) unsort_forces(const int *inv, int64_t n, 
     out[3 * k + 2] = (T)z;
 }
 
-__global__ void finish_sums(const double *acc, double *ev, long long *counts) {
-    int i = threadIdx.x;
-    if (ev && i < 7) ev[i] = acc[i];
-    if (counts && i < 6) counts[i] = (long long)((const unsigned long long *)(acc + 8))[i];
-}
 
 // ---------------------------------------------------------------- adjoint
 // Per pair with r = x_k - x_l', f = g(r^2) r, g = 24 e inv s3 (2 s3 - 1):
@@ -985,7 +957,6 @@ void fill_common(aica_mesh *m, PairArgs &a) {
     for (int d = 0; d < 3; ++d) a.L[d] = m->box.periodic[d] ? m->box.L[d] : 0.0;
     a.facc = m->facc.p;
     a.acc = m->acc.as<double>();
-    a.part = m->part.as<double>();
 }
 
 aica_status check_flags(aica_mesh *m, cudaStream_t st) {
@@ -1043,27 +1014,20 @@ extern "C" aica_status aica_forces(aica_mesh *m, const aica_lj *lj, aica_precisi
     aica_status s = fill_params(m, lj, kMaxSpecies, a);
     if (s != AICA_OK) return s;
     const int grid = pair_grid((int)m->n_cells);
-    int dev = 0, sms = 0;
-    AICA_CUDA(cudaGetDevice(&dev));
-    AICA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    // rows: FP64 grid, or the persistent FP32 grid (at most 16 blocks of 4 warps per SM)
-    const int rows_max = std::max(grid * kWarps, sms * 16 * kWarps32);
-    AICA_CUDA(m->part.reserve(sizeof(double) * kParts * rows_max));
     fill_common(m, a);
     a.next_cell = (unsigned *)(m->acc.as<double>() + 24);
     m->launches = 0;
     const int64_t n = m->n_mol;
     const bool f64 = prec == AICA_FP64;
     if (n > 0) AICA_CUDA(cudaMemsetAsync(m->facc.p, 0, (f64 ? 4 * sizeof(double) : sizeof(float4)) * n, st));
-    AICA_CUDA(cudaMemsetAsync(m->acc.p, 0, 32 * sizeof(double), st));
+    AICA_CUDA(cudaMemsetAsync(m->acc.p, 0, (kAccStripes + kStripes * kParts) * sizeof(double), st));
     const bool multi = a.S > 1, shift = lj->shift != 0;
     cudaEvent_t tstop;
     AICA_CUDA(timing_begin(m, st, &tstop));
-    int rows = grid * kWarps;
     if (!f64) {
         // i-chunk width: 4 for cells of a few molecules (tetrahedra), 8 otherwise
-        if ((double)n < 5.0 * (double)a.C) rows = launch_fwd32<4>(a, multi, shift, st);
-        else rows = launch_fwd32<8>(a, multi, shift, st);
+        if ((double)n < 5.0 * (double)a.C) launch_fwd32<4>(a, multi, shift, st);
+        else launch_fwd32<8>(a, multi, shift, st);
     } else {
         if (multi) {
             if (shift) pair_fwd64<true, true><<<grid, kPairThreads, 0, st>>>(a);
@@ -1074,15 +1038,11 @@ extern "C" aica_status aica_forces(aica_mesh *m, const aica_lj *lj, aica_precisi
         }
     }
     AICA_CUDA(timing_end(tstop, st));
-    finalize_partials<<<(rows + 255) / 256, 256, 0, st>>>(a.part, rows, a.acc);
+    finish_sums<<<1, 32, 0, st>>>(m->acc.as<double>(), ev_out, (long long *)counts_out);
     m->launches = 2;
     if (n > 0) {
         if (f64) unsort_forces<double><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m->inv.as<int>(), n, m->facc.p, (double *)force_out, 1);
         else unsort_forces<float><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m->inv.as<int>(), n, m->facc.p, (float *)force_out, 0);
-        m->launches++;
-    }
-    if (ev_out || counts_out) {
-        finish_sums<<<1, 32, 0, st>>>(m->acc.as<double>(), ev_out, (long long *)counts_out);
         m->launches++;
     }
     AICA_CUDA(cudaGetLastError());

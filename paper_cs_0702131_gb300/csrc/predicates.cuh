@@ -13,29 +13,45 @@
 
 #include <cuda_runtime.h>
 
+#include <cmath>
+
+// The exact stages also run on the host (mesh checks); host code is built
+// with FP contraction off, so every operation rounds as written there too.
+#ifdef __CUDA_ARCH__
+#define AICA_DADD(a, b) __dadd_rn(a, b)
+#define AICA_DSUB(a, b) __dsub_rn(a, b)
+#define AICA_DMUL(a, b) __dmul_rn(a, b)
+#define AICA_DFMA(a, b, c) __fma_rn(a, b, c)
+#else
+#define AICA_DADD(a, b) ((a) + (b))
+#define AICA_DSUB(a, b) ((a) - (b))
+#define AICA_DMUL(a, b) ((a) * (b))
+#define AICA_DFMA(a, b, c) std::fma(a, b, c)
+#endif
+
 namespace aica {
 
 // ------------------------------------------------------------ exact arithmetic
-__device__ __forceinline__ void two_sum(double a, double b, double &x, double &y) {
-    x = __dadd_rn(a, b);
-    double bv = __dsub_rn(x, a);
-    double av = __dsub_rn(x, bv);
-    y = __dadd_rn(__dsub_rn(a, av), __dsub_rn(b, bv));
+__host__ __device__ __forceinline__ void two_sum(double a, double b, double &x, double &y) {
+    x = AICA_DADD(a, b);
+    double bv = AICA_DSUB(x, a);
+    double av = AICA_DSUB(x, bv);
+    y = AICA_DADD(AICA_DSUB(a, av), AICA_DSUB(b, bv));
 }
-__device__ __forceinline__ void two_diff(double a, double b, double &x, double &y) {
-    x = __dsub_rn(a, b);
-    double bv = __dsub_rn(a, x);
-    double av = __dadd_rn(x, bv);
-    y = __dadd_rn(__dsub_rn(a, av), __dsub_rn(bv, b));
+__host__ __device__ __forceinline__ void two_diff(double a, double b, double &x, double &y) {
+    x = AICA_DSUB(a, b);
+    double bv = AICA_DSUB(a, x);
+    double av = AICA_DADD(x, bv);
+    y = AICA_DADD(AICA_DSUB(a, av), AICA_DSUB(bv, b));
 }
-__device__ __forceinline__ void two_prod(double a, double b, double &x, double &y) {
-    x = __dmul_rn(a, b);
-    y = __fma_rn(a, b, -x);
+__host__ __device__ __forceinline__ void two_prod(double a, double b, double &x, double &y) {
+    x = AICA_DMUL(a, b);
+    y = AICA_DFMA(a, b, -x);
 }
 
 // e <- e + b, keeping e a nonoverlapping expansion in increasing magnitude
 // with zero components removed.
-__device__ inline void grow(double *e, int &n, double b) {
+__host__ __device__ inline void grow(double *e, int &n, double b) {
     double q = b;
     int m = 0;
     for (int i = 0; i < n; ++i) {
@@ -48,12 +64,12 @@ __device__ inline void grow(double *e, int &n, double b) {
     n = m;
 }
 
-__device__ inline int expansion_sign(const double *e, int n) {
+__host__ __device__ inline int expansion_sign(const double *e, int n) {
     return n == 0 ? 0 : (e[n - 1] > 0 ? 1 : -1);
 }
 
 // add s * (x1 + x0) * (y1 + y0) * (z1 + z0) to e (each factor a two-term expansion)
-__device__ inline void grow_triple(double *e, int &n, double s, const double x[2], const double y[2],
+__host__ __device__ inline void grow_triple(double *e, int &n, double s, const double x[2], const double y[2],
                                    const double z[2]) {
     for (int i = 0; i < 2; ++i)
         for (int j = 0; j < 2; ++j) {
@@ -72,7 +88,8 @@ __device__ inline void grow_triple(double *e, int &n, double s, const double x[2
 }
 
 // exact sign of det[u; v; w] where u = a - p etc. (rows), FP64 inputs
-__device__ __noinline__ int exact_det3_sign(const double *a, const double *b, const double *c, const double *p) {
+static __host__ __device__ __noinline__ int exact_det3_sign(const double *a, const double *b, const double *c,
+                                                   const double *p) {
     double u[3][2], v[3][2], w[3][2];
     for (int d = 0; d < 3; ++d) {
         two_diff(a[d], p[d], u[d][0], u[d][1]);
@@ -92,7 +109,7 @@ __device__ __noinline__ int exact_det3_sign(const double *a, const double *b, co
 }
 
 // exact sign of (b_i - a_i)(c_j - a_j) - (b_j - a_j)(c_i - a_i)
-__device__ __noinline__ int exact_det2_sign(const double *a, const double *b, const double *c, int i, int j) {
+static __device__ __noinline__ int exact_det2_sign(const double *a, const double *b, const double *c, int i, int j) {
     double x[2], y[2], z[2], t[2];
     two_diff(b[i], a[i], x[0], x[1]);
     two_diff(c[j], a[j], y[0], y[1]);
@@ -115,7 +132,7 @@ __device__ __noinline__ int exact_det2_sign(const double *a, const double *b, co
 
 // --------------------------------------------------------------- the predicate
 // FP64 stage and exact stage of the perturbed orientation sign (FP64 inputs).
-__device__ __noinline__ int orient_sos_slow(const double *a, const double *b, const double *c, const double *p) {
+static __device__ __noinline__ int orient_sos_slow(const double *a, const double *b, const double *c, const double *p) {
     double u[3], v[3], w[3];
     for (int d = 0; d < 3; ++d) {
         u[d] = a[d] - p[d];
