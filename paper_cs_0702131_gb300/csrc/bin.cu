@@ -28,6 +28,7 @@
 //   bin_count, bin_scatter, bin_fixup   the same sort for caller-given cells
 //                (aica_sort_by_cell_noalloc)
 #include <math.h>
+#include <string.h>
 
 #include <algorithm>
 
@@ -52,6 +53,8 @@ struct BinArgs {
     double glo[3], gh[3], ghi[3];
     const int *bkt_off, *bkt_cells;
     const int *tri_off, *ntri, *orgk;
+    const double *org;        // cell origins orgk * 2^-10 (FP64, exact)
+    long long Lkey[3], glo_key[3], ghi_key[3];
     const float *tri32, *ctr32, *box32;
     const double *tri, *ctr;
     float max_local;
@@ -68,8 +71,19 @@ __device__ __forceinline__ void count_located(const BinArgs &a, int c) {
     if (c >= 0 && (int)(threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(a.cnt + c, __popc(same));
 }
 
-__device__ __forceinline__ double wrap_coord(double x, double L) {
-    if (x >= 0.0 && x < L) return x;
+// Order-preserving integer key of a double: for non-NaN values a < b exactly
+// when key(a) < key(b), and key(-0) = key(+0).  Range tests on keys run on the
+// integer units instead of the (narrow) FP64 pipe; NaN and infinite
+// coordinates still fail the mesh bounds test.
+__host__ __device__ __forceinline__ long long dkey(double x) {
+    long long b;
+    memcpy(&b, &x, sizeof(b));
+    return b >= 0 ? b : -(b & 0x7fffffffffffffffLL);
+}
+
+__device__ __forceinline__ double wrap_coord(double x, double L, long long Lkey) {
+    const long long k = dkey(x);
+    if (k >= 0 && k < Lkey) return x;
     x = __dsub_rn(x, __dmul_rn(L, floor(__ddiv_rn(x, L))));
     if (x >= L) x = __dsub_rn(x, L);
     return x;
@@ -146,16 +160,17 @@ __device__ __forceinline__ bool cell_contains(const BinArgs &a, int c, float3 q,
 
 // p relative to the dyadic origin c_k * 2^-10 of cell c, in FP32 (one rounding)
 __device__ __forceinline__ float3 local_to(const BinArgs &a, const double *p, int c) {
-    return make_float3((float)(p[0] - a.orgk[3 * c] * (1.0 / 1024.0)), (float)(p[1] - a.orgk[3 * c + 1] * (1.0 / 1024.0)),
-                       (float)(p[2] - a.orgk[3 * c + 2] * (1.0 / 1024.0)));
+    const double *o = a.org + 3 * c;
+    return make_float3((float)(p[0] - o[0]), (float)(p[1] - o[1]), (float)(p[2] - o[2]));
 }
 
 __device__ __forceinline__ void wrapped_position(const BinArgs &a, int64_t k, double *p, bool &ok) {
     ok = true;
     for (int d = 0; d < 3; ++d) {
         p[d] = a.pos[3 * k + d];
-        if (a.per[d]) p[d] = wrap_coord(p[d], a.L[d]);
-        if (!(p[d] >= a.glo[d] && p[d] <= a.ghi[d])) ok = false;
+        if (a.per[d]) p[d] = wrap_coord(p[d], a.L[d], a.Lkey[d]);
+        const long long key = dkey(p[d]);
+        if (!(key >= a.glo_key[d] && key <= a.ghi_key[d])) ok = false;
     }
 }
 
@@ -388,11 +403,12 @@ __global__ void __launch_bounds__(256) bin_cells(BinArgs a, const int *cell_off,
             double p[3];
             for (int d = 0; d < 3; ++d) {
                 p[d] = a.pos[3 * (int64_t)k + d];
-                if (a.per[d]) p[d] = wrap_coord(p[d], a.L[d]);
+                if (a.per[d]) p[d] = wrap_coord(p[d], a.L[d], a.Lkey[d]);
                 xs64[3 * (int64_t)slot + d] = p[d];
             }
-            x = make_float4((float)(p[0] - a.orgk[3 * c] * (1.0 / 1024.0)), (float)(p[1] - a.orgk[3 * c + 1] * (1.0 / 1024.0)),
-                            (float)(p[2] - a.orgk[3 * c + 2] * (1.0 / 1024.0)), __int_as_float(sp & (kMaxSpecies - 1)));
+            const double *o = a.org + 3 * c;
+            x = make_float4((float)(p[0] - o[0]), (float)(p[1] - o[1]), (float)(p[2] - o[2]),
+                            __int_as_float(sp & (kMaxSpecies - 1)));
             xloc[slot] = x;
         }
         float cx = mine ? x.x : 0.f, cy = mine ? x.y : 0.f, cz = mine ? x.z : 0.f;
@@ -433,12 +449,11 @@ __global__ void __launch_bounds__(256) bin_cells(BinArgs a, const int *cell_off,
                 double p[3];
                 for (int d = 0; d < 3; ++d) {
                     p[d] = a.pos[3 * (int64_t)kk + d];
-                    if (a.per[d]) p[d] = wrap_coord(p[d], a.L[d]);
+                    if (a.per[d]) p[d] = wrap_coord(p[d], a.L[d], a.Lkey[d]);
                     xs64[3 * (int64_t)slot + d] = p[d];
                 }
-                const float4 y = make_float4((float)(p[0] - a.orgk[3 * c] * (1.0 / 1024.0)),
-                                             (float)(p[1] - a.orgk[3 * c + 1] * (1.0 / 1024.0)),
-                                             (float)(p[2] - a.orgk[3 * c + 2] * (1.0 / 1024.0)),
+                const double *o = a.org + 3 * c;
+                const float4 y = make_float4((float)(p[0] - o[0]), (float)(p[1] - o[1]), (float)(p[2] - o[2]),
                                              __int_as_float(sp & (kMaxSpecies - 1)));
                 xloc[slot] = y;
                 sx += y.x; sy += y.y; sz += y.z;
@@ -510,6 +525,12 @@ extern "C" aica_status aica_bin_molecules(aica_mesh *m, const double *pos, const
     a.tri_off = m->tri_off.as<int>();
     a.ntri = m->ntri.as<int>();
     a.orgk = m->orgk.as<int>();
+    a.org = m->org.as<double>();
+    for (int d = 0; d < 3; ++d) {
+        a.Lkey[d] = dkey(a.L[d]);
+        a.glo_key[d] = dkey(a.glo[d]);
+        a.ghi_key[d] = dkey(a.ghi[d]);
+    }
     a.tri32 = m->tri32.as<float>();
     a.ctr32 = m->ctr32.as<float>();
     a.box32 = m->box32.as<float>();

@@ -126,11 +126,13 @@ __device__ void warp_to_stripe(const PairArgs &a, int gwarp, const double (&dsum
 
 // Totals of the stripe rows into acc ([0..6] FP64, [8..15] counters as
 // unsigned 64-bit) and the caller's energy/virial [7] and pair counts [6].
-__global__ void finish_sums(double *acc, double *ev, long long *counts) {
-    const int i = threadIdx.x;
-    if (i >= 15) return;
+// One warp per value (15 warps), lanes over the stripe rows.
+__global__ void __launch_bounds__(15 * 32) finish_sums(double *acc, double *ev, long long *counts) {
+    const int i = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double v = 0.0;
-    for (int r = 0; r < kStripes; ++r) v += acc[kAccStripes + r * kParts + i];
+    for (int r = lane; r < kStripes; r += 32) v += acc[kAccStripes + r * kParts + i];
+    v = warp_sum(v);
+    if (lane != 0) return;
     if (i < 7) {
         acc[i] = v;
         if (ev) ev[i] = v;
@@ -1038,7 +1040,7 @@ extern "C" aica_status aica_forces(aica_mesh *m, const aica_lj *lj, aica_precisi
         }
     }
     AICA_CUDA(timing_end(tstop, st));
-    finish_sums<<<1, 32, 0, st>>>(m->acc.as<double>(), ev_out, (long long *)counts_out);
+    finish_sums<<<1, 15 * 32, 0, st>>>(m->acc.as<double>(), ev_out, (long long *)counts_out);
     m->launches = 2;
     if (n > 0) {
         if (f64) unsort_forces<double><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m->inv.as<int>(), n, m->facc.p, (double *)force_out, 1);

@@ -52,6 +52,7 @@ __host__ __device__ __forceinline__ void two_prod(double a, double b, double &x,
 // e <- e + b, keeping e a nonoverlapping expansion in increasing magnitude
 // with zero components removed.
 __host__ __device__ inline void grow(double *e, int &n, double b) {
+    if (b == 0.0) return;
     double q = b;
     int m = 0;
     for (int i = 0; i < n; ++i) {
@@ -68,23 +69,30 @@ __host__ __device__ inline int expansion_sign(const double *e, int n) {
     return n == 0 ? 0 : (e[n - 1] > 0 ? 1 : -1);
 }
 
-// add s * (x1 + x0) * (y1 + y0) * (z1 + z0) to e (each factor a two-term expansion)
+// add s * (x1 + x0) * (y1 + y0) * (z1 + z0) to e (each factor a two-term
+// expansion; zero terms, common for inputs on a lattice, are skipped)
 __host__ __device__ inline void grow_triple(double *e, int &n, double s, const double x[2], const double y[2],
-                                   const double z[2]) {
-    for (int i = 0; i < 2; ++i)
+                                            const double z[2]) {
+    for (int i = 0; i < 2; ++i) {
+        if (x[i] == 0.0) continue;
         for (int j = 0; j < 2; ++j) {
+            if (y[j] == 0.0) continue;
             double p, q;
             two_prod(x[i], y[j], p, q);
             for (int k = 0; k < 2; ++k) {
+                if (z[k] == 0.0) continue;
                 double r, t;
                 two_prod(p, z[k], r, t);
                 grow(e, n, s * r);
                 grow(e, n, s * t);
-                two_prod(q, z[k], r, t);
-                grow(e, n, s * r);
-                grow(e, n, s * t);
+                if (q != 0.0) {
+                    two_prod(q, z[k], r, t);
+                    grow(e, n, s * r);
+                    grow(e, n, s * t);
+                }
             }
         }
+    }
 }
 
 // exact sign of det[u; v; w] where u = a - p etc. (rows), FP64 inputs
@@ -120,12 +128,16 @@ static __device__ __noinline__ int exact_det2_sign(const double *a, const double
     for (int r = 0; r < 2; ++r)
         for (int s = 0; s < 2; ++s) {
             double p, q;
-            two_prod(x[r], y[s], p, q);
-            grow(e, n, p);
-            grow(e, n, q);
-            two_prod(z[r], t[s], p, q);
-            grow(e, n, -p);
-            grow(e, n, -q);
+            if (x[r] != 0.0 && y[s] != 0.0) {
+                two_prod(x[r], y[s], p, q);
+                grow(e, n, p);
+                grow(e, n, q);
+            }
+            if (z[r] != 0.0 && t[s] != 0.0) {
+                two_prod(z[r], t[s], p, q);
+                grow(e, n, -p);
+                grow(e, n, -q);
+            }
         }
     return expansion_sign(e, n);
 }
