@@ -68,6 +68,13 @@ struct WorkEntry {
     int32_t n;      // image vector, 3 x int8 packed (x in bits 0-7, y 8-15, z 16-23)
 };
 
+// One run of the FP32 kernel's schedule: partner cells j .. j + len - 1 (one
+// contiguous range of binned molecules under one shift).
+struct RunEntry {
+    int32_t j;      // first partner cell
+    int32_t n;      // image vector in bits 0-23 (as WorkEntry), len - 1 in bits 24-31
+};
+
 __host__ __device__ inline int32_t pack_n(int nx, int ny, int nz) {
     return (int32_t)(((unsigned)(nx & 0xff)) | ((unsigned)(ny & 0xff) << 8) | ((unsigned)(nz & 0xff) << 16));
 }
@@ -90,6 +97,9 @@ struct aica_mesh {
     aica::DevBuf box32;                                      // [C*6] float local AABB (lo, hi), rounded outward
     // FP32 copies local to each cell's dyadic origin org_c = orgk_c * 2^-10.
     aica::DevBuf orgk;                                       // [C*3] int32
+    // Molecule frame: binned FP32 coordinates are local to orgm_c * 2^-10, an
+    // origin shared by runs of consecutive cells (see mesh.cu).
+    aica::DevBuf orgm, orgm64;                               // [C*3] int32, double (exact)
     aica::DevBuf tri32, vtx32, edg32, ctr32;                 // float, minus org_c
     aica::DevBuf rad32;                                      // [C] float, rad rounded up
     double max_local = 0;                                    // largest |local coordinate|
@@ -104,8 +114,9 @@ struct aica_mesh {
     // Interaction lists (device), valid when built.
     bool built = false;
     double rc = 0, skin = 0;
-    int64_t n_dil = 0, n_ref = 0, n_ref_ids = 0, n_ties = 0, n_work = 0;
+    int64_t n_dil = 0, n_ref = 0, n_ref_ids = 0, n_ties = 0, n_work = 0, n_runs = 0;
     aica::DevBuf dil_off, dil_ids, ref_src, ref_n, ref_off, ref_ids;   // int32 (ref_n: 3 int32)
+    aica::DevBuf run_off, runs;              // [C+1] int32 first run of each cell; RunEntry
     aica::DevBuf work_off, work;             // [C+1] int32 first entry of each cell; WorkEntry (partner, image)
     aica::DevBuf work_split;                 // [C] int32: first periodic-image entry of each cell
     aica::DevBuf proc_order;                 // [C] int32: cell processing order (spatially local)

@@ -53,7 +53,8 @@ struct BinArgs {
     double glo[3], gh[3], ghi[3];
     const int *bkt_off, *bkt_cells;
     const int *tri_off, *ntri, *orgk;
-    const double *org;        // cell origins orgk * 2^-10 (FP64, exact)
+    const double *org;        // cell origins orgk * 2^-10 (FP64, exact): frame of the cell tests
+    const double *orgm64;     // molecule-frame origins (FP64, exact): frame of the binned coordinates
     long long Lkey[3], glo_key[3], ghi_key[3];
     const float *tri32, *ctr32, *box32;
     const double *tri, *ctr;
@@ -370,7 +371,7 @@ __global__ void __launch_bounds__(256) bin_scatter_down(const int *cell_of, int6
 
 // Per cell, by groups of G lanes: order the cell's molecules by original
 // index (the stable counting sort), gather FP64 positions and FP32
-// coordinates local to the cell's origin into binned order, record the
+// coordinates local to the cell's molecule-frame origin into binned order, record the
 // inverse permutation, and the cell's bounding sphere (centre = mean, radius
 // = largest distance, rounded up) that the pair kernels cull with.
 template <int G>
@@ -406,7 +407,7 @@ __global__ void __launch_bounds__(256) bin_cells(BinArgs a, const int *cell_off,
                 if (a.per[d]) p[d] = wrap_coord(p[d], a.L[d], a.Lkey[d]);
                 xs64[3 * (int64_t)slot + d] = p[d];
             }
-            const double *o = a.org + 3 * c;
+            const double *o = a.orgm64 + 3 * c;
             x = make_float4((float)(p[0] - o[0]), (float)(p[1] - o[1]), (float)(p[2] - o[2]),
                             __int_as_float(sp & (kMaxSpecies - 1)));
             xloc[slot] = x;
@@ -452,7 +453,7 @@ __global__ void __launch_bounds__(256) bin_cells(BinArgs a, const int *cell_off,
                     if (a.per[d]) p[d] = wrap_coord(p[d], a.L[d], a.Lkey[d]);
                     xs64[3 * (int64_t)slot + d] = p[d];
                 }
-                const double *o = a.org + 3 * c;
+                const double *o = a.orgm64 + 3 * c;
                 const float4 y = make_float4((float)(p[0] - o[0]), (float)(p[1] - o[1]), (float)(p[2] - o[2]),
                                              __int_as_float(sp & (kMaxSpecies - 1)));
                 xloc[slot] = y;
@@ -526,6 +527,7 @@ extern "C" aica_status aica_bin_molecules(aica_mesh *m, const double *pos, const
     a.ntri = m->ntri.as<int>();
     a.orgk = m->orgk.as<int>();
     a.org = m->org.as<double>();
+    a.orgm64 = m->orgm64.as<double>();
     for (int d = 0; d < 3; ++d) {
         a.Lkey[d] = dkey(a.L[d]);
         a.glo_key[d] = dkey(a.glo[d]);

@@ -362,6 +362,42 @@ __global__ void lst_fill(FillArgs f) {
     }
 }
 
+// Runs of the pair schedule: consecutive entries of one cell whose partner
+// cells are consecutive, share the image vector and share the molecule-frame
+// origin collapse into one run (first partner, count): their molecules are
+// one contiguous range of the binned order under one shift.
+__device__ __forceinline__ bool run_continues(const WorkEntry &p, const WorkEntry &e, const int *orgm, int len) {
+    if (e.j != p.j + 1 || e.n != p.n || len >= 256) return false;
+    const int *a = orgm + 3 * p.j, *b = orgm + 3 * e.j;
+    return a[0] == b[0] && a[1] == b[1] && a[2] == b[2];
+}
+
+__global__ void lst_runs(const int *work_off, const WorkEntry *work, const int *orgm, int C, const int *run_off,
+                         int *run_cnt, RunEntry *runs) {
+    const int A = blockIdx.x * blockDim.x + threadIdx.x;
+    if (A >= C) return;
+    const int r = run_off ? run_off[A] : 0;
+    int nr = 0, len = 0, j0 = 0;
+    WorkEntry p{0, 0};
+    auto flush = [&]() {
+        if (runs) runs[r + nr] = RunEntry{j0, (p.n & 0xffffff) | ((len - 1) << 24)};
+        ++nr;
+    };
+    for (int e = work_off[A]; e < work_off[A + 1]; ++e) {
+        const WorkEntry w = work[e];
+        if (len > 0 && run_continues(p, w, orgm, len)) {
+            ++len;
+        } else {
+            if (len > 0) flush();
+            j0 = w.j;
+            len = 1;
+        }
+        p = w;
+    }
+    if (len > 0) flush();
+    if (run_cnt) run_cnt[A] = nr;
+}
+
 }  // namespace
 }  // namespace aica
 
@@ -531,6 +567,18 @@ extern "C" aica_status aica_build_interaction_list(aica_mesh *m, double rc, doub
     f.work = m->work.as<WorkEntry>();
     lst_fill<<<(C + 1 + 255) / 256, 256, 0, st>>>(f);
     m->launches += 1;
+    // runs of the schedule (FP32 pair kernel): count, offsets, fill
+    CK(m->run_off.reserve(sizeof(int) * (C + 1)));
+    int *run_cnt = o_re;     // the referral scratch is free again
+    lst_runs<<<(C + 255) / 256, 256, 0, st>>>(f.work_off, f.work, m->orgm.as<int>(), C, nullptr, run_cnt, nullptr);
+    m->launches += 1 + exclusive_scan<int, int>(run_cnt, C, m->run_off.as<int>(), sw, st);
+    int n_runs = 0;
+    CK(cudaMemcpyAsync(&n_runs, m->run_off.as<int>() + C, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    CK(m->runs.reserve(sizeof(RunEntry) * std::max(n_runs, 1)));
+    lst_runs<<<(C + 255) / 256, 256, 0, st>>>(f.work_off, f.work, m->orgm.as<int>(), C, m->run_off.as<int>(),
+                                               nullptr, m->runs.as<RunEntry>());
+    m->launches += 1;
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(st));
 #undef CK
@@ -540,6 +588,7 @@ extern "C" aica_status aica_build_interaction_list(aica_mesh *m, double rc, doub
     m->n_ref_ids = tot[1];
     m->n_ref = tot[2];
     m->n_work = n_work;
+    m->n_runs = n_runs;
     m->n_ties = (int64_t)ties;
     m->rc = rc;
     m->skin = skin;

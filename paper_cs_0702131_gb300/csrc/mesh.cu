@@ -238,6 +238,57 @@ extern "C" aica_status aica_mesh_create(const double *points, int64_t n_points, 
         h_rad32[c] = (float)(h_rad[c] * (1 + 1e-6)) + 1e-6f;
     }
 
+    // ---- molecule-frame origins: consecutive cells whose joint bounding box
+    // stays within twice the median cell extent share one dyadic origin, so
+    // a run of consecutive partner cells is one shift for the pair kernels
+    std::vector<int32_t> h_orgm(3 * n_cells);
+    std::vector<double> h_orgm64(3 * n_cells);
+    {
+        std::vector<double> ext(n_cells);
+        for (int64_t c = 0; c < n_cells; ++c) {
+            double e = 0;
+            for (int d = 0; d < 3; ++d) e = std::max(e, h_hi[3 * c + d] - h_lo[3 * c + d]);
+            ext[c] = e;
+        }
+        std::vector<double> tmp(ext);
+        double emax = 0;
+        if (n_cells > 0) {
+            std::nth_element(tmp.begin(), tmp.begin() + n_cells / 2, tmp.end());
+            emax = 2.0 * tmp[n_cells / 2];
+        }
+        int64_t g0 = 0;
+        double glo_[3], ghi_[3];
+        auto close_group = [&](int64_t g1) {
+            for (int d = 0; d < 3; ++d) {
+                const int32_t k = (int32_t)rint(0.5 * (glo_[d] + ghi_[d]) * 1024.0);
+                for (int64_t c = g0; c < g1; ++c) {
+                    h_orgm[3 * c + d] = k;
+                    h_orgm64[3 * c + d] = (double)k / 1024.0;
+                }
+            }
+        };
+        for (int64_t c = 0; c < n_cells; ++c) {
+            bool join = c > g0 && c - g0 < 64;
+            if (join) {
+                double e = 0;
+                for (int d = 0; d < 3; ++d)
+                    e = std::max(e, std::max(ghi_[d], h_hi[3 * c + d]) - std::min(glo_[d], h_lo[3 * c + d]));
+                join = e <= emax;
+            }
+            if (!join) {
+                if (c > 0) close_group(c);
+                g0 = c;
+                for (int d = 0; d < 3; ++d) { glo_[d] = h_lo[3 * c + d]; ghi_[d] = h_hi[3 * c + d]; }
+            } else {
+                for (int d = 0; d < 3; ++d) {
+                    glo_[d] = std::min(glo_[d], h_lo[3 * c + d]);
+                    ghi_[d] = std::max(ghi_[d], h_hi[3 * c + d]);
+                }
+            }
+        }
+        if (n_cells > 0) close_group(n_cells);
+    }
+
     // ---- point-location bucket grid over the mesh bounding box
     double glo[3], ghi[3];
     for (int d = 0; d < 3; ++d) {
@@ -337,6 +388,8 @@ extern "C" aica_status aica_mesh_create(const double *points, int64_t n_points, 
     if (e == cudaSuccess) e = upload(m->hi, h_hi);
     if (e == cudaSuccess) e = upload(m->org, h_org);
     if (e == cudaSuccess) e = upload(m->orgk, h_orgk);
+    if (e == cudaSuccess) e = upload(m->orgm, h_orgm);
+    if (e == cudaSuccess) e = upload(m->orgm64, h_orgm64);
     if (e == cudaSuccess) e = upload(m->tri32, h_tri32);
     if (e == cudaSuccess) e = upload(m->vtx32, h_vtx32);
     if (e == cudaSuccess) e = upload(m->edg32, h_edg32);
@@ -364,8 +417,8 @@ extern "C" aica_status aica_mesh_create(const double *points, int64_t n_points, 
 extern "C" void aica_mesh_destroy(aica_mesh *m) {
     if (!m) return;
     aica::DevBuf *bufs[] = {&m->tri_off, &m->tri, &m->vtx_off, &m->vtx, &m->edg_off, &m->edg, &m->ctr, &m->rad,
-                            &m->lo, &m->hi, &m->org, &m->ntri, &m->orgk, &m->tri32, &m->vtx32, &m->edg32, &m->ctr32, &m->rad32, &m->box32, &m->bkt_off, &m->bkt_cells, &m->nbr_off, &m->nbr, &m->dil_off,
-                            &m->dil_ids, &m->ref_src, &m->ref_n, &m->ref_off, &m->ref_ids, &m->work_off,
+                            &m->lo, &m->hi, &m->org, &m->ntri, &m->orgk, &m->orgm, &m->orgm64, &m->tri32, &m->vtx32, &m->edg32, &m->ctr32, &m->rad32, &m->box32, &m->bkt_off, &m->bkt_cells, &m->nbr_off, &m->nbr, &m->dil_off,
+                            &m->dil_ids, &m->ref_src, &m->ref_n, &m->ref_off, &m->ref_ids, &m->run_off, &m->runs, &m->work_off,
                             &m->work, &m->work_split, &m->proc_order, &m->cell_of, &m->order,
                             &m->cell_off, &m->fill, &m->inv, &m->sph, &m->xloc, &m->xs64, &m->scratch_i32, &m->facc,
                             &m->vsorted, &m->acc, &m->flags, &m->params, &m->tmp};

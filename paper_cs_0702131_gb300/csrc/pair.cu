@@ -61,7 +61,9 @@ struct PairArgs {
     int C;
     const int *cell_off, *work_off;
     const WorkEntry *work;
-    const int *orgk;             // cell origins in units of 2^-10
+    const int *run_off;
+    const RunEntry *runs;
+    const int *orgm;             // molecule-frame origins in units of 2^-10
     float Lhi[3], Llo[3];        // box lengths as float pairs (Lhi + Llo = L to ~1e-14)
     const float4 *xloc;
     const double *xs64;
@@ -149,7 +151,7 @@ __global__ void __launch_bounds__(15 * 32) finish_sums(double *acc, double *ev, 
 // against it exactly for image pairs (Sterbenz), leaving one rounding for
 // the n.Llo term.
 __device__ __forceinline__ float3 cell_shift(const PairArgs &a, const int *oI, int J, int np) {
-    const int *oJ = a.orgk + 3 * J;
+    const int *oJ = a.orgm + 3 * J;
     float3 d;
     const float nx = (float)unpack_n(np, 0), ny = (float)unpack_n(np, 1), nz = (float)unpack_n(np, 2);
     d.x = fmaf(nx, a.Lhi[0], (float)(oJ[0] - oI[0]) * (1.0f / 1024.0f)) + nx * a.Llo[0];
@@ -323,9 +325,9 @@ __global__ void __launch_bounds__(kThreads32, MINB) pair_fwd32(PairArgs a) {
         for (int I = I0; I < Iend; ++I) {
             const int s0 = a.cell_off[I], nI = a.cell_off[I + 1] - s0;
             if (nI == 0) continue;
-            const int e0 = a.work_off[I], e1 = a.work_off[I + 1];
+            const int e0 = a.run_off[I], e1 = a.run_off[I + 1];
             const float4 sI = a.sph[I];
-            const int *oI = a.orgk + 3 * I;
+            const int *oI = a.orgm + 3 * I;
             const float cull_i = (rcut + sI.w) * (rcut + sI.w) * 1.00002f + 1e-5f;
             for (int i0 = 0; i0 < nI; i0 += NI_) {
                 const int ni = min(NI_, nI - i0), k0 = s0 + i0;
@@ -381,28 +383,34 @@ __global__ void __launch_bounds__(kThreads32, MINB) pair_fwd32(PairArgs a) {
                     const bool alive = li < nI;
                     push(alive, alive ? a.xloc[s0 + li] : far, s0 + li, kSameCell);
                 }
-                // schedule entries, 32 per batch
-                WorkEntry we = e0 + lane < e1 ? a.work[e0 + lane] : WorkEntry{0, 0};
+                // schedule runs, 32 per batch: a run's partner cells are
+                // consecutive, so their molecules are one binned range
+                RunEntry we = e0 + lane < e1 ? a.runs[e0 + lane] : RunEntry{0, 0};
                 for (int eb = e0; eb < e1; eb += 32) {
-                    const WorkEntry cur = we;
+                    const RunEntry cur = we;
                     const bool has = eb + lane < e1;
-                    if (eb + 32 + lane < e1) we = a.work[eb + 32 + lane];
+                    if (eb + 32 + lane < e1) we = a.runs[eb + 32 + lane];
+                    const int np = cur.n & 0xffffff, len = ((unsigned)cur.n >> 24) + 1;
                     int js = 0, n = 0, nall = 0;
+                    bool tested = false;
                     float3 d = make_float3(0.f, 0.f, 0.f);
                     if (has) {
                         js = a.cell_off[cur.j];
-                        nall = n = a.cell_off[cur.j + 1] - js;
+                        nall = n = a.cell_off[cur.j + len] - js;
                         if (n > 0) {
-                            d = cell_shift(a, oI, cur.j, cur.n);
-                            const float4 sJ = a.sph[cur.j];
-                            const float dx = sJ.x + d.x - sI.x, dy = sJ.y + d.y - sI.y, dz = sJ.z + d.z - sI.z;
-                            const float R = rcut + sI.w + sJ.w;
-                            if (dx * dx + dy * dy + dz * dz > R * R * 1.00002f + 1e-5f) n = 0;
+                            d = cell_shift(a, oI, cur.j, np);
+                            if (len == 1) {      // one partner cell: its sphere may rule it out
+                                const float4 sJ = a.sph[cur.j];
+                                const float dx = sJ.x + d.x - sI.x, dy = sJ.y + d.y - sI.y, dz = sJ.z + d.z - sI.z;
+                                const float R = rcut + sI.w + sJ.w;
+                                tested = true;
+                                if (dx * dx + dy * dy + dz * dz > R * R * 1.00002f + 1e-5f) n = 0;
+                            }
                         }
                     }
-                    const unsigned ev_d = __reduce_add_sync(FULL, cur.n == 0 ? (unsigned)(nall * ni) : 0u);
-                    const unsigned ev_r = __reduce_add_sync(FULL, cur.n != 0 ? (unsigned)(nall * ni) : 0u);
-                    const unsigned ncull = __popc(__ballot_sync(FULL, nall > 0));
+                    const unsigned ev_d = __reduce_add_sync(FULL, np == 0 ? (unsigned)(nall * ni) : 0u);
+                    const unsigned ev_r = __reduce_add_sync(FULL, np != 0 ? (unsigned)(nall * ni) : 0u);
+                    const unsigned ncull = __popc(__ballot_sync(FULL, tested));
                     int inc = n;
 #pragma unroll
                     for (int o = 1; o < 32; o <<= 1) {
@@ -414,7 +422,7 @@ __global__ void __launch_bounds__(kThreads32, MINB) pair_fwd32(PairArgs a) {
                     const unsigned lbal = __ballot_sync(FULL, live);
                     if (live) {
                         const int s = __popc(lbal & lt);
-                        w.ed[s] = make_float4(d.x, d.y, d.z, __int_as_float(cur.n));
+                        w.ed[s] = make_float4(d.x, d.y, d.z, __int_as_float(np));
                         w.eb[s] = js - (inc - n);
                     }
                     if (lane == 0) {
@@ -619,7 +627,7 @@ __global__ void __launch_bounds__(kPairThreads) pair_fwd64(PairArgs a) {
                     if (n > 0) {
                         if (np != 0) eval[2] += (unsigned)(n * ni);
                         else eval[1] += (unsigned)(n * ni);
-                        const float3 s3 = cell_shift(a, a.orgk + 3 * I, we.j, np);
+                        const float3 s3 = cell_shift(a, a.orgm + 3 * I, we.j, np);
                         d = make_float4(s3.x, s3.y, s3.z, 0.f);
                         float4 sJ = a.sph[we.j];
                         float dx = sJ.x + d.x - sI4.x, dy = sJ.y + d.y - sI4.y, dz = sJ.z + d.z - sI4.z;
@@ -834,7 +842,7 @@ __global__ void __launch_bounds__(kPairThreads) pair_bwd(BwdArgs b) {
                 WorkEntry we = a.work[e];
                 J = we.j;
                 np = we.n;
-                const float3 s3 = cell_shift(a, a.orgk + 3 * I, J, np);
+                const float3 s3 = cell_shift(a, a.orgm + 3 * I, J, np);
                 d = make_float4(s3.x, s3.y, s3.z, 0.f);
             }
             const int sJ = a.cell_off[J], nJ = a.cell_off[J + 1] - sJ;
@@ -943,7 +951,9 @@ void fill_common(aica_mesh *m, PairArgs &a) {
     a.cell_off = m->cell_off.as<int>();
     a.work_off = m->work_off.as<int>();
     a.work = m->work.as<WorkEntry>();
-    a.orgk = m->orgk.as<int>();
+    a.orgm = m->orgm.as<int>();
+    a.run_off = m->run_off.as<int>();
+    a.runs = m->runs.as<RunEntry>();
     for (int d = 0; d < 3; ++d) {
         double L = m->box.periodic[d] ? m->box.L[d] : 0.0;
         a.Lhi[d] = (float)L;
