@@ -19,24 +19,29 @@
 // skipped.  The counters still report every pair of every scheduled cell pair
 // as "evaluated".
 //
-// FP32 layout.  One warp walks one cell I at a time; up to NI molecules of I
-// (4 for cells of a few molecules, 8 otherwise) sit in registers.  Partner
-// molecules are expanded from the cell ranges of 32 schedule entries at a
-// time (warp scan + binary search), culled, and compacted into a per-warp
-// shared-memory queue; each batch of 32 queued partners is evaluated with one
-// partner per lane against all molecules of the chunk (branch-free pair body).
-// A lane sums its partner's reaction in registers and adds it with one vector
-// atomic; forces on I's molecules are summed over the warp once per chunk.
+// FP32 layout.  A persistent grid of 4-warp blocks; warps claim cells from
+// a global counter.  The chunk (up to NI molecules of I: 4 for cells of a
+// few molecules, 8 otherwise) sits in shared memory.  The FP32 schedule is
+// kept in runs: consecutive partner cells under one image vector and one
+// molecule-frame origin are one contiguous range of binned molecules under
+// one shift.  32 runs at a time are culled, compacted (ballot), and their
+// molecules indexed by a ballot/redux map from candidate position to run;
+// candidates that survive the sphere test go to a per-warp ring in shared
+// memory, and each 32 queued partners are evaluated one partner per lane
+// against the chunk (branch-free pair body).  A lane sums its partner's
+// reaction in registers and adds it with one vector atomic; the chunk's
+// forces are summed over the warp by recursive halving.
 //
-// Precision (FP32 path).  Coordinates are cell-local (dyadic cell origins,
-// so o_J - o_I is exact in FP32).  Pairs whose FP32 r^2 falls within 1e-5
-// rc^2 of the cut-off are re-decided in FP64 exactly as the all-pairs
-// definition computes r^2, so the pair set within rc is the same as in FP64.
-// The virial sum over pairs of r (x) f is accumulated as
-// sum_k x_k (x) F_k + sum_l x_l (x) F_l over the forces each warp adds (both
-// in I's frame; every pair contributes f and -f, so the origin cancels).
-// Energy and virial are summed per lane in FP32 over at most four cells, then
-// in FP64 per warp; a finalize kernel adds the warps.
+// Precision (FP32 path).  Coordinates are local to dyadic origins shared by
+// groups of consecutive cells of bounded extent (o_J - o_I exact in FP32).
+// Pairs whose FP32 r^2 falls within 1e-5 rc^2 of the cut-off are re-decided
+// in FP64 exactly as the all-pairs definition computes r^2, so the pair set
+// within rc is the same as in FP64.  The virial sum over pairs of r (x) f is
+// accumulated as sum_k x_k (x) F_k + sum_l x_l (x) F_l over the forces each
+// warp adds (both in I's frame; every pair contributes f and -f, so the
+// origin cancels).  Energy and virial are summed per lane in FP32 over at
+// most four cells, then in FP64 per warp; warps add their totals to striped
+// FP64 rows that a small kernel sums.
 #include <math.h>
 #include <string.h>
 
