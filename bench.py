@@ -17,6 +17,8 @@ from __future__ import annotations
 
 import argparse
 import json
+
+import numpy as np
 import os
 import statistics
 import subprocess
@@ -47,6 +49,9 @@ def parse():
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--fp64-steps", type=int, default=0, help="timed FP64 steps (default steps/10)")
     p.add_argument("--no-extras", action="store_true", help="skip FP64, e2e, accuracy and CPU legs")
+    p.add_argument("--study", choices=["cost", "vertex"], default=None,
+                   help="instead of the step: the cost-versus-mesh-size study of §2.4 (cost) or the "
+                        "vertex-vertex list criterion of §2.2 against the minimum distance (vertex)")
     return p.parse_args()
 
 
@@ -577,9 +582,103 @@ def run_reference(args):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def n_c(x):
+    """§2.4: cubes of a uniform cubic mesh with a corner within x = rc/w of a
+    corner of the central cube, the central cube included (exact count)."""
+    k = int(np.ceil(x)) + 1
+    r = np.arange(-k, k + 1)
+    I, J, K = np.meshgrid(r, r, r, indexing="ij")
+    g = lambda t: np.maximum(np.abs(t) - 1, 0)
+    return int(((g(I) ** 2 + g(J) ** 2 + g(K) ** 2) < x * x).sum())
+
+
+def _pairs_and_kernel(mesh, cfg, pos, sp, prec="fp32", reps=20):
+    import torch
+    mesh.bin(pos, sp, outputs=False)
+    F, ev, cnt = mesh.forces(cfg["eps"], cfg["sigma"], prec)
+    mesh.set_kernel_timing(True)
+    for _ in range(reps):
+        mesh.forces(cfg["eps"], cfg["sigma"], prec)
+    kms = [float(x) for x in mesh.take_kernel_times()]
+    mesh.set_kernel_timing(False)
+    torch.cuda.synchronize()
+    return F, ev.cpu().numpy(), cnt.cpu().numpy(), statistics.median(kms)
+
+
+def run_study(args):
+    """Studies of the paper's analysis on this GPU (one JSON line)."""
+    import numpy as np
+    import torch
+    from paper_cs_0702131_gb300 import synth
+    from paper_cs_0702131_gb300.aica import Mesh
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    rows = []
+    if args.study == "cost":
+        # uniform cubic meshes over one FCC fluid: evaluated / within-rc pairs
+        # against V_AICA / V_ideal = N_c(rc/w) w^3 / (4/3 pi rc^3) (§2.4)
+        rc, nf = 2.5, 24
+        rng = np.random.default_rng(args.seed)
+        a = synth.A_FCC_08
+        L = nf * a
+        box = dict(L=np.array([L, L, L]), periodic=np.array([1, 1, 1], np.int32))
+        posn = synth.wrap(synth.jitter(synth.fcc_sites(nf, nf, nf, a), 0.05, rng), box["L"], box["periodic"])
+        cfg = dict(eps=np.array([1.0]), sigma=np.array([1.0]))
+        pos = torch.tensor(posn, dtype=torch.float64, device=dev)
+        sp = torch.zeros(len(posn), dtype=torch.int32, device=dev)
+        for nh in (16, 20, 27, 33, 41, 55, 66):
+            w = L / nh
+            mesh = Mesh(synth.hex_mesh((nh,) * 3, (0, 0, 0), (L, L, L), 0.0, np.random.default_rng(0)), box)
+            mesh.build_lists(rc, 0.0)
+            _, ev, c, kms = _pairs_and_kernel(mesh, cfg, pos, sp)
+            within = int(c[3] + c[4] + c[5])
+            evaluated = int(c[0] + c[1] + c[2])
+            v_aica = n_c(rc / w) * w ** 3 / (4.0 / 3.0 * np.pi * rc ** 3)
+            rows.append({"w_over_rc": round(w / rc, 4), "cells": nh ** 3, "N_c": n_c(rc / w),
+                         "evaluated_over_within": round(evaluated / within, 4),
+                         "V_AICA_over_V_ideal": round(v_aica, 4),
+                         "pair_tests_over_within": round(int(mesh.last_stats()[0]) / within, 4),
+                         "kernel_ms": round(kms, 4), "ns_per_pair": round(kms * 1e6 / within, 4)})
+            mesh.close()
+        out = {"study": "cost", "what": ("evaluated/within-rc pairs on uniform cubic meshes vs V_AICA/V_ideal "
+                                          "(§2.4); CCA would be 27 rc^3 / V_ideal = 6.45"),
+               "molecules": len(posn), "rc": rc, "rows": rows}
+    else:
+        # the paper's vertex-vertex criterion against the minimum distance on
+        # jittered meshes: pairs within rc it misses, and the error they make
+        for name in ("t0", "c1", "c4", "c2"):
+            cfg = synth.make(name, args.seed)
+            pos = torch.tensor(cfg["pos"], dtype=torch.float64, device=dev)
+            sp = torch.tensor(cfg["species"], dtype=torch.int32, device=dev)
+            mesh = Mesh(cfg["mesh"], cfg["box"])
+            mesh.build_lists(cfg["rc"], 0.0)
+            F0, ev0, c0, k0 = _pairs_and_kernel(mesh, cfg, pos, sp, "fp64", reps=3)
+            F0 = F0.cpu().numpy()
+            within0 = int(c0[3] + c0[4] + c0[5])
+            scale = np.abs(F0).max()
+            for skin in (0.0, 0.1, 0.25, 0.5):
+                mesh.build_lists(cfg["rc"], skin, criterion="vertex")
+                F, ev, c, _ = _pairs_and_kernel(mesh, cfg, pos, sp, "fp64", reps=3)
+                within = int(c[3] + c[4] + c[5])
+                rows.append({"config": name, "cells": cfg["mesh"]["n_cells"], "skin": skin,
+                             "pairs_within_rc": within0, "missed_pairs": within0 - within,
+                             "missed_fraction": (within0 - within) / within0,
+                             "evaluated_vertex_over_min_distance": round(int(c[0] + c[1] + c[2]) /
+                                                                         int(c0[0] + c0[1] + c0[2]), 4),
+                             "max_force_error_rel_max_force": float(np.abs(F.cpu().numpy() - F0).max() / scale),
+                             "energy_error_rel": float(abs(ev[0] - ev0[0]) / abs(ev0[0]))})
+            mesh.close()
+        out = {"study": "vertex", "what": ("vertex-vertex DIL criterion (§2.2, App. A.1) vs exact minimum "
+                                            "distance, FP64 path, rc as configured"), "rows": rows}
+    return out
+
+
 def main():
     args = parse()
-    out = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if args.study:
+        out = run_study(args)
+    else:
+        out = run_reference(args) if args.impl == "reference" else run_ours(args)
     if out is not None:
         print(json.dumps(out, default=lambda o: o.item() if hasattr(o, "item") else str(o)), flush=True)
 

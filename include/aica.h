@@ -73,6 +73,7 @@ typedef struct {
     int64_t n_ref_ids;  /* entries of all referred-cell real-cell lists    */
     int64_t n_ties;     /* cell-pair decisions within 1e-9 (rc+skin)^2     */
     double rc, skin;
+    int32_t criterion;  /* aica_dil_criterion the lists were built with     */
 } aica_list_info;
 
 /* Create a mesh from a face-based description (OpenFOAM style).  Defines the
@@ -108,6 +109,24 @@ void aica_mesh_destroy(aica_mesh *mesh);
  * skin >= 0 and rc + skin < L/2 on periodic axes.  Runs on `stream` and
  * synchronizes it before returning (the list sizes are needed on the host). */
 aica_status aica_build_interaction_list(aica_mesh *mesh, double rc, double skin, void *stream);
+
+/* Criterion that lists a cell pair. */
+typedef enum {
+    AICA_DIL_MIN_DISTANCE = 0,   /* minimum distance between the polyhedra (default) */
+    AICA_DIL_VERTEX = 1          /* the paper's own search (§2.2, App. A.1): some vertex
+                                    of one cell within rc + skin of a vertex of the
+                                    other; can miss pairs of twisted cells (§2.2) */
+} aica_dil_criterion;
+
+/* aica_build_interaction_list with a choice of criterion (same lists, same
+ * arguments and behaviour for AICA_DIL_MIN_DISTANCE).  With AICA_DIL_VERTEX
+ * the DILs and referred cells are those of the paper's vertex-vertex search,
+ * decided in FP64 with the same tie report; aica_forces then evaluates the
+ * pairs of those lists, which may omit pairs within rc (the twisted-mesh
+ * error of §2.2, reduced by a skin: the paper's guard distance).  An unknown
+ * criterion -> AICA_ERR_INVALID_ARG. */
+aica_status aica_build_interaction_list_ex(aica_mesh *mesh, double rc, double skin,
+                                           aica_dil_criterion criterion, void *stream);
 
 /* Sizes of the current lists (host struct).  AICA_ERR_NOT_BUILT before a build. */
 aica_status aica_get_list_info(const aica_mesh *mesh, aica_list_info *info);

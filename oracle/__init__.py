@@ -62,7 +62,7 @@ def lib():
         L.oracle_lj.argtypes = [ctypes.c_int64, _f64, _i32, ctypes.c_int, _f64, _f64, ctypes.c_double, _f64,
                                 _i32, ctypes.c_int, vp, ctypes.c_int64, _f64, _f64, _f64, _f64, _i64]
         L.oracle_cell_pairs.argtypes = [_i64, _f64, _i64, _f64, _i64, _f64, _f64, _f64, ctypes.c_int64, _i64,
-                                        ctypes.c_int64, ctypes.c_double, _i32, _f64, ctypes.c_int,
+                                        ctypes.c_int64, ctypes.c_double, _i32, _f64, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_int64, _i64, _i32, _i32, _f64, _i64]
         L.oracle_locate.argtypes = [_i64, _f64, _f64, _f64, ctypes.c_int64, _f64, ctypes.c_int64, _f64, _i32,
                                     _i32, _f64]
@@ -204,11 +204,16 @@ def image_range(thr, box):
     return np.array([int(np.ceil(thr / box["L"][d])) if box["periodic"][d] else 0 for d in range(3)], np.int32)
 
 
-def cell_pairs(geo, box, thr, queries=None, use_bound=True, cap=8192):
+def cell_pairs(geo, box, thr, queries=None, use_bound=True, cap=8192, criterion="min_distance"):
     """Every (A, B, n) with min_dist(A, B + n.L) < thr for the query cells A.
 
-    Returns (A, B, n [k,3], d2, ties).  Brute force over all cells and images.
+    With criterion="vertex" the distance is the paper's vertex-vertex one
+    (§2.2, App. A.1) instead of the exact minimum distance between the
+    polyhedra.  Returns (A, B, n [k,3], d2, ties).  Brute force over all cells
+    and images.
     """
+    if criterion not in ("min_distance", "vertex"):
+        raise ValueError(criterion)
     C = geo["n_cells"]
     q = np.arange(C, dtype=np.int64) if queries is None else _c(queries, np.int64)
     nq = q.shape[0]
@@ -220,7 +225,7 @@ def cell_pairs(geo, box, thr, queries=None, use_bound=True, cap=8192):
     outD = np.zeros(nq * cap, np.float64)
     lib().oracle_cell_pairs(geo["tri_off"], geo["tri"], geo["vtx_off"], geo["vtx"], geo["edg_off"], geo["edg"],
                             geo["ctr"], geo["rad"], C, q, nq, float(thr), m, _c(box["L"], np.float64),
-                            int(use_bound), cap, cnt, outB, outN, outD, ties)
+                            int(use_bound), int(criterion == "vertex"), cap, cnt, outB, outN, outD, ties)
     if np.any(cnt < 0):
         raise RuntimeError("oracle_cell_pairs: capacity exceeded")
     sel = np.concatenate([np.arange(i * cap, i * cap + cnt[i]) for i in range(nq)]) if nq else np.zeros(0, int)
@@ -228,7 +233,7 @@ def cell_pairs(geo, box, thr, queries=None, use_bound=True, cap=8192):
     return A, outB[sel].astype(np.int64), outN.reshape(-1, 3)[sel].astype(np.int64), outD[sel], int(ties.sum())
 
 
-def cell_lists(mesh, box, rc, skin, queries=None, geo=None, use_bound=True):
+def cell_lists(mesh, box, rc, skin, queries=None, geo=None, use_bound=True, criterion="min_distance"):
     """Direct interaction lists and periodic referred cells.
 
     DIL(i) = ascending {j > i : min_dist(i, j) < rc + skin} (§2.2, App. A.1).
@@ -238,11 +243,12 @@ def cell_lists(mesh, box, rc, skin, queries=None, geo=None, use_bound=True):
     c's side: min_dist(J, c + n.L) = min_dist(c, J - n.L).
 
     With ``queries`` the lists cover only those cells (as DIL owners and as
-    referred-cell sources).  Returns a dict of CSR arrays and ``ties``.
+    referred-cell sources).  criterion="vertex" replaces min_dist by the
+    paper's vertex-vertex distance.  Returns a dict of CSR arrays and ``ties``.
     """
     geo = geo or cell_geometry(mesh)
     thr = rc + skin
-    A, B, N, _, ties = cell_pairs(geo, box, thr, queries, use_bound)
+    A, B, N, _, ties = cell_pairs(geo, box, thr, queries, use_bound, criterion=criterion)
     C = geo["n_cells"]
     cells = np.arange(C) if queries is None else np.asarray(queries, np.int64)
     zero = ~N.any(axis=1)

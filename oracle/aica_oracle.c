@@ -13,7 +13,8 @@
  *                        definition the method reaches, see §2.3)
  *   oracle_cell_pairs    brute-force cell-cell minimum distance between
  *                        triangulated polyhedra, all periodic images (§2.2,
- *                        App. A.1, with the exact-distance criterion)
+ *                        App. A.1, with the exact-distance criterion), or the
+ *                        paper's vertex-vertex distance
  *   oracle_locate        point location by ray parity with a symbolic
  *                        perturbation tie-break, FP64 with an error filter;
  *                        uncertain cases are flagged for exact resolution
@@ -237,11 +238,28 @@ static double cell_d2(const cellgeo *g, int64_t A, int64_t B, v3 sB)
  * bounds the distance from ctr_c to every vertex of c; every point of a cell
  * lies in the convex hull of its vertices, so this bound never drops a pair.
  * ties[q] counts decisions with |d^2 - thr^2| <= 1e-9 thr^2. */
+/* The paper's own criterion (§2.2, App. A.1): the smallest distance between a
+ * vertex of A and a vertex of B (B shifted by sB). */
+static double cell_vertex_d2(const cellgeo *g, int64_t A, int64_t B, v3 sB)
+{
+    double best = INFINITY, t;
+    for (int64_t i = g->vtx_off[A]; i < g->vtx_off[A + 1]; ++i) {
+        v3 p = ld(g->vtx + 3 * i);
+        for (int64_t j = g->vtx_off[B]; j < g->vtx_off[B + 1]; ++j) {
+            v3 d = sub(p, ldsh(g->vtx + 3 * j, sB));
+            if ((t = dot(d, d)) < best) best = t;
+        }
+    }
+    return best;
+}
+
+/* vertex_only selects the vertex-vertex criterion instead of the exact
+ * minimum distance between the polyhedra. */
 void oracle_cell_pairs(const int64_t *tri_off, const double *tri, const int64_t *vtx_off,
                        const double *vtx, const int64_t *edg_off, const double *edg,
                        const double *ctr, const double *rad, int64_t n_cells,
                        const int64_t *query, int64_t nq, double thr, const int32_t *m,
-                       const double *L, int use_bound, int64_t cap, int64_t *count,
+                       const double *L, int use_bound, int vertex_only, int64_t cap, int64_t *count,
                        int32_t *outB, int32_t *outN, double *outD2, int64_t *ties)
 {
     cellgeo g = {tri_off, vtx_off, edg_off, tri, vtx, edg};
@@ -262,7 +280,7 @@ void oracle_cell_pairs(const int64_t *tri_off, const double *tri, const int64_t 
                             double lb = sqrt(dot(dc, dc)) - rad[A] - rad[B];
                             if (lb > thr * (1 + 1e-9) + 1e-9) continue;
                         }
-                        double d2 = cell_d2(&g, A, B, s);
+                        double d2 = vertex_only ? cell_vertex_d2(&g, A, B, s) : cell_d2(&g, A, B, s);
                         if (fabs(d2 - thr2) <= 1e-9 * thr2) nt++;
                         if (d2 < thr2) {
                             if (c < cap) {

@@ -46,7 +46,7 @@ class LJ(ctypes.Structure):
 class ListInfo(ctypes.Structure):
     _fields_ = [("n_cells", ctypes.c_int64), ("n_dil", ctypes.c_int64), ("n_ref", ctypes.c_int64),
                 ("n_ref_ids", ctypes.c_int64), ("n_ties", ctypes.c_int64), ("rc", ctypes.c_double),
-                ("skin", ctypes.c_double)]
+                ("skin", ctypes.c_double), ("criterion", ctypes.c_int32)]
 
 
 #: every entry point of include/aica.h with its ctypes signature
@@ -55,6 +55,8 @@ SIGNATURES = {
                                         ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                         ctypes.POINTER(Box), ctypes.POINTER(ctypes.c_void_p)]),
     "aica_mesh_destroy": (None, [ctypes.c_void_p]),
+    "aica_build_interaction_list_ex": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
+                                                      ctypes.c_int, ctypes.c_void_p]),
     "aica_build_interaction_list": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
                                                    ctypes.c_void_p]),
     "aica_get_list_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ListInfo)]),
@@ -150,8 +152,17 @@ def aica_mesh_destroy(h):
     lib().aica_mesh_destroy(h)
 
 
+AICA_DIL_MIN_DISTANCE, AICA_DIL_VERTEX = 0, 1
+_CRITERIA = {"min_distance": AICA_DIL_MIN_DISTANCE, "vertex": AICA_DIL_VERTEX}
+
+
 def aica_build_interaction_list(h, rc, skin=1e-3):
     _check(lib().aica_build_interaction_list(h, float(rc), float(skin), _stream()))
+
+
+def aica_build_interaction_list_ex(h, rc, skin=1e-3, criterion="min_distance"):
+    """criterion: "min_distance" (default) or "vertex" (the paper's vertex-vertex search)."""
+    _check(lib().aica_build_interaction_list_ex(h, float(rc), float(skin), _CRITERIA[criterion], _stream()))
 
 
 def aica_get_list_info(h):
@@ -278,8 +289,11 @@ class Mesh:
         except Exception:
             pass
 
-    def build_lists(self, rc, skin=1e-3):
-        aica_build_interaction_list(self.h, rc, skin)
+    def build_lists(self, rc, skin=1e-3, criterion="min_distance"):
+        if criterion == "min_distance":
+            aica_build_interaction_list(self.h, rc, skin)
+        else:
+            aica_build_interaction_list_ex(self.h, rc, skin, criterion)
         self.rc = float(rc)
 
     def lists(self):

@@ -114,6 +114,7 @@ struct aica_mesh {
     // Interaction lists (device), valid when built.
     bool built = false;
     double rc = 0, skin = 0;
+    int criterion = 0;                       // aica_dil_criterion of the built lists
     int64_t n_dil = 0, n_ref = 0, n_ref_ids = 0, n_ties = 0, n_work = 0, n_runs = 0;
     aica::DevBuf dil_off, dil_ids, ref_src, ref_n, ref_off, ref_ids;   // int32 (ref_n: 3 int32)
     aica::DevBuf run_off, runs;              // [C+1] int32 first run of each cell; RunEntry

@@ -3,9 +3,10 @@
 // App. A.2), plus the per-cell pair schedule the force kernels walk.
 //
 // The paper builds DILs by a vertex-vertex search and notes it can miss
-// slivers of twisted cells (§2.2); here a cell pair is listed iff the exact
-// minimum distance between the two closed triangulated polyhedra is below
-// rc + skin.  The paper's iterated referral across patch segments (App. A.2)
+// slivers of twisted cells (§2.2); by default a cell pair is listed iff the
+// exact minimum distance between the two closed triangulated polyhedra is
+// below rc + skin.  The paper's vertex-vertex criterion is available as
+// AICA_DIL_VERTEX (for the comparison of §2.2 and §2.4).  The paper's iterated referral across patch segments (App. A.2)
 // reduces, for a translation-periodic box on one device, to enumerating
 // image vectors n directly: the result does not depend on evaluation order.
 //
@@ -36,6 +37,7 @@ constexpr int kSortMax = 4096;
 
 struct QArgs {
     int C;
+    int vertex_only;      // the paper's vertex-vertex criterion instead of the minimum distance
     double thr2;
     float thr, thr2_lo, thr2_hi;
     double L[3];
@@ -84,6 +86,20 @@ __device__ __noinline__ double min_d2_f64(const QArgs &a, int A, int B, V3<doubl
     return m;
 }
 
+// FP64 smallest vertex-vertex squared distance between cell A and cell B shifted by s.
+__device__ __noinline__ double min_vv_d2_f64(const QArgs &a, int A, int B, V3<double> s) {
+    double m = INFINITY;
+    for (int i = a.vtx_off[A]; i < a.vtx_off[A + 1]; ++i) {
+        const V3<double> p = ldd(a.vtx + 3 * i);
+        for (int j = a.vtx_off[B]; j < a.vtx_off[B + 1]; ++j) {
+            const V3<double> q = ldd(a.vtx + 3 * j) + s;
+            const double dx = __dsub_rn(p.x, q.x), dy = __dsub_rn(p.y, q.y), dz = __dsub_rn(p.z, q.z);
+            m = fmin(m, __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+        }
+    }
+    return m;
+}
+
 struct WarpA {
     const float *T, *V, *E;   // shared: A's triangles, vertices, edges in A's frame
     int nt, nv, ne;
@@ -116,6 +132,13 @@ __device__ __noinline__ int decide(const QArgs &a, const WarpA &w, int A, int B,
             V3<float> d = q - ldf(w.V + 3 * k);
             m = fminf(m, dot3(d, d));
         }
+    }
+    if (a.vertex_only) {
+        if (m < a.thr2_lo) return 1;
+        if (m > a.thr2_hi) return 0;
+        V3<double> s = {nx * a.L[0], ny * a.L[1], nz * a.L[2]};
+        const double d2 = min_vv_d2_f64(a, A, B, s);
+        return (d2 < a.thr2 ? 1 : 0) | (fabs(d2 - a.thr2) <= 1e-9 * a.thr2 ? 2 : 0);
     }
     if (m < a.thr2_lo) return 1;
     float gx = fmaxf(0.f, fmaxf(blo.x - w.hi.x, w.lo.x - bhi.x));
@@ -404,6 +427,15 @@ __global__ void lst_runs(const int *work_off, const WorkEntry *work, const int *
 using namespace aica;
 
 extern "C" aica_status aica_build_interaction_list(aica_mesh *m, double rc, double skin, void *stream) {
+    return aica_build_interaction_list_ex(m, rc, skin, AICA_DIL_MIN_DISTANCE, stream);
+}
+
+extern "C" aica_status aica_build_interaction_list_ex(aica_mesh *m, double rc, double skin,
+                                                      aica_dil_criterion criterion, void *stream) {
+    if (criterion != AICA_DIL_MIN_DISTANCE && criterion != AICA_DIL_VERTEX) {
+        set_error("aica_build_interaction_list_ex: unknown criterion %d", (int)criterion);
+        return AICA_ERR_INVALID_ARG;
+    }
     if (!m) { set_error("aica_build_interaction_list: mesh is NULL"); return AICA_ERR_INVALID_ARG; }
     if (!(rc > 0) || !(skin >= 0) || !isfinite(rc + skin)) {
         set_error("aica_build_interaction_list: need rc > 0 and skin >= 0");
@@ -481,6 +513,7 @@ extern "C" aica_status aica_build_interaction_list(aica_mesh *m, double rc, doub
     CK(cudaMemsetAsync(m->flags.p, 0, 16, st));
 
     a.C = C;
+    a.vertex_only = criterion == AICA_DIL_VERTEX ? 1 : 0;
     a.thr = (float)thr;
     a.thr2 = thr * thr;
     a.thr2_lo = (float)(a.thr2 * (1 - 1e-3));
@@ -592,6 +625,7 @@ extern "C" aica_status aica_build_interaction_list(aica_mesh *m, double rc, doub
     m->n_ties = (int64_t)ties;
     m->rc = rc;
     m->skin = skin;
+    m->criterion = (int)criterion;
     m->built = true;
     return AICA_OK;
 }
@@ -606,6 +640,7 @@ extern "C" aica_status aica_get_list_info(const aica_mesh *m, aica_list_info *in
     info->n_ties = m->n_ties;
     info->rc = m->rc;
     info->skin = m->skin;
+    info->criterion = (aica_dil_criterion)m->criterion;
     return AICA_OK;
 }
 

@@ -51,3 +51,10 @@ def test_reference_arm_other_ranks_exit_quietly(monkeypatch):
     monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--config", "t0", "--steps", "1",
                                       "--warmup", "0"])
     assert bench.run_reference(bench.parse()) is None
+
+
+def test_cost_study_n_c_matches_golden(golden):
+    """bench.n_c (the §2.4 count used by --study cost) equals the pinned N_c values."""
+    import bench
+    for x, n in golden["N_c"].items():
+        assert bench.n_c(float(x)) == n

@@ -146,17 +146,24 @@ def test_list_invariants():
     assert keys == sorted(keys) and len(set(keys)) == len(keys)
 
 
-def test_min_distance_lists_contain_vertex_rule_lists():
-    """Cells with a vertex pair closer than rc + skin are always listed (d_min <= that distance)."""
+def test_vertex_rule_lists_equal_brute_force_and_are_contained():
+    """The oracle's vertex-vertex criterion (§2.2, App. A.1) lists exactly the
+    (A, B, n) with a vertex pair closer than rc + skin (numpy brute force),
+    and the minimum-distance lists always contain them (d_min <= any vertex
+    distance)."""
     c = synth.make("t0", seed=2)
     geo = oracle.cell_geometry(c["mesh"])
     thr = c["rc"] + c["skin"]
-    A, B, N, _, _ = oracle.cell_pairs(geo, c["box"], thr)
+    rng = np.random.default_rng(0)
+    q = np.sort(rng.choice(geo["n_cells"], 12, replace=False))
+    A, B, N, _, _ = oracle.cell_pairs(geo, c["box"], thr, queries=q)
     listed = set(zip(A.tolist(), B.tolist(), map(tuple, N.tolist())))
+    Av, Bv, Nv, _, _ = oracle.cell_pairs(geo, c["box"], thr, queries=q, criterion="vertex")
+    vertex = set(zip(Av.tolist(), Bv.tolist(), map(tuple, Nv.tolist())))
     V = [geo["vtx"][geo["vtx_off"][i]:geo["vtx_off"][i + 1]] for i in range(geo["n_cells"])]
     L = c["box"]["L"]
-    rng = np.random.default_rng(0)
-    for A0 in rng.choice(geo["n_cells"], 12, replace=False):
+    brute = set()
+    for A0 in q:
         for B0 in range(geo["n_cells"]):
             for n in np.ndindex(3, 3, 3):
                 n = np.array(n) - 1
@@ -164,7 +171,41 @@ def test_min_distance_lists_contain_vertex_rule_lists():
                     continue
                 d = V[A0][:, None, :] - (V[B0][None, :, :] + n * L)
                 if np.sqrt((d * d).sum(-1)).min() < thr:
-                    assert (int(A0), B0, tuple(n)) in listed
+                    brute.add((int(A0), B0, tuple(int(x) for x in n)))
+    assert vertex == brute
+    assert vertex <= listed
+    assert len(vertex) < len(listed)      # on tetrahedra the vertex rule drops cell pairs
+
+
+def _twisted_pair(h=1.0):
+    """Two tetrahedra whose long edges cross at distance h while every vertex
+    pair is farther than 3.8: the slivers of the paper's twisted-mesh figure."""
+    pts = np.array([[-3, 0, 0], [3, 0, 0], [0, -0.5, -2], [0, 0.5, -2],
+                    [0, -3, h], [0, 3, h], [-0.5, 0, h + 2], [0.5, 0, h + 2]], float) + 10.0
+    return synth.cells_to_mesh(pts, np.array([[0, 1, 2, 3], [4, 5, 6, 7]]))
+
+
+def test_vertex_rule_misses_twisted_cells():
+    """§2.2: searching from vertices only can miss interacting slivers; the
+    minimum-distance criterion does not.  Two molecules 1.2 apart across the
+    crossing edges: the AICA loops over the vertex lists miss their pair."""
+    mesh = _twisted_pair()
+    lv = oracle.cell_lists(mesh, OPEN, rc=2.5, skin=0.0, criterion="vertex")
+    lm = oracle.cell_lists(mesh, OPEN, rc=2.5, skin=0.0)
+    assert list(lv["dil_ids"]) == [] and list(lm["dil_ids"]) == [1]
+    geo = oracle.cell_geometry(mesh)
+    pos = np.array([[10.0, 10.0, 9.9], [10.0, 10.0, 11.1]])    # inside cell 0 and cell 1
+    cell, xs = oracle.locate(geo, OPEN, pos)
+    assert list(cell) == [0, 1]
+    sp = np.zeros(2, np.int32)
+    order, off = oracle.bin_order(cell, 2)
+    eps, sig = np.array([1.0]), np.array([1.0])
+    av = oracle.aica_loop(lv, off, xs[order], sp, eps, sig, 2.5, OPEN)
+    am = oracle.aica_loop(lm, off, xs[order], sp, eps, sig, 2.5, OPEN)
+    ref = oracle.lj(pos, sp, eps, sig, 2.5, OPEN)
+    assert ref["pairs"] == 1 and am["counts"][4] == 1 and av["counts"][4] == 0
+    assert np.all(av["F"] == 0.0)
+    np.testing.assert_allclose(am["U"], ref["U"], rtol=1e-12)
 
 
 def test_sampled_queries_equal_full():
