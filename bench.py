@@ -49,9 +49,10 @@ def parse():
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--fp64-steps", type=int, default=0, help="timed FP64 steps (default steps/10)")
     p.add_argument("--no-extras", action="store_true", help="skip FP64, e2e, accuracy and CPU legs")
-    p.add_argument("--study", choices=["cost", "vertex"], default=None,
+    p.add_argument("--study", choices=["cost", "vertex", "nve"], default=None,
                    help="instead of the step: the cost-versus-mesh-size study of §2.4 (cost) or the "
-                        "vertex-vertex list criterion of §2.2 against the minimum distance (vertex)")
+                        "vertex-vertex list criterion of §2.2 against the minimum distance (vertex), or the "
+                        "paper's verification run of §3 on two meshes (nve)")
     return p.parse_args()
 
 
@@ -605,6 +606,79 @@ def _pairs_and_kernel(mesh, cfg, pos, sp, prec="fp32", reps=20):
     return F, ev.cpu().numpy(), cnt.cpu().numpy(), statistics.median(kms)
 
 
+def nve_study(args, steps=2000, dt=0.005, every=20):
+    """§3 verification run: 27 000 LJ molecules from a simple cubic lattice at
+    120 K (T* = 120 / 119.8), no thermostat, velocity Verlet; the same start on
+    jittered hexahedra and on Kuhn tetrahedra, FP64 and FP32 pairs."""
+    import torch
+    from paper_cs_0702131_gb300 import synth
+    from paper_cs_0702131_gb300.aica import Mesh, aica_kinetic
+    dev = torch.device("cuda", 0)
+    rho, nsc, rc, T = 0.8, 30, 2.5, 120.0 / 119.8
+    a = (1.0 / rho) ** (1.0 / 3.0)
+    L = nsc * a
+    box = dict(L=np.array([L, L, L]), periodic=np.array([1, 1, 1], np.int32))
+    g = (np.arange(nsc) + 0.5) * a
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    pos0 = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)
+    n = len(pos0)
+    rng = np.random.default_rng(args.seed + 120)
+    v0 = rng.normal(size=(n, 3))
+    v0 -= v0.mean(0)
+    v0 *= np.sqrt(3.0 * (n - 1) * T / (v0 * v0).sum())
+    eps, sig, mass = np.array([1.0]), np.array([1.0]), [1.0]
+    meshes = {"hex 12^3 jittered": synth.hex_mesh((12, 12, 12), (0, 0, 0), (L, L, L), 0.15, np.random.default_rng(1)),
+              "tet 10^3 x 6 Kuhn": synth.hex_mesh((10, 10, 10), (0, 0, 0), (L, L, L), 0.15, np.random.default_rng(2),
+                                                 tets=True)}
+    runs = {}
+    for prec in ("fp64", "fp32"):
+        for name, mesh_d in meshes.items():
+            m = Mesh(mesh_d, box)
+            m.build_lists(rc, 1e-3)
+            pos = torch.tensor(pos0, dtype=torch.float64, device=dev)
+            vel = torch.tensor(v0, dtype=torch.float64, device=dev)
+            sp = torch.zeros(n, dtype=torch.int32, device=dev)
+            m.bin(pos, sp, outputs=False)
+            F, ev, _ = m.forces(eps, sig, prec, shift=True)
+            kin = torch.empty(4, dtype=torch.float64, device=dev)
+            aica_kinetic(mass, sp, vel, kin)
+            rec = [(0, kin[0].item() / n, ev[0].item() / n, *kin[1:].tolist())]
+            m.set_deferred(True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for i in range(1, steps + 1):
+                m.verlet_step(eps, sig, mass, dt, pos, vel, sp, F, prec=prec, ev=ev, kin=kin, shift=True)
+                if i % every == 0:
+                    rec.append((i, kin[0].item() / n, ev[0].item() / n, *kin[1:].tolist()))
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            m.check()
+            m.close()
+            rec = np.array(rec)
+            te = rec[:, 1] + rec[:, 2]
+            runs[(prec, name)] = rec
+            rows_ = {"precision": prec, "mesh": name, "cells": mesh_d["n_cells"],
+                     "KE_PE_TE_per_molecule_start": [round(rec[0, 1], 6), round(rec[0, 2], 6), round(te[0], 6)],
+                     "KE_PE_TE_per_molecule_end": [round(rec[-1, 1], 6), round(rec[-1, 2], 6), round(te[-1], 6)],
+                     "TE_max_rel_drift": float(np.abs(te - te[0]).max() / abs(te[0])),
+                     "momentum_max_abs": float(np.abs(rec[:, 3:]).max()),
+                     "steps_per_s": steps / wall}
+            runs[(prec, name, "row")] = rows_
+    rows = [v for k, v in runs.items() if len(k) == 3]
+    names = list(meshes)
+    same = {}
+    for prec in ("fp64", "fp32"):
+        a_, b_ = runs[(prec, names[0])], runs[(prec, names[1])]
+        ta, tb = a_[:, 1] + a_[:, 2], b_[:, 1] + b_[:, 2]
+        d = np.abs(ta - tb) / np.abs(ta)
+        same[prec] = {"TE_rel_difference_between_meshes_at_step": {int(a_[j, 0]): float(d[j])
+                                                                   for j in range(0, len(d), len(d) // 10)}}
+    return {"study": "nve", "what": ("27 000 LJ molecules, simple cubic start at rho* = 0.8, T = 120 K (T* = "
+                                      f"{T:.4f}), rc = 2.5, dt = {dt} (reduced), {steps} steps, no thermostat, "
+                                      "velocity Verlet (aica_verlet_step), energy-shifted potential"),
+            "rows": rows, "mesh_independence": same}
+
+
 def run_study(args):
     """Studies of the paper's analysis on this GPU (one JSON line)."""
     import numpy as np
@@ -643,6 +717,8 @@ def run_study(args):
         out = {"study": "cost", "what": ("evaluated/within-rc pairs on uniform cubic meshes vs V_AICA/V_ideal "
                                           "(§2.4); CCA would be 27 rc^3 / V_ideal = 6.45"),
                "molecules": len(posn), "rc": rc, "rows": rows}
+    elif args.study == "nve":
+        out = nve_study(args)
     else:
         # the paper's vertex-vertex criterion against the minimum distance on
         # jittered meshes: pairs within rc it misses, and the error they make

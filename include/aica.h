@@ -193,6 +193,35 @@ aica_status aica_forces_backward(aica_mesh *mesh, const aica_lj *lj, aica_precis
                                  const void *grad_force, void *grad_pos, double *grad_eps,
                                  double *grad_sigma, void *stream);
 
+/* One velocity-Verlet step around the per-step hot path, for the paper's
+ * verification runs (§3: conservation of momentum and energy, results
+ * independent of the mesh and of the decomposition):
+ *   v += (dt/2) F(t)/m;  x += dt v;  bin (aica_bin_molecules);
+ *   F(t+dt) (aica_forces);  v += (dt/2) F(t+dt)/m.
+ *   mass     host double [S] (S = lj->n_species), positive
+ *   dt       time step (> 0), in the units of mass, length and energy used
+ *   n, species  device int32 [n]
+ *   pos, vel device double [n*3], original order, updated in place; pos is
+ *            not wrapped (binning wraps periodic coordinates itself)
+ *   force    device [n*3], float (FP32) or double (FP64), original order:
+ *            F(t) on entry (e.g. from aica_forces after binning pos), F(t+dt)
+ *            on return
+ *   ev_out   device double [7] or NULL: U and W at t+dt (as aica_forces)
+ *   kin_out  device double [4] or NULL: kinetic energy sum m v^2 / 2 and
+ *            momentum sum m v at t+dt
+ * Errors as aica_bin_molecules and aica_forces (AICA_ERR_OUTSIDE_MESH when a
+ * molecule leaves the mesh through a non-periodic side).  Asynchronous on
+ * `stream` apart from the synchronizing checks of those two calls. */
+aica_status aica_verlet_step(aica_mesh *mesh, const aica_lj *lj, aica_precision prec, const double *mass,
+                             double dt, int64_t n, const int32_t *species, double *pos, double *vel,
+                             void *force, double *ev_out, double *kin_out, void *stream);
+
+/* Kinetic energy sum m v^2 / 2 and momentum sum m v (device double [4],
+ * FP64) of n molecules with device velocities vel [n*3] and species [n];
+ * mass host [n_species].  Asynchronous on `stream`. */
+aica_status aica_kinetic(const double *mass, int32_t n_species, const int32_t *species, int64_t n,
+                         const double *vel, double *kin_out, void *stream);
+
 /* Stable counting sort of molecules by cell that allocates no device memory.
  * The paper has no counterpart; this entry point exists for callers that
  * cannot allocate device memory while they run: code recorded into a CUDA

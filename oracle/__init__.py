@@ -16,6 +16,11 @@ Functions and the passage each follows
   locate, bin_order  the containing cell of each molecule and the stable
                      binned order (§2.2: a molecule's cell is always known)
   aica_loop          the two force loops of §2.3 over the oracle's own lists
+  lj_cells           the same LJ sum by the cubic-cell algorithm of §2.1
+                     (CPU baseline)
+  verlet             velocity-Verlet trajectories with all-pairs forces, for
+                     the verification runs of §3 (conservation, mesh
+                     independence)
   torch_ref          autograd-of-oracle reference for the adjoint (torch FP64)
 
 Parity pins live in ``tests/test_oracle_*.py``.  Readings of the paper used
@@ -362,3 +367,28 @@ def aica_loop(lists, cell_off, xs, species_sorted, eps, sigma, rc, box, shift=Fa
                            _c(lists["ref_n"], np.int32).reshape(-1), _c(lists["ref_off"], np.int64),
                            _c(lists["ref_ids"], np.int32), F, ev, counts)
     return dict(F=F, U=ev[0], W=ev[1:].copy(), counts=counts)
+
+
+# ----------------------------------------------------------------- integration
+def verlet(pos, vel, species, eps, sigma, mass, rc, box, dt, steps):
+    """Velocity-Verlet trajectory with all-pairs FP64 forces (the runs of §3).
+
+    x(t+dt) = x + dt v + dt^2 F(t) / (2m);  v(t+dt) = v + dt (F(t) + F(t+dt)) / (2m).
+    Returns dict(pos, vel) at the end and per-step arrays (step 0 = start)
+    KE = sum m v^2 / 2, PE = U, P = sum m v.
+    """
+    x = np.array(pos, dtype=np.float64)
+    v = np.array(vel, dtype=np.float64)
+    m = np.asarray(mass, dtype=np.float64)[np.asarray(species)][:, None]
+    r = lj(x, species, eps, sigma, rc, box)
+    F = r["F"]
+    KE, PE, P = [0.5 * float((m * v * v).sum())], [r["U"]], [(m * v).sum(0)]
+    for _ in range(steps):
+        x = x + dt * v + (dt * dt) * F / (2.0 * m)
+        r = lj(x, species, eps, sigma, rc, box)
+        v = v + dt * (F + r["F"]) / (2.0 * m)
+        F = r["F"]
+        KE.append(0.5 * float((m * v * v).sum()))
+        PE.append(r["U"])
+        P.append((m * v).sum(0))
+    return dict(pos=x, vel=v, KE=np.array(KE), PE=np.array(PE), P=np.array(P))

@@ -78,6 +78,12 @@ SIGNATURES = {
                                                  ctypes.c_void_p, ctypes.c_void_p]),
     "aica_probe_fma_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
                                            ctypes.c_void_p]),
+    "aica_verlet_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(LJ), ctypes.c_int, ctypes.c_void_p,
+                                        ctypes.c_double, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p]),
+    "aica_kinetic": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p]),
     "aica_last_error": (ctypes.c_char_p, []),
     "aica_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -207,6 +213,23 @@ def aica_forces_backward(h, eps, sigma, prec, grad_force, grad_pos, grad_eps=Non
                                       _ptr(grad_eps), _ptr(grad_sigma), _stream()))
 
 
+def aica_verlet_step(h, eps, sigma, prec, mass, dt, species, pos, vel, force, ev_out=None, kin_out=None,
+                     shift=False):
+    lj = _lj(eps, sigma, shift)
+    ms = np.ascontiguousarray(mass, dtype=np.float64)
+    if len(ms) != lj.n_species:
+        raise ValueError("need one mass per species")
+    _check(lib().aica_verlet_step(h, ctypes.byref(lj), int(prec), ms.ctypes.data, float(dt), pos.shape[0],
+                                  _ptr(species), _ptr(pos), _ptr(vel), _ptr(force), _ptr(ev_out), _ptr(kin_out),
+                                  _stream()))
+
+
+def aica_kinetic(mass, species, vel, kin_out):
+    ms = np.ascontiguousarray(mass, dtype=np.float64)
+    _check(lib().aica_kinetic(ms.ctypes.data, len(ms), _ptr(species), vel.shape[0], _ptr(vel), _ptr(kin_out),
+                              _stream()))
+
+
 def aica_sort_by_cell_noalloc(cell_of, n_cells, order, cell_off):
     """Counting sort by cell with no device allocation (see include/aica.h)."""
     n = cell_of.shape[0]
@@ -331,6 +354,18 @@ class Mesh:
         gs = torch.empty(S, dtype=torch.float64, device=g.device)
         aica_forces_backward(self.h, eps, sigma, p, g, gp, ge, gs)
         return gp, ge, gs
+
+    def verlet_step(self, eps, sigma, mass, dt, pos, vel, species, force, prec="fp64", ev=None, kin=None,
+                    shift=False):
+        """One velocity-Verlet step (aica_verlet_step): pos, vel (FP64, device,
+        original order) updated in place; force holds F(t) on entry and
+        F(t + dt) on return (float32 for "fp32", float64 for "fp64")."""
+        p, dt_ = _prec(prec)
+        pos = _dev(pos, torch.float64, (self.n, 3), "pos")
+        vel = _dev(vel, torch.float64, (self.n, 3), "vel")
+        force = _dev(force, dt_, (self.n, 3), "force")
+        species = _dev(species, torch.int32, (self.n,), "species")
+        aica_verlet_step(self.h, eps, sigma, p, mass, dt, species, pos, vel, force, ev, kin, shift)
 
     def set_deferred(self, deferred=True):
         aica_set_deferred_checks(self.h, deferred)
