@@ -110,6 +110,37 @@ void aica_mesh_destroy(aica_mesh *mesh);
  * synchronizes it before returning (the list sizes are needed on the host). */
 aica_status aica_build_interaction_list(aica_mesh *mesh, double rc, double skin, void *stream);
 
+/* General periodic boundaries (§2.2.2): the referring transforms P' = y + R.P
+ * that carry the domain onto its periodic images (rotation R, row-major
+ * [n*9], and shift y [n*3], host arrays; one per coupled boundary, its
+ * inverse is implied).  They replace the box periodicity: the mesh's box must
+ * have no periodic axis (translations are given as transforms with R = I).
+ * The next list build enumerates their compositions (duplicates removed by
+ * comparing R and y, App. A.2), keeps those that bring an image of the
+ * domain within rc + skin, and builds the referred cells (source cell,
+ * transform) with their real cells by the exact minimum distance (on the
+ * host, once).  Real-referred pairs are evaluated from the real side only,
+ * as §2.3 does (each physical pair is met from both sides; energy and virial
+ * take half of each, and the referred pair counts count both sides).  In the
+ * referred-cell lists of aica_get_lists, ref_n holds (transform index, 0, 0).
+ * Molecules must lie in the mesh (binning does not fold them through a
+ * rotated boundary).  The adjoint supports box periodicity only.  Each R
+ * must be a proper rotation (R^T R = I, det R = 1, to 1e-9), else
+ * AICA_ERR_INVALID_ARG; n = 0 removes the transforms.  At most 64
+ * transforms may reach the domain (AICA_ERR_CAPACITY at the list build). */
+aica_status aica_mesh_set_transforms(aica_mesh *mesh, int32_t n, const double *R, const double *y);
+
+/* The referring transform of a pair of coupled faces (§2.2.2, Eq. of
+ * R_{alpha beta}): R turns -n_alpha into n_beta,
+ *   R = -(a.b) I + (1 + a.b) u u + a b - b a,  u = (a x b) / |a x b|,
+ * with a, b the unit face normals, and y = C_beta - R.C_alpha from the face
+ * centres.  Antiparallel normals give R = I (a translation); parallel
+ * normals leave the rotation axis undefined -> AICA_ERR_INVALID_ARG.  Host
+ * arrays: n_alpha, c_alpha, n_beta, c_beta [3] in, R [9] (row-major), y [3]
+ * out. */
+aica_status aica_coupling_transform(const double *n_alpha, const double *c_alpha, const double *n_beta,
+                                    const double *c_beta, double *R, double *y);
+
 /* Criterion that lists a cell pair. */
 typedef enum {
     AICA_DIL_MIN_DISTANCE = 0,   /* minimum distance between the polyhedra (default) */

@@ -20,6 +20,8 @@
  *                        uncertain cases are flagged for exact resolution
  *   oracle_aica_loop     the real-real and real-referred loops of §2.3 over
  *                        the oracle's own lists and binning
+ *   oracle_lj_images     the LJ sum over the images of all molecules under
+ *                        general referring transforms (§2.2.2)
  *   oracle_lj_cells      the same LJ sum by the textbook cubic-cell
  *                        algorithm of §2.1 (bins of side >= rc, 27-bin
  *                        stencil): the practical CPU baseline, not a pin
@@ -665,6 +667,75 @@ void oracle_lj_cells(int64_t n, const double *pos, const int32_t *species, const
     free(bin);
     free(start);
     free(sorted);
+}
+
+/* ------------------------------------------- general referring transforms */
+/* Forces on every molecule from all images P' = y_t + R_t . P of all
+ * molecules under the given transforms (§2.2.2, Eq. P' = y + R.P), the
+ * identity among them (its own image excluded): F_k = sum_t sum_l f(x_k -
+ * (y_t + R_t x_l)) over r < rc.  Each physical pair appears once from each
+ * side, so U and W take half of every term.  R row-major [nt*9], y [nt*3]. */
+void oracle_lj_images(int64_t n, const double *pos, const int32_t *species, const double *eps,
+                      const double *sigma, double rc, int64_t nt, const double *R, const double *y,
+                      int shift, double *F, double *Fabs, double *ev7, double *abs2, int64_t *count)
+{
+    double rc2 = rc * rc;
+    double U = 0, wxx = 0, wyy = 0, wzz = 0, wxy = 0, wxz = 0, wyz = 0, Ua = 0, Va = 0;
+    int64_t cnt = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : U, wxx, wyy, wzz, wxy, wxz, wyz, Ua, Va, cnt)
+    for (int64_t k = 0; k < n; ++k) {
+        double fx = 0, fy = 0, fz = 0, fa = 0;
+        int a = species[k];
+        for (int64_t t = 0; t < nt; ++t) {
+            const double *Rt = R + 9 * t, *yt = y + 3 * t;
+            int ident = Rt[0] == 1 && Rt[4] == 1 && Rt[8] == 1 && Rt[1] == 0 && Rt[2] == 0 && Rt[3] == 0 &&
+                        Rt[5] == 0 && Rt[6] == 0 && Rt[7] == 0 && yt[0] == 0 && yt[1] == 0 && yt[2] == 0;
+            for (int64_t l = 0; l < n; ++l) {
+                if (ident && l == k) continue;
+                const double *x = pos + 3 * l;
+                double q0 = yt[0] + ((Rt[0] * x[0] + Rt[1] * x[1]) + Rt[2] * x[2]);
+                double q1 = yt[1] + ((Rt[3] * x[0] + Rt[4] * x[1]) + Rt[5] * x[2]);
+                double q2 = yt[2] + ((Rt[6] * x[0] + Rt[7] * x[1]) + Rt[8] * x[2]);
+                double dx = pos[3 * k] - q0, dy = pos[3 * k + 1] - q1, dz = pos[3 * k + 2] - q2;
+                double r2 = (dx * dx + dy * dy) + dz * dz;
+                if (!(r2 < rc2)) continue;
+                int b = species[l];
+                double eab = sqrt(eps[a] * eps[b]);
+                double sab = 0.5 * (sigma[a] + sigma[b]);
+                double fs, u;
+                lj_pair(r2, eab, sab, &fs, &u);
+                if (shift) {
+                    double fc, uc;
+                    lj_pair(rc2, eab, sab, &fc, &uc);
+                    u -= uc;
+                }
+                fx += fs * dx;
+                fy += fs * dy;
+                fz += fs * dz;
+                fa += fabs(fs) * sqrt(r2);
+                U += 0.5 * u;
+                Ua += 0.5 * fabs(u);
+                Va += 0.5 * fabs(fs) * r2;
+                wxx += 0.5 * dx * (fs * dx);
+                wyy += 0.5 * dy * (fs * dy);
+                wzz += 0.5 * dz * (fs * dz);
+                wxy += 0.5 * dx * (fs * dy);
+                wxz += 0.5 * dx * (fs * dz);
+                wyz += 0.5 * dy * (fs * dz);
+                cnt += 1;
+            }
+        }
+        F[3 * k + 0] = fx;
+        F[3 * k + 1] = fy;
+        F[3 * k + 2] = fz;
+        Fabs[k] = fa;
+    }
+    ev7[0] = U;
+    ev7[1] = wxx; ev7[2] = wyy; ev7[3] = wzz;
+    ev7[4] = wxy; ev7[5] = wxz; ev7[6] = wyz;
+    abs2[0] = Ua;
+    abs2[1] = Va;
+    *count = cnt;
 }
 
 int oracle_num_threads(void)

@@ -84,6 +84,8 @@ SIGNATURES = {
                                         ctypes.c_void_p]),
     "aica_kinetic": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                     ctypes.c_void_p, ctypes.c_void_p]),
+    "aica_mesh_set_transforms": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
+    "aica_coupling_transform": (ctypes.c_int, [ctypes.c_void_p] * 6),
     "aica_last_error": (ctypes.c_char_p, []),
     "aica_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -230,6 +232,23 @@ def aica_kinetic(mass, species, vel, kin_out):
                               _stream()))
 
 
+def aica_mesh_set_transforms(h, transforms):
+    """transforms: list of (R [3,3], y [3]) referring transforms P' = y + R.P."""
+    R = np.ascontiguousarray(np.array([t[0] for t in transforms], dtype=np.float64).reshape(-1))
+    y = np.ascontiguousarray(np.array([t[1] for t in transforms], dtype=np.float64).reshape(-1))
+    _check(lib().aica_mesh_set_transforms(h, len(transforms), R.ctypes.data if len(transforms) else None,
+                                          y.ctypes.data if len(transforms) else None))
+
+
+def aica_coupling_transform(n_alpha, c_alpha, n_beta, c_beta):
+    """(R [3,3], y [3]) of the coupled faces (normals, centres) by §2.2.2."""
+    args = [np.ascontiguousarray(v, dtype=np.float64) for v in (n_alpha, c_alpha, n_beta, c_beta)]
+    R = np.zeros(9)
+    y = np.zeros(3)
+    _check(lib().aica_coupling_transform(*[a.ctypes.data for a in args], R.ctypes.data, y.ctypes.data))
+    return R.reshape(3, 3), y
+
+
 def aica_sort_by_cell_noalloc(cell_of, n_cells, order, cell_off):
     """Counting sort by cell with no device allocation (see include/aica.h)."""
     n = cell_of.shape[0]
@@ -311,6 +330,10 @@ class Mesh:
             self.close()
         except Exception:
             pass
+
+    def set_transforms(self, transforms):
+        """General periodic boundaries: list of (R, y) referring transforms."""
+        aica_mesh_set_transforms(self.h, transforms)
 
     def build_lists(self, rc, skin=1e-3, criterion="min_distance"):
         if criterion == "min_distance":

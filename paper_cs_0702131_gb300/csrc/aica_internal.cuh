@@ -75,6 +75,17 @@ struct RunEntry {
     int32_t n;      // image vector in bits 0-23 (as WorkEntry), len - 1 in bits 24-31
 };
 
+// A referring transform P' = y + R.P (§2.2.2), R row-major.
+struct Xform {
+    double R[9], y[3];
+};
+// Its device copy: FP64 for exact decisions, FP32 rotation for the FP32 path.
+struct XfDev {
+    double R[9], y[3];
+    float Rf[9], pad[3];
+};
+constexpr int kMaxXf = 64;          // transforms reaching the domain (identity included)
+
 __host__ __device__ inline int32_t pack_n(int nx, int ny, int nz) {
     return (int32_t)(((unsigned)(nx & 0xff)) | ((unsigned)(ny & 0xff) << 8) | ((unsigned)(nz & 0xff) << 16));
 }
@@ -83,6 +94,11 @@ __host__ __device__ inline int unpack_n(int32_t p, int axis) {
 }
 
 }  // namespace aica
+
+struct aica_mesh;
+namespace aica {
+aica_status build_transform_referral(aica_mesh *m, double thr, cudaStream_t st);
+}
 
 struct aica_mesh {
     int device = 0;
@@ -118,6 +134,12 @@ struct aica_mesh {
     int64_t n_dil = 0, n_ref = 0, n_ref_ids = 0, n_ties = 0, n_work = 0, n_runs = 0;
     aica::DevBuf dil_off, dil_ids, ref_src, ref_n, ref_off, ref_ids;   // int32 (ref_n: 3 int32)
     aica::DevBuf run_off, runs;              // [C+1] int32 first run of each cell; RunEntry
+    // General referring transforms (empty: box periodicity).  With them the
+    // image field of work entries and runs holds a transform index (0 = none).
+    std::vector<aica::Xform> xf_gen;         // generators given by the caller
+    int n_xf = 0;                            // transforms of the built lists (identity first)
+    aica::DevBuf xf_dev;                     // [n_xf] XfDev
+    aica::DevBuf run_d;                      // [runs] float4 shift of each run in I's molecule frame
     aica::DevBuf work_off, work;             // [C+1] int32 first entry of each cell; WorkEntry (partner, image)
     aica::DevBuf work_split;                 // [C] int32: first periodic-image entry of each cell
     aica::DevBuf proc_order;                 // [C] int32: cell processing order (spatially local)

@@ -11,16 +11,16 @@ namespace aica {
 
 template <class T> struct V3 { T x, y, z; };
 
-template <class T> __device__ __forceinline__ V3<T> operator-(V3<T> a, V3<T> b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
-template <class T> __device__ __forceinline__ V3<T> operator+(V3<T> a, V3<T> b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
-template <class T> __device__ __forceinline__ V3<T> operator*(V3<T> a, T s) { return {a.x * s, a.y * s, a.z * s}; }
-template <class T> __device__ __forceinline__ T dot3(V3<T> a, V3<T> b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+template <class T> __host__ __device__ __forceinline__ V3<T> operator-(V3<T> a, V3<T> b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+template <class T> __host__ __device__ __forceinline__ V3<T> operator+(V3<T> a, V3<T> b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+template <class T> __host__ __device__ __forceinline__ V3<T> operator*(V3<T> a, T s) { return {a.x * s, a.y * s, a.z * s}; }
+template <class T> __host__ __device__ __forceinline__ T dot3(V3<T> a, V3<T> b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 
-template <class T> __device__ __forceinline__ T clamp01(T v) { return v < T(0) ? T(0) : (v > T(1) ? T(1) : v); }
+template <class T> __host__ __device__ __forceinline__ T clamp01(T v) { return v < T(0) ? T(0) : (v > T(1) ? T(1) : v); }
 
 // squared distance from p to triangle abc
 template <class T>
-__device__ inline T d2_point_triangle(V3<T> p, V3<T> a, V3<T> b, V3<T> c) {
+__host__ __device__ inline T d2_point_triangle(V3<T> p, V3<T> a, V3<T> b, V3<T> c) {
     V3<T> ab = b - a, ac = c - a, ap = p - a;
     T d1 = dot3(ab, ap), d2 = dot3(ac, ap);
     V3<T> q;
@@ -63,7 +63,7 @@ __device__ inline T d2_point_triangle(V3<T> p, V3<T> a, V3<T> b, V3<T> c) {
 
 // squared distance between segments p0p1 and q0q1 (non-degenerate)
 template <class T>
-__device__ inline T d2_segment_segment(V3<T> p0, V3<T> p1, V3<T> q0, V3<T> q1) {
+__host__ __device__ inline T d2_segment_segment(V3<T> p0, V3<T> p1, V3<T> q0, V3<T> q1) {
     V3<T> d1 = p1 - p0, d2 = q1 - q0, r = p0 - q0;
     T a = dot3(d1, d1), e = dot3(d2, d2), f = dot3(d2, r);
     T c = dot3(d1, r), b = dot3(d1, d2);

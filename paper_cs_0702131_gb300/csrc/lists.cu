@@ -436,6 +436,10 @@ extern "C" aica_status aica_build_interaction_list_ex(aica_mesh *m, double rc, d
         set_error("aica_build_interaction_list_ex: unknown criterion %d", (int)criterion);
         return AICA_ERR_INVALID_ARG;
     }
+    if (m && !m->xf_gen.empty() && criterion != AICA_DIL_MIN_DISTANCE) {
+        set_error("aica_build_interaction_list_ex: general transforms take the minimum-distance criterion only");
+        return AICA_ERR_INVALID_ARG;
+    }
     if (!m) { set_error("aica_build_interaction_list: mesh is NULL"); return AICA_ERR_INVALID_ARG; }
     if (!(rc > 0) || !(skin >= 0) || !isfinite(rc + skin)) {
         set_error("aica_build_interaction_list: need rc > 0 and skin >= 0");
@@ -615,6 +619,22 @@ extern "C" aica_status aica_build_interaction_list_ex(aica_mesh *m, double rc, d
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(st));
 #undef CK
+    m->n_xf = 0;
+    if (!m->xf_gen.empty()) {
+        // general referring transforms: the referral and schedule are built on the host
+        m->n_work = n_work;
+        m->n_ties = (int64_t)ties;
+        aica_status s2 = build_transform_referral(m, thr, st);
+        d_boff.release(); d_bcell.release(); d_cnt.release(); d_seg.release(); d_keys.release(); d_scan.release();
+        d_ties.release();
+        if (s2 != AICA_OK) return s2;
+        m->n_dil = tot[0];
+        m->rc = rc;
+        m->skin = skin;
+        m->criterion = (int)criterion;
+        m->built = true;
+        return AICA_OK;
+    }
     d_boff.release(); d_bcell.release(); d_cnt.release(); d_seg.release(); d_keys.release(); d_scan.release();
     d_ties.release();
     m->n_dil = tot[0];

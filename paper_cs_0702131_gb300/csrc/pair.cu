@@ -81,6 +81,10 @@ struct PairArgs {
     const void *vs;              // backward: grad_force in binned order (float4 / double4)
     double *acc;                 // [0..6] U, W; [8..15] counters (as unsigned long long); [16..] grads
     unsigned *next_cell;         // FP32 kernel: next unclaimed cell (zero at launch)
+    int xf;                      // general referring transforms: image field = transform index
+    int n_xf;                    // transforms in xft
+    const XfDev *xft;            // [n_xf] transforms (identity first)
+    const float4 *run_d;         // general transforms: shift of each run in I's molecule frame
     SpeciesTab tab;
 };
 
@@ -104,8 +108,21 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // FP64 re-decision of r^2 < rc^2 with the all-pairs definition's operation order
+// image y_t + R_t x of x under referring transform t, in the oracle's operation order
+__device__ __forceinline__ void xf_image(const XfDev &t, const double *x, double *q) {
+    for (int i = 0; i < 3; ++i)
+        q[i] = __dadd_rn(t.y[i], __dadd_rn(__dadd_rn(__dmul_rn(t.R[3 * i], x[0]), __dmul_rn(t.R[3 * i + 1], x[1])),
+                                           __dmul_rn(t.R[3 * i + 2], x[2])));
+}
+
 __device__ __noinline__ bool band_in(const PairArgs &a, int k, int l, int np) {
     const double *xk = a.xs64 + 3 * (size_t)k, *xl = a.xs64 + 3 * (size_t)l;
+    if (a.xf && np != 0) {
+        double q[3];
+        xf_image(a.xft[np], xl, q);
+        const double dx = __dsub_rn(xk[0], q[0]), dy = __dsub_rn(xk[1], q[1]), dz = __dsub_rn(xk[2], q[2]);
+        return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)) < a.rc2_d;
+    }
     double dx = __dsub_rn(__dsub_rn(xk[0], xl[0]), __dmul_rn(a.L[0], (double)unpack_n(np, 0)));
     double dy = __dsub_rn(__dsub_rn(xk[1], xl[1]), __dmul_rn(a.L[1], (double)unpack_n(np, 1)));
     double dz = __dsub_rn(__dsub_rn(xk[2], xl[2]), __dmul_rn(a.L[2], (double)unpack_n(np, 2)));
@@ -165,6 +182,12 @@ __device__ __forceinline__ float3 cell_shift(const PairArgs &a, const int *oI, i
     return d;
 }
 
+// R x for a row-major FP32 rotation R
+__device__ __forceinline__ float3 rot32(const float *R, float x, float y, float z) {
+    return make_float3(fmaf(R[0], x, fmaf(R[1], y, R[2] * z)), fmaf(R[3], x, fmaf(R[4], y, R[5] * z)),
+                       fmaf(R[6], x, fmaf(R[7], y, R[8] * z)));
+}
+
 // Per-warp queue of partner molecules that survived culling: position in I's
 // frame (species bits in .w), binned index and image vector.
 constexpr int kQ = 64;
@@ -210,20 +233,30 @@ struct Warp32 {
 };
 
 // One pair's force and energy (FP32 body, branch-free): f is added to fi3
-// and subtracted from fj when `in`, u to u_acc.
-template <bool MULTI, bool SHIFT>
+// and subtracted from fj when `in`, u to v[0].  Under general transforms
+// (XF) the pair's energy and virial r (x) f are added here with weight w.
+template <bool MULTI, bool SHIFT, bool XF>
 __device__ __forceinline__ void pair32(const float4 *tab, float4 t0, int spi, int spj, float rx, float ry, float rz,
-                                       float r2, bool in, float *fi3, R3<float> &fj, float &u_acc) {
+                                       float r2, bool in, float w, float *fi3, R3<float> &fj, float (&v)[7]) {
     float fs, u;
     lj32<MULTI, SHIFT>(tab, t0, spi, spj, r2, fs, u);
     fs = in ? fs : 0.f;
-    u_acc += in ? u : 0.f;
+    v[0] += in ? (XF ? w * u : u) : 0.f;
     fi3[0] = fmaf(fs, rx, fi3[0]);
     fi3[1] = fmaf(fs, ry, fi3[1]);
     fi3[2] = fmaf(fs, rz, fi3[2]);
     fj.x = fmaf(-fs, rx, fj.x);
     fj.y = fmaf(-fs, ry, fj.y);
     fj.z = fmaf(-fs, rz, fj.z);
+    if (XF) {
+        const float g = w * fs, gx = g * rx, gy = g * ry;
+        v[1] = fmaf(gx, rx, v[1]);
+        v[2] = fmaf(gy, ry, v[2]);
+        v[3] = fmaf(g * rz, rz, v[3]);
+        v[4] = fmaf(gx, ry, v[4]);
+        v[5] = fmaf(gx, rz, v[5]);
+        v[6] = fmaf(gy, rz, v[6]);
+    }
 }
 
 // One lane's partner xj against the chunk's ni molecules: every pair with
@@ -231,10 +264,10 @@ __device__ __forceinline__ void pair32(const float4 *tab, float4 t0, int spi, in
 // FP32 r^2 within 1e-5 rc^2 of the cut-off is re-decided in FP64 after the
 // pass (one vote per batch).  With SAME, only chunk molecules of binned
 // index below lmax_k take part.  Returns the pairs within rc.
-template <int NI_, bool MULTI, bool SHIFT, bool SAME>
+template <int NI_, bool MULTI, bool SHIFT, bool SAME, bool XF>
 __device__ __forceinline__ unsigned eval_partner(const PairArgs &a, const float4 *tab, const float4 *xi, int ni,
                                                  int k0, float4 xj, int l, int np, int lmax_k, float (&fi)[3 * NI_],
-                                                 R3<float> &fj, float &u_acc) {
+                                                 R3<float> &fj, float (&v)[7], float w) {
     unsigned nin = 0, bm = 0;
     const float4 t0 = tab[0];
 #pragma unroll
@@ -246,8 +279,8 @@ __device__ __forceinline__ unsigned eval_partner(const PairArgs &a, const float4
             const bool ok = !SAME || k0 + t < lmax_k;
             const bool in = ok && r2 < a.rc2_lo;
             if (ok && !in && r2 < a.rc2_hi) bm |= 1u << t;
-            pair32<MULTI, SHIFT>(tab, t0, __float_as_int(x.w), __float_as_int(xj.w), rx, ry, rz, r2, in, &fi[3 * t],
-                                 fj, u_acc);
+            pair32<MULTI, SHIFT, XF>(tab, t0, __float_as_int(x.w), __float_as_int(xj.w), rx, ry, rz, r2, in, w,
+                                     &fi[3 * t], fj, v);
             nin += in;
         }
     }
@@ -259,8 +292,8 @@ __device__ __forceinline__ unsigned eval_partner(const PairArgs &a, const float4
                     const float4 x = xi[t];
                     const float rx = x.x - xj.x, ry = x.y - xj.y, rz = x.z - xj.z;
                     const float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
-                    pair32<MULTI, SHIFT>(tab, t0, __float_as_int(x.w), __float_as_int(xj.w), rx, ry, rz, r2, true,
-                                         &fi[3 * t], fj, u_acc);
+                    pair32<MULTI, SHIFT, XF>(tab, t0, __float_as_int(x.w), __float_as_int(xj.w), rx, ry, rz, r2, true,
+                                             w, &fi[3 * t], fj, v);
                     nin++;
                 }
             }
@@ -302,12 +335,18 @@ __device__ __forceinline__ void outer7(float (&v)[7], float ax, float ay, float 
     v[6] = fmaf(ay, bz, v[6]);
 }
 
-template <int NI_, bool MULTI, bool SHIFT, int MINB>
+// XF: general referring transforms (rotated referred cells, evaluated from
+// the real side only, energy and virial per pair with weight 1/2).
+template <int NI_, bool MULTI, bool SHIFT, int MINB, bool XF>
 __global__ void __launch_bounds__(kThreads32, MINB) pair_fwd32(PairArgs a) {
     __shared__ float4 tab[kMaxSpecies * kMaxSpecies];
     __shared__ Warp32<NI_> wsh[kWarps32];
     __shared__ double dsums[kWarps32][8];
+    __shared__ float xR[XF ? kMaxXf : 1][9];
     for (int i = threadIdx.x; i < kMaxSpecies * kMaxSpecies; i += blockDim.x) tab[i] = a.tab.f[i];
+    if (XF)
+        for (int i = threadIdx.x; i < 9 * kMaxXf; i += blockDim.x)
+            xR[i / 9][i % 9] = (a.xft && i / 9 < a.n_xf) ? a.xft[i / 9].Rf[i % 9] : 0.f;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     Warp32<NI_> &w = wsh[wib];
     if (lane < 8) dsums[wib][lane] = 0.0;
@@ -352,17 +391,20 @@ __global__ void __launch_bounds__(kThreads32, MINB) pair_fwd32(PairArgs a) {
                     if (lane == 0) w.cnt[3] += (unsigned)(count * ni);
                     R3<float> fj = {0.f, 0.f, 0.f};
                     const bool same = q.y == kSameCell;
+                    const bool one = XF && !same && q.y != 0;     // referred under a transform: one side
+                    const float wgt = one ? 0.5f : 1.f;
                     const unsigned nin =
                         __any_sync(FULL, same)
-                            ? eval_partner<NI_, MULTI, SHIFT, true>(a, tab, w.xi, ni, k0, xj, q.x, same ? 0 : q.y,
-                                                                    same ? q.x : 0x7fffffff, fi, fj, v[0])
-                            : eval_partner<NI_, MULTI, SHIFT, false>(a, tab, w.xi, ni, k0, xj, q.x, q.y, 0, fi, fj, v[0]);
+                            ? eval_partner<NI_, MULTI, SHIFT, true, XF>(a, tab, w.xi, ni, k0, xj, q.x, same ? 0 : q.y,
+                                                                        same ? q.x : 0x7fffffff, fi, fj, v, wgt)
+                            : eval_partner<NI_, MULTI, SHIFT, false, XF>(a, tab, w.xi, ni, k0, xj, q.x, q.y, 0, fi, fj,
+                                                                         v, wgt);
                     if (same) within[0] += nin;
                     else if (q.y != 0) within[2] += nin;
                     else within[1] += nin;
-                    if (nin) {
+                    if (nin && !one) {
                         atomicAdd((float4 *)a.facc + q.x, make_float4(fj.x, fj.y, fj.z, 0.f));
-                        outer7(v, xj.x, xj.y, xj.z, fj.x, fj.y, fj.z);
+                        if (!XF) outer7(v, xj.x, xj.y, xj.z, fj.x, fj.y, fj.z);
                     }
                     head = (head + count) & (kRing - 1);
                     __syncwarp();
@@ -403,9 +445,18 @@ __global__ void __launch_bounds__(kThreads32, MINB) pair_fwd32(PairArgs a) {
                         js = a.cell_off[cur.j];
                         nall = n = a.cell_off[cur.j + len] - js;
                         if (n > 0) {
-                            d = cell_shift(a, oI, cur.j, np);
+                            if (XF) {
+                                const float4 rd = a.run_d[eb + lane];
+                                d = make_float3(rd.x, rd.y, rd.z);
+                            } else {
+                                d = cell_shift(a, oI, cur.j, np);
+                            }
                             if (len == 1) {      // one partner cell: its sphere may rule it out
-                                const float4 sJ = a.sph[cur.j];
+                                float4 sJ = a.sph[cur.j];
+                                if (XF) {
+                                    const float3 c = rot32(xR[np], sJ.x, sJ.y, sJ.z);
+                                    sJ.x = c.x; sJ.y = c.y; sJ.z = c.z;
+                                }
                                 const float dx = sJ.x + d.x - sI.x, dy = sJ.y + d.y - sI.y, dz = sJ.z + d.z - sI.z;
                                 const float R = rcut + sI.w + sJ.w;
                                 tested = true;
@@ -450,7 +501,11 @@ __global__ void __launch_bounds__(kThreads32, MINB) pair_fwd32(PairArgs a) {
                             const float4 e = w.ed[o];
                             l = p + w.eb[o];
                             npl = __float_as_int(e.w);
-                            const float4 xl = a.xloc[l];
+                            float4 xl = a.xloc[l];
+                            if (XF) {
+                                const float3 c = rot32(xR[npl], xl.x, xl.y, xl.z);
+                                xl.x = c.x; xl.y = c.y; xl.z = c.z;
+                            }
                             xj = make_float4(xl.x + e.x, xl.y + e.y, xl.z + e.z, xl.w);
                             const float cx = xj.x - sI.x, cy = xj.y - sI.y, cz = xj.z - sI.z;
                             alive = cx * cx + cy * cy + cz * cz <= cull_i;
@@ -465,8 +520,10 @@ __global__ void __launch_bounds__(kThreads32, MINB) pair_fwd32(PairArgs a) {
                 const int t = lane / (32 / NI_);
                 if ((lane & (32 / NI_ - 1)) == 0 && t < ni) {
                     atomicAdd((float4 *)a.facc + k0 + t, make_float4(fi[0], fi[1], fi[2], 0.f));
-                    const float4 x = w.xi[t];
-                    outer7(v, x.x, x.y, x.z, fi[0], fi[1], fi[2]);
+                    if (!XF) {
+                        const float4 x = w.xi[t];
+                        outer7(v, x.x, x.y, x.z, fi[0], fi[1], fi[2]);
+                    }
                 }
             }
             if (lane == 0) w.cnt[0] += (unsigned)(nI * (nI - 1) / 2);
@@ -498,9 +555,11 @@ __global__ void __launch_bounds__(kThreads32, MINB) pair_fwd32(PairArgs a) {
 }
 
 // ------------------------------------------------------------------ FP64 path
+// w: weight of the pair's energy and virial (1/2 for a pair evaluated from
+// each of its sides, under general referring transforms)
 template <bool MULTI, bool SHIFT>
 __device__ __forceinline__ void pair64(const double (*tab)[4], double rx, double ry, double rz, double r2, int spi,
-                                       int spj, R3<double> &fi, R3<double> &fj, double (&acc)[7]) {
+                                       int spj, R3<double> &fi, R3<double> &fj, double (&acc)[7], double w = 1.0) {
     const double *t = MULTI ? tab[spi * kMaxSpecies + spj] : tab[0];
     double inv = 1.0 / r2;
     double s = t[0] * inv;
@@ -511,9 +570,9 @@ __device__ __forceinline__ void pair64(const double (*tab)[4], double rx, double
     fj.x -= fx; fj.y -= fy; fj.z -= fz;
     double u = t[2] * s3 * (s3 - 1.0);
     if (SHIFT) u -= t[3];
-    acc[0] += u;
-    acc[1] += rx * fx; acc[2] += ry * fy; acc[3] += rz * fz;
-    acc[4] += rx * fy; acc[5] += rx * fz; acc[6] += ry * fz;
+    acc[0] += w * u;
+    acc[1] += w * (rx * fx); acc[2] += w * (ry * fy); acc[3] += w * (rz * fz);
+    acc[4] += w * (rx * fy); acc[5] += w * (rx * fz); acc[6] += w * (ry * fz);
 }
 
 __device__ __forceinline__ void atomic_add3(double *p, double x, double y, double z) {
@@ -529,6 +588,32 @@ __device__ __forceinline__ void sep64(const double *xk, const double *xl, const 
     ry = __dsub_rn(__dsub_rn(xk[1], xl[1]), __dmul_rn(L[1], (double)unpack_n(np, 1)));
     rz = __dsub_rn(__dsub_rn(xk[2], xl[2]), __dmul_rn(L[2], (double)unpack_n(np, 2)));
     r2 = __dadd_rn(__dadd_rn(__dmul_rn(rx, rx), __dmul_rn(ry, ry)), __dmul_rn(rz, rz));
+}
+
+// r = x_k - (y_t + R_t x_l) under referring transform t (general transforms), else sep64
+__device__ __forceinline__ void sep64x(const PairArgs &a, const double *xk, const double *xl, int np, double &rx,
+                                       double &ry, double &rz, double &r2) {
+    if (a.xf && np != 0) {
+        double q[3];
+        xf_image(a.xft[np], xl, q);
+        rx = __dsub_rn(xk[0], q[0]);
+        ry = __dsub_rn(xk[1], q[1]);
+        rz = __dsub_rn(xk[2], q[2]);
+        r2 = __dadd_rn(__dadd_rn(__dmul_rn(rx, rx), __dmul_rn(ry, ry)), __dmul_rn(rz, rz));
+    } else {
+        sep64(xk, xl, a.L, np, rx, ry, rz, r2);
+    }
+}
+
+// Shift of cell J's molecule frame (under transform t) into cell I's, FP64 then FP32
+__device__ __forceinline__ float3 xf_shift(const PairArgs &a, int I, int J, int t) {
+    const XfDev &T = a.xft[t];
+    const int *oJ = a.orgm + 3 * J, *oI = a.orgm + 3 * I;
+    const double o[3] = {oJ[0] * (1.0 / 1024.0), oJ[1] * (1.0 / 1024.0), oJ[2] * (1.0 / 1024.0)};
+    double q[3];
+    xf_image(T, o, q);
+    return make_float3((float)(q[0] - oI[0] * (1.0 / 1024.0)), (float)(q[1] - oI[1] * (1.0 / 1024.0)),
+                       (float)(q[2] - oI[2] * (1.0 / 1024.0)));
 }
 
 // FP64: one warp per cell, lanes over the culled partner molecules (queue
@@ -602,13 +687,17 @@ __global__ void __launch_bounds__(kPairThreads) pair_fwd64(PairArgs a) {
                     R3<double> fj = {0, 0, 0};
                     bool any = false;
                     unsigned nin = 0;
+                    // general transforms: a referred pair acts on I's molecule only and is met
+                    // again from the other side, so its energy and virial count half
+                    const bool one = a.xf && npl != 0;
+                    const double w = one ? 0.5 : 1.0;
 #pragma unroll
                     for (int t = 0; t < NI; ++t) {
                         if (t < ni) {
                             double rx, ry, rz, r2;
-                            sep64(xi[t], xl, a.L, npl, rx, ry, rz, r2);
+                            sep64x(a, xi[t], xl, npl, rx, ry, rz, r2);
                             if (r2 < a.rc2_d) {
-                                pair64<MULTI, SHIFT>(tab, rx, ry, rz, r2, spi[t], spj, fi[t], fj, acc);
+                                pair64<MULTI, SHIFT>(tab, rx, ry, rz, r2, spi[t], spj, fi[t], fj, acc, w);
                                 nin++;
                                 any = true;
                             }
@@ -616,7 +705,7 @@ __global__ void __launch_bounds__(kPairThreads) pair_fwd64(PairArgs a) {
                     }
                     if (npl != 0) within[2] += nin;
                     else within[1] += nin;
-                    if (any) atomic_add3(facc + 4 * (size_t)l, fj.x, fj.y, fj.z);
+                    if (any && !one) atomic_add3(facc + 4 * (size_t)l, fj.x, fj.y, fj.z);
                 }
                 __syncwarp();
             };
@@ -632,9 +721,13 @@ __global__ void __launch_bounds__(kPairThreads) pair_fwd64(PairArgs a) {
                     if (n > 0) {
                         if (np != 0) eval[2] += (unsigned)(n * ni);
                         else eval[1] += (unsigned)(n * ni);
-                        const float3 s3 = cell_shift(a, a.orgm + 3 * I, we.j, np);
+                        const float3 s3 = a.xf ? xf_shift(a, I, we.j, np) : cell_shift(a, a.orgm + 3 * I, we.j, np);
                         d = make_float4(s3.x, s3.y, s3.z, 0.f);
                         float4 sJ = a.sph[we.j];
+                        if (a.xf) {
+                            const float3 c = rot32(a.xft[np].Rf, sJ.x, sJ.y, sJ.z);
+                            sJ.x = c.x; sJ.y = c.y; sJ.z = c.z;
+                        }
                         float dx = sJ.x + d.x - sI4.x, dy = sJ.y + d.y - sI4.y, dz = sJ.z + d.z - sI4.z;
                         float R = rcut + sI4.w + sJ.w;
                         culls++;
@@ -666,6 +759,10 @@ __global__ void __launch_bounds__(kPairThreads) pair_fwd64(PairArgs a) {
                     float4 xj;
                     if (p < total) {
                         float4 xl = a.xloc[l];
+                        if (a.xf) {
+                            const float3 c = rot32(a.xft[npl].Rf, xl.x, xl.y, xl.z);
+                            xl.x = c.x; xl.y = c.y; xl.z = c.z;
+                        }
                         xj = make_float4(xl.x + dx, xl.y + dy, xl.z + dz, xl.w);
                         float cx = xj.x - sI4.x, cy = xj.y - sI4.y, cz = xj.z - sI4.z;
                         alive = cx * cx + cy * cy + cz * cz <= cull_i;
@@ -959,6 +1056,10 @@ void fill_common(aica_mesh *m, PairArgs &a) {
     a.orgm = m->orgm.as<int>();
     a.run_off = m->run_off.as<int>();
     a.runs = m->runs.as<RunEntry>();
+    a.xf = m->n_xf > 0 ? 1 : 0;
+    a.n_xf = m->n_xf;
+    a.xft = m->n_xf > 0 ? m->xf_dev.as<XfDev>() : nullptr;
+    a.run_d = m->n_xf > 0 ? m->run_d.as<float4>() : nullptr;
     for (int d = 0; d < 3; ++d) {
         double L = m->box.periodic[d] ? m->box.L[d] : 0.0;
         a.Lhi[d] = (float)L;
@@ -987,7 +1088,7 @@ aica_status check_flags(aica_mesh *m, cudaStream_t st) {
 }
 
 // Blocks of the persistent FP32 kernel: every SM filled to its occupancy.
-template <int NI_, bool MULTI, bool SHIFT, int MINB>
+template <int NI_, bool MULTI, bool SHIFT, int MINB, bool XF>
 int fwd32_grid() {
     static int cache[64] = {0};
     int dev = 0;
@@ -995,25 +1096,30 @@ int fwd32_grid() {
     if (!cache[dev]) {
         int sms = 0, per = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pair_fwd32<NI_, MULTI, SHIFT, MINB>, kThreads32, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pair_fwd32<NI_, MULTI, SHIFT, MINB, XF>, kThreads32, 0);
         cache[dev] = std::max(1, sms * std::max(1, per));
     }
     return cache[dev];
 }
 
-template <int NI_, bool MULTI, bool SHIFT>
+template <int NI_, bool MULTI, bool SHIFT, bool XF>
 int launch_fwd32_t(const PairArgs &a, cudaStream_t st) {
     constexpr int MINB = NI_ <= 4 ? 7 : 6;
-    const int grid = std::min(fwd32_grid<NI_, MULTI, SHIFT, MINB>(), std::max(1, (a.C + kWarps32 - 1) / kWarps32));
-    pair_fwd32<NI_, MULTI, SHIFT, MINB><<<grid, kThreads32, 0, st>>>(a);
+    const int grid = std::min(fwd32_grid<NI_, MULTI, SHIFT, MINB, XF>(), std::max(1, (a.C + kWarps32 - 1) / kWarps32));
+    pair_fwd32<NI_, MULTI, SHIFT, MINB, XF><<<grid, kThreads32, 0, st>>>(a);
     return grid * kWarps32;
 }
 
-// Launch the FP32 kernel; returns the number of warps (partial-sum rows).
+template <int NI_, bool XF>
+int launch_fwd32_x(const PairArgs &a, bool multi, bool shift, cudaStream_t st) {
+    if (multi) return shift ? launch_fwd32_t<NI_, true, true, XF>(a, st) : launch_fwd32_t<NI_, true, false, XF>(a, st);
+    return shift ? launch_fwd32_t<NI_, false, true, XF>(a, st) : launch_fwd32_t<NI_, false, false, XF>(a, st);
+}
+
+// Launch the FP32 kernel; returns the number of warps.
 template <int NI_>
 int launch_fwd32(const PairArgs &a, bool multi, bool shift, cudaStream_t st) {
-    if (multi) return shift ? launch_fwd32_t<NI_, true, true>(a, st) : launch_fwd32_t<NI_, true, false>(a, st);
-    return shift ? launch_fwd32_t<NI_, false, true>(a, st) : launch_fwd32_t<NI_, false, false>(a, st);
+    return a.xf ? launch_fwd32_x<NI_, true>(a, multi, shift, st) : launch_fwd32_x<NI_, false>(a, multi, shift, st);
 }
 
 }  // namespace
@@ -1073,6 +1179,10 @@ extern "C" aica_status aica_forces_backward(aica_mesh *m, const aica_lj *lj, aic
     if (!m || !grad_force || !grad_pos) { set_error("aica_forces_backward: NULL argument"); return AICA_ERR_INVALID_ARG; }
     if (prec != AICA_FP32 && prec != AICA_FP64) { set_error("aica_forces_backward: bad precision"); return AICA_ERR_INVALID_ARG; }
     if (!m->built || !m->binned) { set_error("aica_forces_backward: build the lists and bin the molecules first"); return AICA_ERR_NOT_BUILT; }
+    if (m->n_xf > 0) {
+        set_error("aica_forces_backward: the adjoint supports box periodicity only (general transforms are set)");
+        return AICA_ERR_INVALID_ARG;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     BwdArgs b{};
     aica_status s = fill_params(m, lj, kMaxSpeciesBwd, b.p);

@@ -231,6 +231,52 @@ def two_species(seed, nfcc=(16, 32, 32), hex_shape=(16, 16, 16), rc=2.5):
     return cfg
 
 
+def wedge(seed, r0=4.0, r1=12.0, nz_sc=8, nr=4, ntheta=6, nz=4, jitter_std=0.05):
+    """A 90-degree sector of an annulus, rotationally periodic about the z axis
+    and periodic in z: the general (rotated) referral of §2.2.2.
+
+    Cells: hexahedra of a polar grid (planar chord faces).  Molecules: sites
+    ((i+1/2)a, (j+1/2)a, (k+1/2)a) of a simple cubic lattice at density 0.8,
+    a lattice the quarter turn maps onto itself, jittered, kept where they lie
+    inside a cell.  Transforms (R, y): the quarter turn from the coupled faces
+    theta = 0 (normal -y) and theta = 90 degrees (normal -x), and the shift
+    (0, 0, H).  The box has no periodic axis (z periodicity is a transform).
+    """
+    rng = np.random.default_rng(seed)
+    a = (1.0 / 0.8) ** (1.0 / 3.0)
+    H = nz_sc * a
+    r = np.linspace(r0, r1, nr + 1)
+    th = np.linspace(0.0, 0.5 * np.pi, ntheta + 1)
+    z = np.linspace(0.0, H, nz + 1)
+    R_, T_, Z_ = np.meshgrid(r, th, z, indexing="ij")
+    pts = np.stack([R_ * np.cos(T_), R_ * np.sin(T_), Z_], -1).reshape(-1, 3)
+    pts[np.abs(pts) < 1e-12] = 0.0
+    vid = lambda i, j, k: (i * (ntheta + 1) + j) * (nz + 1) + k
+    cells = []
+    for i in range(nr):
+        for j in range(ntheta):
+            for k in range(nz):
+                cells.append([vid(i + (v & 1), j + ((v >> 1) & 1), k + ((v >> 2) & 1)) for v in range(8)])
+    mesh = cells_to_mesh(pts, np.array(cells))
+    n1 = int(np.ceil(r1 / a)) + 1
+    g = (np.arange(n1) + 0.5) * a
+    gz = (np.arange(nz_sc) + 0.5) * a
+    X, Y, Zs = np.meshgrid(g, g, gz, indexing="ij")
+    sites = np.stack([X.ravel(), Y.ravel(), Zs.ravel()], 1)
+    rad = np.hypot(sites[:, 0], sites[:, 1])
+    sites = sites[(rad > r0 + 0.2) & (rad < r1 * np.cos(0.25 * np.pi / ntheta) - 0.2)]
+    pos = sites + rng.normal(scale=jitter_std, size=sites.shape)
+    pos[:, 2] = np.clip(pos[:, 2], 1e-6, H - 1e-6)
+    keep = (pos[:, 0] > 1e-6) & (pos[:, 1] > 1e-6)
+    pos = pos[keep]
+    rot = np.array([[0.0, -1.0, 0.0], [1.0, 0.0, 0.0], [0.0, 0.0, 1.0]])
+    transforms = [(rot, np.zeros(3)), (np.eye(3), np.array([0.0, 0.0, H]))]
+    box = _box((2 * r1, 2 * r1, H), (0, 0, 0))
+    n = pos.shape[0]
+    return dict(pos=pos, species=np.zeros(n, np.int32), eps=np.array([1.0]), sigma=np.array([1.0]), rc=2.5,
+                box=box, mesh=mesh, transforms=transforms, H=H, skin=1e-3, name=f"wedge-s{seed}")
+
+
 #: Named workloads.  ``c1``..``c5`` follow the five configurations of the
 #: benchmark table; ``t0`` and ``h0`` are small tet/hex cases for full parity.
 CONFIGS = {
