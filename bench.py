@@ -49,10 +49,11 @@ def parse():
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--fp64-steps", type=int, default=0, help="timed FP64 steps (default steps/10)")
     p.add_argument("--no-extras", action="store_true", help="skip FP64, e2e, accuracy and CPU legs")
-    p.add_argument("--study", choices=["cost", "vertex", "nve"], default=None,
+    p.add_argument("--study", choices=["cost", "vertex", "nve", "wedge"], default=None,
                    help="instead of the step: the cost-versus-mesh-size study of §2.4 (cost) or the "
                         "vertex-vertex list criterion of §2.2 against the minimum distance (vertex), or the "
-                        "paper's verification run of §3 on two meshes (nve)")
+                        "paper's verification run of §3 on two meshes (nve), or rotational periodicity through "
+                        "general referring transforms (wedge)")
     return p.parse_args()
 
 
@@ -679,6 +680,59 @@ def nve_study(args, steps=2000, dt=0.005, every=20):
             "rows": rows, "mesh_independence": same}
 
 
+def wedge_study(args, steps=100):
+    """Rotational periodicity (§2.2.2): a quarter annulus with the quarter
+    turn and the z shift as referring transforms; pairs within rc per second
+    of bin + forces (FP32 and FP64), against the oracle's sum over images on
+    sampled molecules."""
+    import torch
+    import oracle
+    from oracle import transforms as T
+    from paper_cs_0702131_gb300 import synth
+    from paper_cs_0702131_gb300.aica import Mesh
+    dev = torch.device("cuda", 0)
+    c = synth.wedge(args.seed, r0=20.0, r1=100.0, nz_sc=20, nr=32, ntheta=48, nz=8)
+    n = len(c["pos"])
+    m = Mesh(c["mesh"], c["box"])
+    m.set_transforms(c["transforms"])
+    t0 = time.perf_counter()
+    m.build_lists(c["rc"], c["skin"])
+    t_build = time.perf_counter() - t0
+    pos = torch.tensor(c["pos"], dtype=torch.float64, device=dev)
+    sp = torch.tensor(c["species"], dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    out = {"study": "wedge", "molecules": n, "cells": c["mesh"]["n_cells"], "build_lists_s": round(t_build, 3),
+           "referred_cells": int(len(m.lists()["ref_src"]))}
+    idx = np.sort(np.random.default_rng(5).choice(n, 64, replace=False))
+    pos_s = c["pos"]
+    for prec in ("fp32", "fp64"):
+        m.bin(pos, sp, outputs=False)
+        F, ev, cnt = m.forces(c["eps"], c["sigma"], prec)
+        k = cnt.cpu().numpy()
+        pairs = int(k[3] + k[4]) + int(k[5]) / 2.0
+        ms = []
+        for _ in range(steps if prec == "fp32" else max(5, steps // 10)):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            m.bin(pos, sp, outputs=False)
+            m.forces(c["eps"], c["sigma"], prec, out=F, ev=ev, counts=cnt)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        t = statistics.median(ms)
+        out[prec] = {"pairs_per_s": pairs / (t * 1e-3), "ms_per_step": round(t, 4), "pairs_within_rc": pairs}
+    # sampled rows of the oracle's image sum (all molecules as partners, closure of depth 6)
+    xf = T.closure(c["transforms"], 6)
+    ref = oracle.lj_images(pos_s, c["species"], c["eps"], c["sigma"], c["rc"], xf, idx=idx)
+    for prec in ("fp32", "fp64"):
+        F, _, _ = m.forces(c["eps"], c["sigma"], prec)
+        err = np.abs(F.double().cpu().numpy()[idx] - ref["F"]) / ref["Fabs"][:, None]
+        out[prec]["max_rel_to_sum_abs_f"] = float(err.max())
+    m.close()
+    return out
+
+
 def run_study(args):
     """Studies of the paper's analysis on this GPU (one JSON line)."""
     import numpy as np
@@ -719,6 +773,8 @@ def run_study(args):
                "molecules": len(posn), "rc": rc, "rows": rows}
     elif args.study == "nve":
         out = nve_study(args)
+    elif args.study == "wedge":
+        out = wedge_study(args)
     else:
         # the paper's vertex-vertex criterion against the minimum distance on
         # jittered meshes: pairs within rc it misses, and the error they make

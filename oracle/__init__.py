@@ -77,7 +77,8 @@ def lib():
         L.oracle_lj_cells.argtypes = [ctypes.c_int64, _f64, _i32, _f64, _f64, ctypes.c_double, _f64, _i32,
                                       ctypes.c_int, _f64, _f64, _f64, _f64, _i64]
         L.oracle_lj_images.argtypes = [ctypes.c_int64, _f64, _i32, _f64, _f64, ctypes.c_double, ctypes.c_int64,
-                                       _f64, _f64, ctypes.c_int, _f64, _f64, _f64, _f64, _i64]
+                                       _f64, _f64, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, _f64, _f64, _f64,
+                                       _f64, _i64]
         L.oracle_num_threads.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -139,24 +140,30 @@ def lj_cells(pos, species, eps, sigma, rc, box, shift=False):
                 pairs=int(cnt[0]) // 2)
 
 
-def lj_images(pos, species, eps, sigma, rc, transforms, shift=False):
+def lj_images(pos, species, eps, sigma, rc, transforms, shift=False, idx=None):
     """LJ forces from the images y + R.x of all molecules under `transforms`
     (a list of (R, y), the identity included; see oracle.transforms): the
     plain definition of the forces under general periodicity (§2.2.2).
-    Returns the keys of lj(); pairs = within-rc (k, image) terms / 2."""
+    Returns the keys of lj() for the rows idx (all molecules if None); pairs =
+    within-rc (k, image) terms / 2 when all rows are computed."""
     pos = _c(pos, np.float64)
     n = pos.shape[0]
+    idx_arr = None if idx is None else _c(idx, np.int64)
+    m = n if idx is None else idx_arr.shape[0]
     R = _c(np.array([t[0] for t in transforms]).reshape(-1), np.float64)
     y = _c(np.array([t[1] for t in transforms]).reshape(-1), np.float64)
-    F = np.zeros((n, 3))
-    Fabs = np.zeros(n)
+    F = np.zeros((m, 3))
+    Fabs = np.zeros(m)
     ev = np.zeros(7)
     ab = np.zeros(2)
     cnt = np.zeros(1, np.int64)
     lib().oracle_lj_images(n, pos, _c(species, np.int32), _c(eps, np.float64), _c(sigma, np.float64), float(rc),
-                           len(transforms), R, y, int(bool(shift)), F, Fabs, ev, ab, cnt)
-    return dict(F=F, Fabs=Fabs, U=ev[0], W=ev[1:].copy(), Uabs=ab[0], Wabs=ab[1], row_pairs=int(cnt[0]),
-                pairs=int(cnt[0]) // 2)
+                           len(transforms), R, y, int(bool(shift)),
+                           None if idx_arr is None else idx_arr.ctypes.data, m, F, Fabs, ev, ab, cnt)
+    out = dict(F=F, Fabs=Fabs, U=ev[0], W=ev[1:].copy(), Uabs=ab[0], Wabs=ab[1], row_pairs=int(cnt[0]))
+    if idx is None:
+        out["pairs"] = int(cnt[0]) // 2
+    return out
 
 
 # ------------------------------------------------------------------ cell geometry

@@ -674,16 +674,20 @@ void oracle_lj_cells(int64_t n, const double *pos, const int32_t *species, const
  * molecules under the given transforms (§2.2.2, Eq. P' = y + R.P), the
  * identity among them (its own image excluded): F_k = sum_t sum_l f(x_k -
  * (y_t + R_t x_l)) over r < rc.  Each physical pair appears once from each
- * side, so U and W take half of every term.  R row-major [nt*9], y [nt*3]. */
+ * side, so U and W take half of every term.  R row-major [nt*9], y [nt*3].
+ * With idx only the rows k = idx[0..nidx) are computed (into F[row]). */
 void oracle_lj_images(int64_t n, const double *pos, const int32_t *species, const double *eps,
                       const double *sigma, double rc, int64_t nt, const double *R, const double *y,
-                      int shift, double *F, double *Fabs, double *ev7, double *abs2, int64_t *count)
+                      int shift, const int64_t *idx, int64_t nidx, double *F, double *Fabs, double *ev7,
+                      double *abs2, int64_t *count)
 {
     double rc2 = rc * rc;
     double U = 0, wxx = 0, wyy = 0, wzz = 0, wxy = 0, wxz = 0, wyz = 0, Ua = 0, Va = 0;
     int64_t cnt = 0;
+    int64_t rows = idx ? nidx : n;
 #pragma omp parallel for schedule(dynamic, 16) reduction(+ : U, wxx, wyy, wzz, wxy, wxz, wyz, Ua, Va, cnt)
-    for (int64_t k = 0; k < n; ++k) {
+    for (int64_t row = 0; row < rows; ++row) {
+        int64_t k = idx ? idx[row] : row;
         double fx = 0, fy = 0, fz = 0, fa = 0;
         int a = species[k];
         for (int64_t t = 0; t < nt; ++t) {
@@ -725,10 +729,10 @@ void oracle_lj_images(int64_t n, const double *pos, const int32_t *species, cons
                 cnt += 1;
             }
         }
-        F[3 * k + 0] = fx;
-        F[3 * k + 1] = fy;
-        F[3 * k + 2] = fz;
-        Fabs[k] = fa;
+        F[3 * row + 0] = fx;
+        F[3 * row + 1] = fy;
+        F[3 * row + 2] = fz;
+        Fabs[row] = fa;
     }
     ev7[0] = U;
     ev7[1] = wxx; ev7[2] = wyy; ev7[3] = wzz;

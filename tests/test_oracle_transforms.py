@@ -77,3 +77,12 @@ def test_wedge_images_equal_full_annulus():
     # deeper compositions add no image within rc
     img8 = oracle.lj_images(c["pos"], c["species"], c["eps"], c["sigma"], c["rc"], T.closure(c["transforms"], 8))
     np.testing.assert_array_equal(img8["F"], img["F"])
+
+
+def test_image_rows_equal_full():
+    c = synth.wedge(3)
+    xf = T.closure(c["transforms"], 6)
+    full = oracle.lj_images(c["pos"], c["species"], c["eps"], c["sigma"], c["rc"], xf)
+    idx = np.array([0, 5, 17, len(c["pos"]) - 1])
+    part = oracle.lj_images(c["pos"], c["species"], c["eps"], c["sigma"], c["rc"], xf, idx=idx)
+    np.testing.assert_array_equal(part["F"], full["F"][idx])
