@@ -115,14 +115,17 @@ __device__ __forceinline__ void xf_image(const XfDev &t, const double *x, double
                                            __dmul_rn(t.R[3 * i + 2], x[2])));
 }
 
+// the same decision under referring transform np (general transforms)
+__device__ __noinline__ bool band_in_xf(const PairArgs &a, int k, int l, int np) {
+    const double *xk = a.xs64 + 3 * (size_t)k, *xl = a.xs64 + 3 * (size_t)l;
+    double q[3] = {xl[0], xl[1], xl[2]};
+    if (np != 0) xf_image(a.xft[np], xl, q);
+    const double dx = __dsub_rn(xk[0], q[0]), dy = __dsub_rn(xk[1], q[1]), dz = __dsub_rn(xk[2], q[2]);
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)) < a.rc2_d;
+}
+
 __device__ __noinline__ bool band_in(const PairArgs &a, int k, int l, int np) {
     const double *xk = a.xs64 + 3 * (size_t)k, *xl = a.xs64 + 3 * (size_t)l;
-    if (a.xf && np != 0) {
-        double q[3];
-        xf_image(a.xft[np], xl, q);
-        const double dx = __dsub_rn(xk[0], q[0]), dy = __dsub_rn(xk[1], q[1]), dz = __dsub_rn(xk[2], q[2]);
-        return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)) < a.rc2_d;
-    }
     double dx = __dsub_rn(__dsub_rn(xk[0], xl[0]), __dmul_rn(a.L[0], (double)unpack_n(np, 0)));
     double dy = __dsub_rn(__dsub_rn(xk[1], xl[1]), __dmul_rn(a.L[1], (double)unpack_n(np, 1)));
     double dz = __dsub_rn(__dsub_rn(xk[2], xl[2]), __dmul_rn(a.L[2], (double)unpack_n(np, 2)));
@@ -237,11 +240,13 @@ struct Warp32 {
 // (XF) the pair's energy and virial r (x) f are added here with weight w.
 template <bool MULTI, bool SHIFT, bool XF>
 __device__ __forceinline__ void pair32(const float4 *tab, float4 t0, int spi, int spj, float rx, float ry, float rz,
-                                       float r2, bool in, float w, float *fi3, R3<float> &fj, float (&v)[7]) {
+                                       float r2, bool in, float w, float *fi3, R3<float> &fj, float &u_acc,
+                                       float *v) {
     float fs, u;
     lj32<MULTI, SHIFT>(tab, t0, spi, spj, r2, fs, u);
     fs = in ? fs : 0.f;
-    v[0] += in ? (XF ? w * u : u) : 0.f;
+    if (XF) u_acc += in ? w * u : 0.f;
+    else u_acc += in ? u : 0.f;
     fi3[0] = fmaf(fs, rx, fi3[0]);
     fi3[1] = fmaf(fs, ry, fi3[1]);
     fi3[2] = fmaf(fs, rz, fi3[2]);
@@ -267,7 +272,7 @@ __device__ __forceinline__ void pair32(const float4 *tab, float4 t0, int spi, in
 template <int NI_, bool MULTI, bool SHIFT, bool SAME, bool XF>
 __device__ __forceinline__ unsigned eval_partner(const PairArgs &a, const float4 *tab, const float4 *xi, int ni,
                                                  int k0, float4 xj, int l, int np, int lmax_k, float (&fi)[3 * NI_],
-                                                 R3<float> &fj, float (&v)[7], float w) {
+                                                 R3<float> &fj, float &u_acc, float *v, float w) {
     unsigned nin = 0, bm = 0;
     const float4 t0 = tab[0];
 #pragma unroll
@@ -280,7 +285,7 @@ __device__ __forceinline__ unsigned eval_partner(const PairArgs &a, const float4
             const bool in = ok && r2 < a.rc2_lo;
             if (ok && !in && r2 < a.rc2_hi) bm |= 1u << t;
             pair32<MULTI, SHIFT, XF>(tab, t0, __float_as_int(x.w), __float_as_int(xj.w), rx, ry, rz, r2, in, w,
-                                     &fi[3 * t], fj, v);
+                                     &fi[3 * t], fj, u_acc, v);
             nin += in;
         }
     }
@@ -288,12 +293,12 @@ __device__ __forceinline__ unsigned eval_partner(const PairArgs &a, const float4
 #pragma unroll
         for (int t = 0; t < NI_; ++t) {
             if ((bm >> t) & 1u) {
-                if (band_in(a, k0 + t, l, np)) {
+                if (XF ? band_in_xf(a, k0 + t, l, np) : band_in(a, k0 + t, l, np)) {
                     const float4 x = xi[t];
                     const float rx = x.x - xj.x, ry = x.y - xj.y, rz = x.z - xj.z;
                     const float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
                     pair32<MULTI, SHIFT, XF>(tab, t0, __float_as_int(x.w), __float_as_int(xj.w), rx, ry, rz, r2, true,
-                                             w, &fi[3 * t], fj, v);
+                                             w, &fi[3 * t], fj, u_acc, v);
                     nin++;
                 }
             }
@@ -396,9 +401,10 @@ __global__ void __launch_bounds__(kThreads32, MINB) pair_fwd32(PairArgs a) {
                     const unsigned nin =
                         __any_sync(FULL, same)
                             ? eval_partner<NI_, MULTI, SHIFT, true, XF>(a, tab, w.xi, ni, k0, xj, q.x, same ? 0 : q.y,
-                                                                        same ? q.x : 0x7fffffff, fi, fj, v, wgt)
+                                                                        same ? q.x : 0x7fffffff, fi, fj, v[0],
+                                                                        XF ? v : nullptr, wgt)
                             : eval_partner<NI_, MULTI, SHIFT, false, XF>(a, tab, w.xi, ni, k0, xj, q.x, q.y, 0, fi, fj,
-                                                                         v, wgt);
+                                                                         v[0], XF ? v : nullptr, wgt);
                     if (same) within[0] += nin;
                     else if (q.y != 0) within[2] += nin;
                     else within[1] += nin;
@@ -591,9 +597,10 @@ __device__ __forceinline__ void sep64(const double *xk, const double *xl, const 
 }
 
 // r = x_k - (y_t + R_t x_l) under referring transform t (general transforms), else sep64
+template <bool XF>
 __device__ __forceinline__ void sep64x(const PairArgs &a, const double *xk, const double *xl, int np, double &rx,
                                        double &ry, double &rz, double &r2) {
-    if (a.xf && np != 0) {
+    if (XF && np != 0) {
         double q[3];
         xf_image(a.xft[np], xl, q);
         rx = __dsub_rn(xk[0], q[0]);
@@ -618,7 +625,7 @@ __device__ __forceinline__ float3 xf_shift(const PairArgs &a, int I, int J, int 
 
 // FP64: one warp per cell, lanes over the culled partner molecules (queue
 // batches of 32), up to NI molecules of I per chunk in registers.
-template <bool MULTI, bool SHIFT>
+template <bool MULTI, bool SHIFT, bool XF>
 __global__ void __launch_bounds__(kPairThreads) pair_fwd64(PairArgs a) {
     __shared__ double tab[kMaxSpecies * kMaxSpecies][4];
     __shared__ WarpQueue queues[kWarps];
@@ -689,13 +696,13 @@ __global__ void __launch_bounds__(kPairThreads) pair_fwd64(PairArgs a) {
                     unsigned nin = 0;
                     // general transforms: a referred pair acts on I's molecule only and is met
                     // again from the other side, so its energy and virial count half
-                    const bool one = a.xf && npl != 0;
+                    const bool one = XF && npl != 0;
                     const double w = one ? 0.5 : 1.0;
 #pragma unroll
                     for (int t = 0; t < NI; ++t) {
                         if (t < ni) {
                             double rx, ry, rz, r2;
-                            sep64x(a, xi[t], xl, npl, rx, ry, rz, r2);
+                            sep64x<XF>(a, xi[t], xl, npl, rx, ry, rz, r2);
                             if (r2 < a.rc2_d) {
                                 pair64<MULTI, SHIFT>(tab, rx, ry, rz, r2, spi[t], spj, fi[t], fj, acc, w);
                                 nin++;
@@ -721,10 +728,10 @@ __global__ void __launch_bounds__(kPairThreads) pair_fwd64(PairArgs a) {
                     if (n > 0) {
                         if (np != 0) eval[2] += (unsigned)(n * ni);
                         else eval[1] += (unsigned)(n * ni);
-                        const float3 s3 = a.xf ? xf_shift(a, I, we.j, np) : cell_shift(a, a.orgm + 3 * I, we.j, np);
+                        const float3 s3 = XF ? xf_shift(a, I, we.j, np) : cell_shift(a, a.orgm + 3 * I, we.j, np);
                         d = make_float4(s3.x, s3.y, s3.z, 0.f);
                         float4 sJ = a.sph[we.j];
-                        if (a.xf) {
+                        if (XF) {
                             const float3 c = rot32(a.xft[np].Rf, sJ.x, sJ.y, sJ.z);
                             sJ.x = c.x; sJ.y = c.y; sJ.z = c.z;
                         }
@@ -759,7 +766,7 @@ __global__ void __launch_bounds__(kPairThreads) pair_fwd64(PairArgs a) {
                     float4 xj;
                     if (p < total) {
                         float4 xl = a.xloc[l];
-                        if (a.xf) {
+                        if (XF) {
                             const float3 c = rot32(a.xft[npl].Rf, xl.x, xl.y, xl.z);
                             xl.x = c.x; xl.y = c.y; xl.z = c.z;
                         }
@@ -1087,6 +1094,17 @@ aica_status check_flags(aica_mesh *m, cudaStream_t st) {
     return AICA_OK;
 }
 
+template <bool XF>
+void launch_fwd64(const PairArgs &a, bool multi, bool shift, int grid, cudaStream_t st) {
+    if (multi) {
+        if (shift) pair_fwd64<true, true, XF><<<grid, kPairThreads, 0, st>>>(a);
+        else pair_fwd64<true, false, XF><<<grid, kPairThreads, 0, st>>>(a);
+    } else {
+        if (shift) pair_fwd64<false, true, XF><<<grid, kPairThreads, 0, st>>>(a);
+        else pair_fwd64<false, false, XF><<<grid, kPairThreads, 0, st>>>(a);
+    }
+}
+
 // Blocks of the persistent FP32 kernel: every SM filled to its occupancy.
 template <int NI_, bool MULTI, bool SHIFT, int MINB, bool XF>
 int fwd32_grid() {
@@ -1152,13 +1170,8 @@ extern "C" aica_status aica_forces(aica_mesh *m, const aica_lj *lj, aica_precisi
         if ((double)n < 5.0 * (double)a.C) launch_fwd32<4>(a, multi, shift, st);
         else launch_fwd32<8>(a, multi, shift, st);
     } else {
-        if (multi) {
-            if (shift) pair_fwd64<true, true><<<grid, kPairThreads, 0, st>>>(a);
-            else pair_fwd64<true, false><<<grid, kPairThreads, 0, st>>>(a);
-        } else {
-            if (shift) pair_fwd64<false, true><<<grid, kPairThreads, 0, st>>>(a);
-            else pair_fwd64<false, false><<<grid, kPairThreads, 0, st>>>(a);
-        }
+        if (a.xf) launch_fwd64<true>(a, multi, shift, grid, st);
+        else launch_fwd64<false>(a, multi, shift, grid, st);
     }
     AICA_CUDA(timing_end(tstop, st));
     finish_sums<<<1, 15 * 32, 0, st>>>(m->acc.as<double>(), ev_out, (long long *)counts_out);
