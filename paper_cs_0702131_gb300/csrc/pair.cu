@@ -1122,7 +1122,7 @@ int fwd32_grid() {
 
 template <int NI_, bool MULTI, bool SHIFT, bool XF>
 int launch_fwd32_t(const PairArgs &a, cudaStream_t st) {
-    constexpr int MINB = NI_ <= 4 ? 7 : 6;
+    constexpr int MINB = 7;                    // 7 blocks of 4 warps per SM (72 registers)
     const int grid = std::min(fwd32_grid<NI_, MULTI, SHIFT, MINB, XF>(), std::max(1, (a.C + kWarps32 - 1) / kWarps32));
     pair_fwd32<NI_, MULTI, SHIFT, MINB, XF><<<grid, kThreads32, 0, st>>>(a);
     return grid * kWarps32;
