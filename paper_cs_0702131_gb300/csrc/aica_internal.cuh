@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -33,6 +34,16 @@ cudaError_t timing_end(cudaEvent_t stop, cudaStream_t st);
 // Thread-local last error message.
 void set_error(const char *fmt, ...);
 aica_status cuda_fail(cudaError_t e, const char *what);
+
+// NVTX range over one C-ABI call (header-only NVTX v3: free unless a
+// profiler is attached).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
+#define AICA_RANGE(name) aica::Range aica_range_(name)
 
 #define AICA_CUDA(call)                                        \
     do {                                                       \

@@ -482,6 +482,7 @@ using namespace aica;
 
 extern "C" aica_status aica_bin_molecules(aica_mesh *m, const double *pos, const int32_t *species, int64_t n,
                                           int32_t *cell_of, int32_t *order, int32_t *cell_off, void *stream) {
+    AICA_RANGE("aica_bin_molecules");
     if (!m) { set_error("aica_bin_molecules: mesh is NULL"); return AICA_ERR_INVALID_ARG; }
     if (n < 0 || n > (int64_t)INT32_MAX / 2 || (n > 0 && (!pos || !species))) {
         set_error("aica_bin_molecules: bad molecule arrays (n = %lld)", (long long)n);
@@ -626,6 +627,7 @@ static __device__ __align__(256) int g_noalloc_scratch[kNoAllocWords];
 
 extern "C" aica_status aica_sort_by_cell_noalloc(const int32_t *cell_of, int64_t n, int64_t n_cells, int32_t *order,
                                                  int32_t *cell_off, void *stream) {
+    AICA_RANGE("aica_sort_by_cell_noalloc");
     if (n < 0 || n > (int64_t(1) << 30) || n_cells < 1 || !cell_off || (n > 0 && (!cell_of || !order))) {
         set_error("aica_sort_by_cell_noalloc: bad arguments (n = %lld, n_cells = %lld)", (long long)n,
                   (long long)n_cells);

@@ -432,6 +432,7 @@ extern "C" aica_status aica_build_interaction_list(aica_mesh *m, double rc, doub
 
 extern "C" aica_status aica_build_interaction_list_ex(aica_mesh *m, double rc, double skin,
                                                       aica_dil_criterion criterion, void *stream) {
+    AICA_RANGE("aica_build_interaction_list_ex");
     if (criterion != AICA_DIL_MIN_DISTANCE && criterion != AICA_DIL_VERTEX) {
         set_error("aica_build_interaction_list_ex: unknown criterion %d", (int)criterion);
         return AICA_ERR_INVALID_ARG;

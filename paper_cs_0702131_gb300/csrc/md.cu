@@ -87,6 +87,7 @@ using namespace aica;
 extern "C" aica_status aica_verlet_step(aica_mesh *m, const aica_lj *lj, aica_precision prec, const double *mass,
                                         double dt, int64_t n, const int32_t *species, double *pos, double *vel,
                                         void *force, double *ev_out, double *kin_out, void *stream) {
+    AICA_RANGE("aica_verlet_step");
     if (!m || !pos || !vel || !force || !species || n < 1) {
         set_error("aica_verlet_step: NULL argument or no molecules");
         return AICA_ERR_INVALID_ARG;

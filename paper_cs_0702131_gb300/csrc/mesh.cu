@@ -51,6 +51,7 @@ extern "C" aica_status aica_mesh_create(const double *points, int64_t n_points, 
                                         const int64_t *face_vertices, int64_t n_faces, const int64_t *owner,
                                         const int64_t *neighbour, int64_t n_cells, const aica_box *box,
                                         aica_mesh **out) {
+    AICA_RANGE("aica_mesh_create");
     using namespace aica;
     if (!out) { set_error("aica_mesh_create: out is NULL"); return AICA_ERR_INVALID_ARG; }
     *out = nullptr;
