@@ -200,7 +200,7 @@ aica_status aica_bin_molecules(aica_mesh *mesh, const double *pos, const int32_t
  *          FP32 value lies within 1e-5 rc^2 of the cut-off;
  *          AICA_FP64: all FP64.
  *   force_out  device [n*3], float (FP32) or double (FP64), original order;
- *              overwritten
+ *              overwritten (may be NULL when no molecules were binned)
  *   ev_out     device double [7], optional: U, Wxx, Wyy, Wzz, Wxy, Wxz, Wyz
  *              with W_ab = sum over pairs of r_a f_b, each physical pair once
  *   counts_out device int64 [6], optional: evaluated pairs {same-cell, DIL,

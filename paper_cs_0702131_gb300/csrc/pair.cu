@@ -1148,7 +1148,7 @@ using namespace aica;
 extern "C" aica_status aica_forces(aica_mesh *m, const aica_lj *lj, aica_precision prec, void *force_out,
                                    double *ev_out, int64_t *counts_out, void *stream) {
     AICA_RANGE("aica_forces");
-    if (!m || !force_out) { set_error("aica_forces: NULL argument"); return AICA_ERR_INVALID_ARG; }
+    if (!m || (!force_out && m->n_mol > 0)) { set_error("aica_forces: NULL argument"); return AICA_ERR_INVALID_ARG; }
     if (prec != AICA_FP32 && prec != AICA_FP64) { set_error("aica_forces: bad precision"); return AICA_ERR_INVALID_ARG; }
     if (!m->built || !m->binned) { set_error("aica_forces: build the lists and bin the molecules first"); return AICA_ERR_NOT_BUILT; }
     cudaStream_t st = (cudaStream_t)stream;
@@ -1191,7 +1191,10 @@ extern "C" aica_status aica_forces_backward(aica_mesh *m, const aica_lj *lj, aic
                                             const void *grad_force, void *grad_pos, double *grad_eps,
                                             double *grad_sigma, void *stream) {
     AICA_RANGE("aica_forces_backward");
-    if (!m || !grad_force || !grad_pos) { set_error("aica_forces_backward: NULL argument"); return AICA_ERR_INVALID_ARG; }
+    if (!m || ((!grad_force || !grad_pos) && m->n_mol > 0)) {
+        set_error("aica_forces_backward: NULL argument");
+        return AICA_ERR_INVALID_ARG;
+    }
     if (prec != AICA_FP32 && prec != AICA_FP64) { set_error("aica_forces_backward: bad precision"); return AICA_ERR_INVALID_ARG; }
     if (!m->built || !m->binned) { set_error("aica_forces_backward: build the lists and bin the molecules first"); return AICA_ERR_NOT_BUILT; }
     if (m->n_xf > 0) {
