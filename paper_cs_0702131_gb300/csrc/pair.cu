@@ -153,9 +153,8 @@ __device__ void warp_to_stripe(const PairArgs &a, int gwarp, const double (&dsum
 
 // Totals of the stripe rows into acc ([0..6] FP64, [8..15] counters as
 // unsigned 64-bit) and the caller's energy/virial [7] and pair counts [6].
-// One warp per value (15 warps), lanes over the stripe rows.
-__global__ void __launch_bounds__(15 * 32) finish_sums(double *acc, double *ev, long long *counts) {
-    const int i = threadIdx.x >> 5, lane = threadIdx.x & 31;
+// Value i of the sums (one warp): lanes over the stripe rows.
+__device__ __forceinline__ void finish_value(double *acc, double *ev, long long *counts, int i, int lane) {
     double v = 0.0;
     for (int r = lane; r < kStripes; r += 32) v += acc[kAccStripes + r * kParts + i];
     v = warp_sum(v);
@@ -168,6 +167,12 @@ __global__ void __launch_bounds__(15 * 32) finish_sums(double *acc, double *ev, 
         ((unsigned long long *)(acc + 8))[i - 7] = c;
         if (counts && i < 13) counts[i - 7] = (long long)c;
     }
+}
+
+// One warp per value (15 warps); used when no molecule was binned (otherwise
+// the first block of unsort_forces does it).
+__global__ void __launch_bounds__(15 * 32) finish_sums(double *acc, double *ev, long long *counts) {
+    finish_value(acc, ev, counts, threadIdx.x >> 5, threadIdx.x & 31);
 }
 
 // ------------------------------------------------------------------ FP32 path
@@ -814,8 +819,14 @@ __global__ void __launch_bounds__(kPairThreads) pair_fwd64(PairArgs a) {
 }
 
 // ---------------------------------------------------------------- unsort
+// Forces back to the original order; with acc, the first block also adds
+// up the pair kernel's striped sums (finish_value).
 template <class T>
-__global__ void __launch_bounds__(256) unsort_forces(const int *inv, int64_t n, const void *facc, T *out, int f64) {
+__global__ void __launch_bounds__(256) unsort_forces(const int *inv, int64_t n, const void *facc, T *out, int f64,
+                                                     double *acc = nullptr, double *ev = nullptr,
+                                                     long long *counts = nullptr) {
+    if (acc && blockIdx.x == 0)
+        for (int i = threadIdx.x >> 5; i < 15; i += blockDim.x >> 5) finish_value(acc, ev, counts, i, threadIdx.x & 31);
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     int s = inv[k];
@@ -1175,12 +1186,14 @@ extern "C" aica_status aica_forces(aica_mesh *m, const aica_lj *lj, aica_precisi
         else launch_fwd64<false>(a, multi, shift, grid, st);
     }
     AICA_CUDA(timing_end(tstop, st));
-    finish_sums<<<1, 15 * 32, 0, st>>>(m->acc.as<double>(), ev_out, (long long *)counts_out);
     m->launches = 2;
+    double *acc = m->acc.as<double>();
     if (n > 0) {
-        if (f64) unsort_forces<double><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m->inv.as<int>(), n, m->facc.p, (double *)force_out, 1);
-        else unsort_forces<float><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m->inv.as<int>(), n, m->facc.p, (float *)force_out, 0);
-        m->launches++;
+        const unsigned g = (unsigned)((n + 255) / 256);
+        if (f64) unsort_forces<double><<<g, 256, 0, st>>>(m->inv.as<int>(), n, m->facc.p, (double *)force_out, 1, acc, ev_out, (long long *)counts_out);
+        else unsort_forces<float><<<g, 256, 0, st>>>(m->inv.as<int>(), n, m->facc.p, (float *)force_out, 0, acc, ev_out, (long long *)counts_out);
+    } else {
+        finish_sums<<<1, 15 * 32, 0, st>>>(acc, ev_out, (long long *)counts_out);
     }
     AICA_CUDA(cudaGetLastError());
     if (!m->deferred) return check_flags(m, st);
