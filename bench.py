@@ -454,6 +454,7 @@ def adjoint_timing(cfg, mesh, flush, dev, pairs):
         for _ in range(2):
             mesh.forces_backward(cfg["eps"], cfg["sigma"], g, prec)
         ms = []
+        mesh.set_kernel_timing(True)
         for _ in range(10):
             flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -462,10 +463,13 @@ def adjoint_timing(cfg, mesh, flush, dev, pairs):
             e1.record()
             torch.cuda.synchronize()
             ms.append(e0.elapsed_time(e1))
+        kms = [float(x) for x in mesh.take_kernel_times()]
+        mesh.set_kernel_timing(False)
         t = statistics.median(ms)
-        res[prec] = {"ms": round(t, 4), "pairs_per_s": pairs / (t * 1e-3)}
+        res[prec] = {"ms": round(t, 4), "pairs_per_s": pairs / (t * 1e-3),
+                     "kernel_ms": round(statistics.median(kms), 4) if kms else None}
     res["note"] = ("one backward call (gather of dL/dF, pair kernel recomputing every pair term, scatter); "
-                   "binning of the current positions not included")
+                   "kernel_ms: the adjoint pair kernel alone; binning of the current positions not included")
     return res
 
 

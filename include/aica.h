@@ -60,7 +60,7 @@ typedef struct {
  * eps_b), sigma_ab = (sigma_a + sigma_b) / 2 and one absolute rc for every
  * pair (the largest cut-off builds the lists, App. A). */
 typedef struct {
-    int32_t n_species;   /* S: 1..8 forward, 1..4 backward                 */
+    int32_t n_species;   /* S: 1..8                                         */
     const double *eps;   /* host [S]                                       */
     const double *sigma; /* host [S]                                       */
     int32_t shift;       /* nonzero: subtract u(rc) from each pair's energy */
@@ -218,8 +218,14 @@ aica_status aica_forces(aica_mesh *mesh, const aica_lj *lj, aica_precision prec,
  *   grad_sigma device double [S], optional: dL/d sigma_s
  * Pair terms are recomputed over the same pair set (nothing is stored by the
  * forward call).  A periodic image pair couples a molecule to the source
- * molecule of the referred copy, so both receive position gradient.  The
- * cut-off is not differentiated. */
+ * molecule of the referred copy, so both receive position gradient.  Under
+ * general referring transforms (aica_mesh_set_transforms, §2.2.2) a referred
+ * pair acts on the real molecule only and the source molecule's gradient is
+ * rotated back (-R^T J v).  The cut-off is not differentiated.  FP32 sums
+ * per-molecule gradients with FP32 atomics (run-to-run differences in the
+ * last bits); the species sums are FP64.  AICA_ERR_INVALID_ARG for bad
+ * species parameters (1..8 species), AICA_ERR_NOT_BUILT without lists and
+ * binning. */
 aica_status aica_forces_backward(aica_mesh *mesh, const aica_lj *lj, aica_precision prec,
                                  const void *grad_force, void *grad_pos, double *grad_eps,
                                  double *grad_sigma, void *stream);

@@ -19,7 +19,6 @@ constexpr int kMaxTri = 32;
 constexpr int kMaxVtx = 24;
 constexpr int kMaxEdg = 48;
 constexpr int kMaxSpecies = 8;
-constexpr int kMaxSpeciesBwd = 4;
 
 // Device-side error flags (bitwise OR into mesh->d_flags[0]).
 enum : unsigned {

@@ -345,6 +345,107 @@ __device__ __forceinline__ void outer7(float (&v)[7], float ax, float ay, float 
     v[6] = fmaf(ay, bz, v[6]);
 }
 
+// Candidates of cell I's schedule runs e0 .. e1 for a chunk of ni molecules:
+// a run's partner cells are consecutive, so their molecules are one binned
+// range under one shift.  32 runs at a time are culled by their partner
+// cell's sphere (single-cell runs), compacted (ballot) into ed / ebi, and
+// their molecules indexed by a ballot/redux map from candidate position to
+// run; every candidate (lane = candidate) goes to push(alive, position in I's
+// frame, binned index, image field), alive = inside I's culling sphere.
+// COUNT adds the evaluated-pair and sphere-test tallies to cnt[1], cnt[2], cnt[4].
+template <bool XF, bool COUNT, class Push>
+__device__ __forceinline__ void walk_runs(const PairArgs &a, float4 *ed, int *ebi, unsigned *cnt,
+                                          const float (*xR)[9], int e0, int e1, int ni, const int *oI, float4 sI,
+                                          float rcut, float cull_i, int lane, Push &push) {
+    const unsigned FULL = 0xffffffffu, lt = (1u << lane) - 1u, le = FULL >> (31 - lane);
+    const float4 far = make_float4(1e18f, 1e18f, 1e18f, 0.f);
+    RunEntry we = e0 + lane < e1 ? a.runs[e0 + lane] : RunEntry{0, 0};
+    for (int eb = e0; eb < e1; eb += 32) {
+        const RunEntry cur = we;
+        const bool has = eb + lane < e1;
+        if (eb + 32 + lane < e1) we = a.runs[eb + 32 + lane];
+        const int np = cur.n & 0xffffff, len = ((unsigned)cur.n >> 24) + 1;
+        int js = 0, n = 0, nall = 0;
+        bool tested = false;
+        float3 d = make_float3(0.f, 0.f, 0.f);
+        if (has) {
+            js = a.cell_off[cur.j];
+            nall = n = a.cell_off[cur.j + len] - js;
+            if (n > 0) {
+                if (XF) {
+                    const float4 rd = a.run_d[eb + lane];
+                    d = make_float3(rd.x, rd.y, rd.z);
+                } else {
+                    d = cell_shift(a, oI, cur.j, np);
+                }
+                if (len == 1) {      // one partner cell: its sphere may rule it out
+                    float4 sJ = a.sph[cur.j];
+                    if (XF) {
+                        const float3 c = rot32(xR[np], sJ.x, sJ.y, sJ.z);
+                        sJ.x = c.x; sJ.y = c.y; sJ.z = c.z;
+                    }
+                    const float dx = sJ.x + d.x - sI.x, dy = sJ.y + d.y - sI.y, dz = sJ.z + d.z - sI.z;
+                    const float R = rcut + sI.w + sJ.w;
+                    tested = true;
+                    if (dx * dx + dy * dy + dz * dz > R * R * 1.00002f + 1e-5f) n = 0;
+                }
+            }
+        }
+        unsigned ev_d = 0, ev_r = 0, ncull = 0;
+        if (COUNT) {
+            ev_d = __reduce_add_sync(FULL, np == 0 ? (unsigned)(nall * ni) : 0u);
+            ev_r = __reduce_add_sync(FULL, np != 0 ? (unsigned)(nall * ni) : 0u);
+            ncull = __popc(__ballot_sync(FULL, tested));
+        }
+        int inc = n;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, inc, o);
+            if (lane >= o) inc += y;
+        }
+        const int total = __shfl_sync(FULL, inc, 31);
+        const bool live = n > 0;
+        const unsigned lbal = __ballot_sync(FULL, live);
+        if (live) {
+            const int s = __popc(lbal & lt);
+            ed[s] = make_float4(d.x, d.y, d.z, __int_as_float(np));
+            ebi[s] = js - (inc - n);
+        }
+        if (COUNT && lane == 0) {
+            cnt[1] += ev_d;
+            cnt[2] += ev_r;
+            cnt[4] += ncull + (unsigned)total;
+        }
+        __syncwarp();
+        for (int p0 = 0; p0 < total; p0 += 32) {
+            // entry holding candidate p = p0 + lane: the live entries ending at or before p
+            const int b = inc - p0;
+            const int base = __popc(__ballot_sync(FULL, live && b <= 0));
+            const unsigned M = __reduce_or_sync(FULL, (live && b > 0 && b < 32) ? (1u << b) : 0u);
+            const int p = p0 + lane;
+            bool alive = false;
+            float4 xj = far;
+            int l = 0, npl = 0;
+            if (p < total) {
+                const int o = base + __popc(M & le);
+                const float4 e = ed[o];
+                l = p + ebi[o];
+                npl = __float_as_int(e.w);
+                float4 xl = a.xloc[l];
+                if (XF) {
+                    const float3 c = rot32(xR[npl], xl.x, xl.y, xl.z);
+                    xl.x = c.x; xl.y = c.y; xl.z = c.z;
+                }
+                xj = make_float4(xl.x + e.x, xl.y + e.y, xl.z + e.z, xl.w);
+                const float cx = xj.x - sI.x, cy = xj.y - sI.y, cz = xj.z - sI.z;
+                alive = cx * cx + cy * cy + cz * cz <= cull_i;
+            }
+            push(alive, xj, l, npl);
+        }
+        __syncwarp();
+    }
+}
+
 // XF: general referring transforms (rotated referred cells, evaluated from
 // the real side only, energy and virial per pair with weight 1/2).
 template <int NI_, bool MULTI, bool SHIFT, int MINB, bool XF>
@@ -362,7 +463,7 @@ __global__ void __launch_bounds__(kThreads32, MINB) pair_fwd32(PairArgs a) {
     if (lane < 8) dsums[wib][lane] = 0.0;
     if (lane < 5) w.cnt[lane] = 0;
     __syncthreads();
-    const unsigned FULL = 0xffffffffu, lt = (1u << lane) - 1u, le = FULL >> (31 - lane);
+    const unsigned FULL = 0xffffffffu, lt = (1u << lane) - 1u;
     const float4 far = make_float4(1e18f, 1e18f, 1e18f, 0.f);
     const float rcut = sqrtf(a.rc2_hi);
     double *dsum = dsums[wib];
@@ -441,90 +542,7 @@ __global__ void __launch_bounds__(kThreads32, MINB) pair_fwd32(PairArgs a) {
                     const bool alive = li < nI;
                     push(alive, alive ? a.xloc[s0 + li] : far, s0 + li, kSameCell);
                 }
-                // schedule runs, 32 per batch: a run's partner cells are
-                // consecutive, so their molecules are one binned range
-                RunEntry we = e0 + lane < e1 ? a.runs[e0 + lane] : RunEntry{0, 0};
-                for (int eb = e0; eb < e1; eb += 32) {
-                    const RunEntry cur = we;
-                    const bool has = eb + lane < e1;
-                    if (eb + 32 + lane < e1) we = a.runs[eb + 32 + lane];
-                    const int np = cur.n & 0xffffff, len = ((unsigned)cur.n >> 24) + 1;
-                    int js = 0, n = 0, nall = 0;
-                    bool tested = false;
-                    float3 d = make_float3(0.f, 0.f, 0.f);
-                    if (has) {
-                        js = a.cell_off[cur.j];
-                        nall = n = a.cell_off[cur.j + len] - js;
-                        if (n > 0) {
-                            if (XF) {
-                                const float4 rd = a.run_d[eb + lane];
-                                d = make_float3(rd.x, rd.y, rd.z);
-                            } else {
-                                d = cell_shift(a, oI, cur.j, np);
-                            }
-                            if (len == 1) {      // one partner cell: its sphere may rule it out
-                                float4 sJ = a.sph[cur.j];
-                                if (XF) {
-                                    const float3 c = rot32(xR[np], sJ.x, sJ.y, sJ.z);
-                                    sJ.x = c.x; sJ.y = c.y; sJ.z = c.z;
-                                }
-                                const float dx = sJ.x + d.x - sI.x, dy = sJ.y + d.y - sI.y, dz = sJ.z + d.z - sI.z;
-                                const float R = rcut + sI.w + sJ.w;
-                                tested = true;
-                                if (dx * dx + dy * dy + dz * dz > R * R * 1.00002f + 1e-5f) n = 0;
-                            }
-                        }
-                    }
-                    const unsigned ev_d = __reduce_add_sync(FULL, np == 0 ? (unsigned)(nall * ni) : 0u);
-                    const unsigned ev_r = __reduce_add_sync(FULL, np != 0 ? (unsigned)(nall * ni) : 0u);
-                    const unsigned ncull = __popc(__ballot_sync(FULL, tested));
-                    int inc = n;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const int y = __shfl_up_sync(FULL, inc, o);
-                        if (lane >= o) inc += y;
-                    }
-                    const int total = __shfl_sync(FULL, inc, 31);
-                    const bool live = n > 0;
-                    const unsigned lbal = __ballot_sync(FULL, live);
-                    if (live) {
-                        const int s = __popc(lbal & lt);
-                        w.ed[s] = make_float4(d.x, d.y, d.z, __int_as_float(np));
-                        w.eb[s] = js - (inc - n);
-                    }
-                    if (lane == 0) {
-                        w.cnt[1] += ev_d;
-                        w.cnt[2] += ev_r;
-                        w.cnt[4] += ncull + (unsigned)total;
-                    }
-                    __syncwarp();
-                    for (int p0 = 0; p0 < total; p0 += 32) {
-                        // entry holding candidate p = p0 + lane: the live entries ending at or before p
-                        const int b = inc - p0;
-                        const int base = __popc(__ballot_sync(FULL, live && b <= 0));
-                        const unsigned M = __reduce_or_sync(FULL, (live && b > 0 && b < 32) ? (1u << b) : 0u);
-                        const int p = p0 + lane;
-                        bool alive = false;
-                        float4 xj = far;
-                        int l = 0, npl = 0;
-                        if (p < total) {
-                            const int o = base + __popc(M & le);
-                            const float4 e = w.ed[o];
-                            l = p + w.eb[o];
-                            npl = __float_as_int(e.w);
-                            float4 xl = a.xloc[l];
-                            if (XF) {
-                                const float3 c = rot32(xR[npl], xl.x, xl.y, xl.z);
-                                xl.x = c.x; xl.y = c.y; xl.z = c.z;
-                            }
-                            xj = make_float4(xl.x + e.x, xl.y + e.y, xl.z + e.z, xl.w);
-                            const float cx = xj.x - sI.x, cy = xj.y - sI.y, cz = xj.z - sI.z;
-                            alive = cx * cx + cy * cy + cz * cz <= cull_i;
-                        }
-                        push(alive, xj, l, npl);
-                    }
-                    __syncwarp();
-                }
+                walk_runs<XF, true>(a, w.ed, w.eb, w.cnt, xR, e0, e1, ni, oI, sI, rcut, cull_i, lane, push);
                 if (qn > 0) run(qn);
                 // forces on the chunk's molecules: transposed warp sum, one vector atomic each, k-side virial
                 chunk_reduce<NI_>(fi, lane);
@@ -848,162 +866,378 @@ __global__ void __launch_bounds__(256) unsort_forces(const int *inv, int64_t n, 
 
 // ---------------------------------------------------------------- adjoint
 // Per pair with r = x_k - x_l', f = g(r^2) r, g = 24 e inv s3 (2 s3 - 1):
-//   J = df/dr = g I + 2 g' r r^T,  g' = dg/d(r^2) = 24 e inv^2 (4 s3 - 14 s6).
-// With w = v_k - v_l (v = dL/dF; every scheduled pair carries Newton's third
-// law, periodic image pairs included): dL/dr = J w, x_k gets +J w and the
-// partner (for an image pair, its source molecule) gets -J w;
-// dL/d eps_ab = g (r.w) / eps_ab and dL/d sigma_ab = 24 e inv (24 s6 - 6 s3) (r.w) / sigma_ab,
-// chained to the species parameters through the mixing rule.
+//   J = df/dr = g I + 2 g' r r^T,  g' = dg/d(r^2) = 24 e inv^2 s3 (4 - 14 s3).
+// For L = sum_k v_k . F_k (v = dL/dF), a pair evaluated with Newton's third
+// law (every scheduled pair under box periodicity, image pairs included)
+// adds (v_k - v_l) . f, so with w = v_k - v_l x_k gets +J w and the partner
+// (for an image pair, its source molecule) gets -J w.  A pair whose partner
+// is referred through a general transform t (x_l' = y_t + R_t x_l, §2.2.2)
+// acts on x_k only and is met again from the other side: w = v_k, and the
+// source molecule gets -R_t^T J w.  dL/d eps_ab = g (r.w) / eps_ab and
+// dL/d sigma_ab = 24 e inv s3 (24 s3 - 6) (r.w) / sigma_ab, chained to the
+// species parameters through the mixing rule (eps_ab = sqrt(eps_a eps_b),
+// sigma_ab = (sigma_a + sigma_b) / 2).  Pair terms are recomputed over the
+// forward call's pair set (same schedule, same cut-off decisions).
+//
+// Species sums: slots [0, 8) hold dL/d eps_s and [8, 16) dL/d sigma_s; each
+// warp adds its totals to the striped FP64 rows of the forward kernels, and
+// finish_bwd adds the rows.
+constexpr int kGradSlots = 2 * kMaxSpecies;
+static_assert(kGradSlots <= kParts, "gradient slots must fit a stripe row");
+
 struct BwdTab {
     double eps, sig2, inv_eps, inv_sig, fa, fb;   // fa, fb: d eps_ab / d eps_a, d eps_ab / d eps_b
 };
 
 struct BwdArgs {
     PairArgs p;
-    BwdTab t[kMaxSpeciesBwd * kMaxSpeciesBwd];
+    BwdTab t[kMaxSpecies * kMaxSpecies];
+    float4 tb[kMaxSpecies * kMaxSpecies];   // FP32 chain factors {fa / eps_ab, fb / eps_ab, 1 / (2 sigma_ab), 0}
+    double e1, s1;                          // one species: 1 / eps, 1 / sigma
     int S;
 };
 
-template <class R> struct BwdLane {
-    R ge[kMaxSpeciesBwd], gs[kMaxSpeciesBwd];
-};
+// A warp's species-gradient totals (lane q < kGradSlots holds slot q) into its stripe row.
+__device__ __forceinline__ void grads_to_stripe(const PairArgs &a, int gwarp, double g, int lane) {
+    double *row = a.acc + kAccStripes + (size_t)(gwarp % kStripes) * kParts;
+    if (lane < kGradSlots && g != 0.0) atomicAdd(row + lane, g);
+}
 
-template <class R>
-__device__ __forceinline__ void bwd_pair(const BwdTab *tab, int S, R rx, R ry, R rz, R r2, int spi, int spj, R wx,
-                                         R wy, R wz, R3<R> &gi, R3<R> &gj, BwdLane<R> &gl) {
-    spi &= kMaxSpeciesBwd - 1;
-    spj &= kMaxSpeciesBwd - 1;
-    const BwdTab &t = tab[spi * kMaxSpeciesBwd + spj];
-    R eps = (R)t.eps;
-    R inv = R(1) / r2;
-    R s = (R)t.sig2 * inv;
-    R s3 = s * s * s, s6 = s3 * s3;
-    R g = R(24) * eps * inv * s3 * (R(2) * s3 - R(1));
-    R gp = R(24) * eps * inv * inv * (R(4) * s3 - R(14) * s6);
-    R rw = rx * wx + ry * wy + rz * wz;
-    R c = R(2) * gp * rw;
-    R jx = g * wx + c * rx, jy = g * wy + c * ry, jz = g * wz + c * rz;
-    gi.x += jx; gi.y += jy; gi.z += jz;
-    gj.x -= jx; gj.y -= jy; gj.z -= jz;
-    R Ge = g * rw * (R)t.inv_eps;
-    R Gs = R(24) * eps * inv * (R(24) * s6 - R(6) * s3) * rw * (R)t.inv_sig;
+// R^T g for a row-major FP32 rotation R
+__device__ __forceinline__ float3 rot32t(const float *R, float x, float y, float z) {
+    return make_float3(fmaf(R[0], x, fmaf(R[3], y, R[6] * z)), fmaf(R[1], x, fmaf(R[4], y, R[7] * z)),
+                       fmaf(R[2], x, fmaf(R[5], y, R[8] * z)));
+}
+
+// One pair's adjoint terms (FP32 body, branch-free but for the species
+// slots): +J w to gi3, -J w to gj; (r.w) g and (r.w) dg/d sigma to the species
+// sums (one species: ea, sa in registers; several: the lane's column of the
+// warp's slots gsl).
+template <bool MULTI>
+__device__ __forceinline__ void bwd32(const float4 *tab, const float4 *tb, float4 t0, int spi, int spj, float rx,
+                                      float ry, float rz, float r2, bool in, float wx, float wy, float wz,
+                                      float *gi3, R3<float> &gj, float &ea, float &sa, float (*gsl)[32], int lane) {
+    const float4 t = MULTI ? tab[spi * kMaxSpecies + spj] : t0;
+    const float inv = rcp_approx(r2);
+    const float s = t.x * inv, s3 = s * s * s;
+    const float a24 = (t.y * inv) * s3;
+    const float rw = fmaf(rz, wz, fmaf(ry, wy, rx * wx));
+    const float fs = in ? a24 * fmaf(2.f, s3, -1.f) : 0.f;
+    const float c = in ? (2.f * a24 * inv) * fmaf(-14.f, s3, 4.f) * rw : 0.f;
+    const float jx = fmaf(fs, wx, c * rx), jy = fmaf(fs, wy, c * ry), jz = fmaf(fs, wz, c * rz);
+    gi3[0] += jx;
+    gi3[1] += jy;
+    gi3[2] += jz;
+    gj.x -= jx;
+    gj.y -= jy;
+    gj.z -= jz;
+    const float A = fs * rw;
+    const float B = in ? a24 * fmaf(24.f, s3, -6.f) * rw : 0.f;
+    if (MULTI) {
+        if (in) {
+            const int p = spi & (kMaxSpecies - 1), q = spj & (kMaxSpecies - 1);
+            const float4 f = tb[p * kMaxSpecies + q];
+            gsl[p][lane] = fmaf(A, f.x, gsl[p][lane]);
+            gsl[q][lane] = fmaf(A, f.y, gsl[q][lane]);
+            gsl[kMaxSpecies + p][lane] = fmaf(B, f.z, gsl[kMaxSpecies + p][lane]);
+            gsl[kMaxSpecies + q][lane] = fmaf(B, f.z, gsl[kMaxSpecies + q][lane]);
+        }
+    } else {
+        ea += A;
+        sa += B;
+    }
+}
+
+// One lane's partner (xj, its v in vl; vl = 0 for a one-sided pair) against
+// the chunk: the forward's pair set (FP32 test, FP64 re-decision in the
+// 1e-5 rc^2 band, SAME: chunk molecules below lmax_k only).
+template <int NI_, bool MULTI, bool SAME, bool XF>
+__device__ __forceinline__ unsigned bwd_partner(const PairArgs &a, const float4 *tab, const float4 *tb,
+                                                const float4 *xi, const float4 *vi, int ni, int k0, float4 xj,
+                                                float4 vl, int l, int np, int lmax_k, float (&gi)[3 * NI_],
+                                                R3<float> &gj, float &ea, float &sa, float (*gsl)[32], int lane) {
+    unsigned nin = 0, bm = 0;
+    const float4 t0 = tab[0];
 #pragma unroll
-    for (int q = 0; q < kMaxSpeciesBwd; ++q) {
-        if (q < S) {
-            gl.ge[q] += (spi == q ? Ge * (R)t.fa : R(0)) + (spj == q ? Ge * (R)t.fb : R(0));
-            gl.gs[q] += (spi == q ? R(0.5) * Gs : R(0)) + (spj == q ? R(0.5) * Gs : R(0));
+    for (int t = 0; t < NI_; ++t) {
+        if (t < ni) {
+            const float4 x = xi[t], vk = vi[t];
+            const float rx = x.x - xj.x, ry = x.y - xj.y, rz = x.z - xj.z;
+            const float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
+            const bool ok = !SAME || k0 + t < lmax_k;
+            const bool in = ok && r2 < a.rc2_lo;
+            if (ok && !in && r2 < a.rc2_hi) bm |= 1u << t;
+            bwd32<MULTI>(tab, tb, t0, __float_as_int(x.w), __float_as_int(xj.w), rx, ry, rz, r2, in, vk.x - vl.x,
+                         vk.y - vl.y, vk.z - vl.z, &gi[3 * t], gj, ea, sa, gsl, lane);
+            nin += in;
         }
     }
+    if (__any_sync(0xffffffffu, bm != 0)) {
+#pragma unroll
+        for (int t = 0; t < NI_; ++t) {
+            if ((bm >> t) & 1u) {
+                if (XF ? band_in_xf(a, k0 + t, l, np) : band_in(a, k0 + t, l, np)) {
+                    const float4 x = xi[t], vk = vi[t];
+                    const float rx = x.x - xj.x, ry = x.y - xj.y, rz = x.z - xj.z;
+                    const float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
+                    bwd32<MULTI>(tab, tb, t0, __float_as_int(x.w), __float_as_int(xj.w), rx, ry, rz, r2, true,
+                                 vk.x - vl.x, vk.y - vl.y, vk.z - vl.z, &gi[3 * t], gj, ea, sa, gsl, lane);
+                    nin++;
+                }
+            }
+        }
+    }
+    return nin;
 }
 
-template <class R> struct Pos;
-template <> struct Pos<float> {
-    // positions of k (I frame) and partner l (its frame + Delta)
-    __device__ static void sep(const PairArgs &a, const float4 &xk, int l, float4 d, int np, int kidx, float &rx,
-                               float &ry, float &rz, float &r2, bool &in) {
-        float4 xl = a.xloc[l];
-        rx = xk.x - (xl.x + d.x);
-        ry = xk.y - (xl.y + d.y);
-        rz = xk.z - (xl.z + d.z);
-        r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
-        in = r2 < a.rc2_hi && (r2 < a.rc2_lo || band_in(a, kidx, l, np));
-    }
+template <int NI_>
+struct WarpB32 {
+    float4 qx[kRing];    // queued partners: position in I's frame (.w species bits)
+    int2 ql[kRing];      // queued partners: binned index, image code (kSameCell: same cell)
+    float4 ed[32];       // live runs of the batch (walk_runs)
+    int eb[32];
+    float4 xi[NI_];      // molecules of the current chunk
+    float4 vi[NI_];      // ... and their v = dL/dF
 };
-template <> struct Pos<double> {
-    __device__ static void sep(const PairArgs &a, const float4 &, int l, float4, int np, int kidx, double &rx,
-                               double &ry, double &rz, double &r2, bool &in) {
-        sep64(a.xs64 + 3 * (size_t)kidx, a.xs64 + 3 * (size_t)l, a.L, np, rx, ry, rz, r2);
-        in = r2 < a.rc2_d;
-    }
-};
 
-template <class R>
-__device__ __forceinline__ void ldv(const void *vs, int s, R &x, R &y, R &z) {
-    if (sizeof(R) == 4) {
-        float4 v = ((const float4 *)vs)[s];
-        x = (R)v.x; y = (R)v.y; z = (R)v.z;
-    } else {
-        const double *v = (const double *)vs + 4 * (size_t)s;
-        x = (R)v[0]; y = (R)v[1]; z = (R)v[2];
-    }
-}
-template <class R>
-__device__ __forceinline__ void add_grad(void *g, int s, R x, R y, R z) {
-    if (sizeof(R) == 4) atomicAdd((float4 *)g + s, make_float4((float)x, (float)y, (float)z, 0.f));
-    else atomic_add3((double *)g + 4 * (size_t)s, (double)x, (double)y, (double)z);
-}
-
-// Warp per cell I, lanes over the (molecule of I, partner molecule) pairs of
-// one schedule entry at a time; the adjoint is not on the per-step path.
-template <class R>
-__global__ void __launch_bounds__(kPairThreads) pair_bwd(BwdArgs b) {
+// FP32 adjoint: the forward kernel's schedule walk (persistent grid, cells
+// claimed from a counter, runs culled and queued, one partner per lane
+// against the chunk), with the adjoint pair body.
+template <int NI_, bool MULTI, bool XF>
+__global__ void __launch_bounds__(kThreads32, 4) pair_bwd32(BwdArgs b) {
     const PairArgs &a = b.p;
-    __shared__ BwdTab tab[kMaxSpeciesBwd * kMaxSpeciesBwd];
-    __shared__ double red[kWarps][2 * kMaxSpeciesBwd];
-    for (int i = threadIdx.x; i < kMaxSpeciesBwd * kMaxSpeciesBwd; i += blockDim.x) tab[i] = b.t[i];
+    __shared__ float4 tab[kMaxSpecies * kMaxSpecies];
+    __shared__ float4 tbs[MULTI ? kMaxSpecies * kMaxSpecies : 1];
+    __shared__ WarpB32<NI_> wsh[kWarps32];
+    __shared__ float slots[kWarps32][MULTI ? kGradSlots : 1][32];
+    __shared__ float xR[XF ? kMaxXf : 1][9];
+    for (int i = threadIdx.x; i < kMaxSpecies * kMaxSpecies; i += blockDim.x) {
+        tab[i] = a.tab.f[i];
+        if (MULTI) tbs[i] = b.tb[i];
+    }
+    if (XF)
+        for (int i = threadIdx.x; i < 9 * kMaxXf; i += blockDim.x)
+            xR[i / 9][i % 9] = (a.xft && i / 9 < a.n_xf) ? a.xft[i / 9].Rf[i % 9] : 0.f;
+    for (int i = threadIdx.x; i < kWarps32 * (MULTI ? kGradSlots : 1) * 32; i += blockDim.x)
+        (&slots[0][0][0])[i] = 0.f;
     __syncthreads();
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int nwarps = gridDim.x * kWarps;
-    BwdLane<double> tot;
-    for (int q = 0; q < kMaxSpeciesBwd; ++q) tot.ge[q] = tot.gs[q] = 0;
-    for (int I = blockIdx.x * kWarps + wib; I < a.C; I += nwarps) {
+    WarpB32<NI_> &w = wsh[wib];
+    float(*gsl)[32] = slots[wib];
+    const unsigned FULL = 0xffffffffu, lt = (1u << lane) - 1u;
+    const float4 far = make_float4(1e18f, 1e18f, 1e18f, 0.f), zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float rcut = sqrtf(a.rc2_hi);
+    const float4 *vs = (const float4 *)a.vs;
+    float4 *gacc = (float4 *)a.facc;
+    float ea = 0.f, sa = 0.f;
+    double dg = 0.0;     // lane q < kGradSlots: slot q
+    // FP32 species sums into the lane's FP64 slot (every few cells)
+    auto flush = [&]() {
+        if (MULTI) {
+            __syncwarp();
+            if (lane < kGradSlots) {
+                double t = 0.0;
+                for (int c = 0; c < 32; ++c) {
+                    const int cc = (c + lane) & 31;
+                    t += (double)gsl[lane][cc];
+                    gsl[lane][cc] = 0.f;
+                }
+                dg += t;
+            }
+            __syncwarp();
+        } else {
+            const float e = warp_sum(ea), s = warp_sum(sa);
+            if (lane == 0) dg += (double)e * b.e1;
+            if (lane == kMaxSpecies) dg += (double)s * b.s1;
+            ea = sa = 0.f;
+        }
+    };
+    int ncell = 0;
+    int I0 = lane == 0 ? (int)atomicAdd(a.next_cell, (unsigned)kGrab) : 0;
+    I0 = __shfl_sync(FULL, I0, 0);
+    while (I0 < a.C) {
+        const int Inext = lane == 0 ? (int)atomicAdd(a.next_cell, (unsigned)kGrab) : 0;
+        const int Iend = min(I0 + kGrab, a.C);
+        for (int I = I0; I < Iend; ++I) {
+            const int s0 = a.cell_off[I], nI = a.cell_off[I + 1] - s0;
+            if (nI == 0) continue;
+            const int e0 = a.run_off[I], e1 = a.run_off[I + 1];
+            const float4 sI = a.sph[I];
+            const int *oI = a.orgm + 3 * I;
+            const float cull_i = (rcut + sI.w) * (rcut + sI.w) * 1.00002f + 1e-5f;
+            for (int i0 = 0; i0 < nI; i0 += NI_) {
+                const int ni = min(NI_, nI - i0), k0 = s0 + i0;
+                __syncwarp();
+                if (lane < ni) {
+                    w.xi[lane] = a.xloc[k0 + lane];
+                    w.vi[lane] = vs[k0 + lane];
+                }
+                float gi[3 * NI_];
+#pragma unroll
+                for (int i = 0; i < 3 * NI_; ++i) gi[i] = 0.f;
+                int head = 0, qn = 0;
+                __syncwarp();
+                auto run = [&](int count) {
+                    const int s = (head + lane) & (kRing - 1);
+                    const bool valid = lane < count;
+                    const float4 xj = valid ? w.qx[s] : far;
+                    const int2 q = valid ? w.ql[s] : make_int2(0, 0);
+                    const bool same = q.y == kSameCell;
+                    const bool one = XF && !same && q.y != 0;
+                    const float4 vl = valid && !one ? vs[q.x] : zero;
+                    R3<float> gj = {0.f, 0.f, 0.f};
+                    const unsigned nin =
+                        __any_sync(FULL, same)
+                            ? bwd_partner<NI_, MULTI, true, XF>(a, tab, tbs, w.xi, w.vi, ni, k0, xj, vl, q.x,
+                                                                same ? 0 : q.y, same ? q.x : 0x7fffffff, gi, gj, ea,
+                                                                sa, gsl, lane)
+                            : bwd_partner<NI_, MULTI, false, XF>(a, tab, tbs, w.xi, w.vi, ni, k0, xj, vl, q.x, q.y, 0,
+                                                                 gi, gj, ea, sa, gsl, lane);
+                    if (nin) {
+                        if (one) {
+                            const float3 r = rot32t(xR[q.y], gj.x, gj.y, gj.z);
+                            gj.x = r.x; gj.y = r.y; gj.z = r.z;
+                        }
+                        atomicAdd(gacc + q.x, make_float4(gj.x, gj.y, gj.z, 0.f));
+                    }
+                    head = (head + count) & (kRing - 1);
+                    __syncwarp();
+                };
+                auto push = [&](bool alive, float4 xj, int l, int np) {
+                    const unsigned bal = __ballot_sync(FULL, alive);
+                    if (alive) {
+                        const int s = (head + qn + __popc(bal & lt)) & (kRing - 1);
+                        w.qx[s] = xj;
+                        w.ql[s] = make_int2(l, np);
+                    }
+                    qn += __popc(bal);
+                    __syncwarp();
+                    if (qn >= 32) {
+                        run(32);
+                        qn -= 32;
+                    }
+                };
+                for (int lb = i0 + 1; lb < nI; lb += 32) {
+                    const int li = lb + lane;
+                    const bool alive = li < nI;
+                    push(alive, alive ? a.xloc[s0 + li] : far, s0 + li, kSameCell);
+                }
+                walk_runs<XF, false>(a, w.ed, w.eb, nullptr, xR, e0, e1, ni, oI, sI, rcut, cull_i, lane, push);
+                if (qn > 0) run(qn);
+                chunk_reduce<NI_>(gi, lane);
+                const int t = lane / (32 / NI_);
+                if ((lane & (32 / NI_ - 1)) == 0 && t < ni)
+                    atomicAdd(gacc + k0 + t, make_float4(gi[0], gi[1], gi[2], 0.f));
+            }
+            if (++ncell == 4) {
+                ncell = 0;
+                flush();
+            }
+        }
+        I0 = __shfl_sync(FULL, Inext, 0);
+    }
+    flush();
+    grads_to_stripe(a, blockIdx.x * kWarps32 + wib, dg, lane);
+}
+
+// FP64 pair terms (same formulas)
+template <bool MULTI>
+__device__ __forceinline__ void bwd64(const BwdTab *tab, int spi, int spj, double rx, double ry, double rz, double r2,
+                                      double wx, double wy, double wz, R3<double> &gi, R3<double> &gj, double &ea,
+                                      double &sa, double (*gsl)[32], int lane) {
+    spi &= kMaxSpecies - 1;
+    spj &= kMaxSpecies - 1;
+    const BwdTab &t = tab[MULTI ? spi * kMaxSpecies + spj : 0];
+    const double inv = 1.0 / r2;
+    const double s = t.sig2 * inv, s3 = s * s * s;
+    const double a24 = 24.0 * t.eps * inv * s3;
+    const double fs = a24 * (2.0 * s3 - 1.0);
+    const double rw = rx * wx + ry * wy + rz * wz;
+    const double c = 2.0 * a24 * inv * (4.0 - 14.0 * s3) * rw;
+    const double jx = fs * wx + c * rx, jy = fs * wy + c * ry, jz = fs * wz + c * rz;
+    gi.x += jx; gi.y += jy; gi.z += jz;
+    gj.x -= jx; gj.y -= jy; gj.z -= jz;
+    const double A = fs * rw * t.inv_eps;
+    const double B = a24 * (24.0 * s3 - 6.0) * rw * t.inv_sig;
+    if (MULTI) {
+        gsl[spi][lane] += A * t.fa;
+        gsl[spj][lane] += A * t.fb;
+        gsl[kMaxSpecies + spi][lane] += 0.5 * B;
+        gsl[kMaxSpecies + spj][lane] += 0.5 * B;
+    } else {
+        ea += A;
+        sa += B;
+    }
+}
+
+// FP64 adjoint: one warp per cell I, lanes over the (molecule of I, partner
+// molecule) pairs of one schedule entry at a time; pairs within rc are
+// decided in FP64 exactly as the forward FP64 kernel decides them.
+template <bool MULTI, bool XF>
+__global__ void __launch_bounds__(kPairThreads) pair_bwd64(BwdArgs b) {
+    const PairArgs &a = b.p;
+    __shared__ BwdTab tab[kMaxSpecies * kMaxSpecies];
+    __shared__ double slots[kWarps][MULTI ? kGradSlots : 1][32];
+    for (int i = threadIdx.x; i < kMaxSpecies * kMaxSpecies; i += blockDim.x) tab[i] = b.t[i];
+    for (int i = threadIdx.x; i < kWarps * (MULTI ? kGradSlots : 1) * 32; i += blockDim.x)
+        (&slots[0][0][0])[i] = 0.0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int gwarp = blockIdx.x * kWarps + wib, nwarps = gridDim.x * kWarps;
+    double(*gsl)[32] = slots[wib];
+    const double *vs = (const double *)a.vs;
+    double *gacc = (double *)a.facc;
+    double ea = 0.0, sa = 0.0;
+    for (int I = gwarp; I < a.C; I += nwarps) {
         const int sI = a.cell_off[I], nI = a.cell_off[I + 1] - sI;
         if (nI == 0) continue;
         const int e0 = a.work_off[I], e1 = a.work_off[I + 1];
-        BwdLane<R> gl;
-        for (int q = 0; q < kMaxSpeciesBwd; ++q) gl.ge[q] = gl.gs[q] = R(0);
         // entry e0 - 1 stands for the cell itself (pairs k' > k)
         for (int e = e0 - 1; e < e1; ++e) {
-            int J, np = 0;
-            float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (e < e0) {
-                J = I;
-            } else {
-                WorkEntry we = a.work[e];
+            int J = I, np = 0;
+            if (e >= e0) {
+                const WorkEntry we = a.work[e];
                 J = we.j;
                 np = we.n;
-                const float3 s3 = cell_shift(a, a.orgm + 3 * I, J, np);
-                d = make_float4(s3.x, s3.y, s3.z, 0.f);
             }
+            const bool one = XF && np != 0;
             const int sJ = a.cell_off[J], nJ = a.cell_off[J + 1] - sJ;
             const int npairs = nI * nJ;
             for (int p = lane; p < npairs; p += 32) {
-                int ki = p / nJ, lj = p - ki * nJ;
+                const int ki = p / nJ, lj = p - ki * nJ;
                 if (e < e0 && lj <= ki) continue;
-                int k = sI + ki, l = sJ + lj;
-                float4 xk = a.xloc[k];
-                R rx, ry, rz, r2;
-                bool in;
-                Pos<R>::sep(a, xk, l, d, np, k, rx, ry, rz, r2, in);
-                if (!in) continue;
-                R vkx, vky, vkz, vlx, vly, vlz;
-                ldv<R>(a.vs, k, vkx, vky, vkz);
-                ldv<R>(a.vs, l, vlx, vly, vlz);
-                R3<R> gi = {0, 0, 0}, gj = {0, 0, 0};
-                bwd_pair<R>(tab, b.S, rx, ry, rz, r2, __float_as_int(xk.w), __float_as_int(a.xloc[l].w), vkx - vlx,
-                            vky - vly, vkz - vlz, gi, gj, gl);
-                add_grad<R>(a.facc, k, gi.x, gi.y, gi.z);
-                add_grad<R>(a.facc, l, gj.x, gj.y, gj.z);
+                const int k = sI + ki, l = sJ + lj;
+                double rx, ry, rz, r2;
+                sep64x<XF>(a, a.xs64 + 3 * (size_t)k, a.xs64 + 3 * (size_t)l, np, rx, ry, rz, r2);
+                if (!(r2 < a.rc2_d)) continue;
+                const double *vk = vs + 4 * (size_t)k, *vl = vs + 4 * (size_t)l;
+                const double wx = one ? vk[0] : vk[0] - vl[0];
+                const double wy = one ? vk[1] : vk[1] - vl[1];
+                const double wz = one ? vk[2] : vk[2] - vl[2];
+                R3<double> gi = {0, 0, 0}, gj = {0, 0, 0};
+                bwd64<MULTI>(tab, __float_as_int(a.xloc[k].w), __float_as_int(a.xloc[l].w), rx, ry, rz, r2, wx, wy,
+                             wz, gi, gj, ea, sa, gsl, lane);
+                atomic_add3(gacc + 4 * (size_t)k, gi.x, gi.y, gi.z);
+                if (one) {
+                    const double *R = a.xft[np].R;
+                    atomic_add3(gacc + 4 * (size_t)l, R[0] * gj.x + R[3] * gj.y + R[6] * gj.z,
+                                R[1] * gj.x + R[4] * gj.y + R[7] * gj.z, R[2] * gj.x + R[5] * gj.y + R[8] * gj.z);
+                } else {
+                    atomic_add3(gacc + 4 * (size_t)l, gj.x, gj.y, gj.z);
+                }
             }
         }
-        for (int q = 0; q < kMaxSpeciesBwd; ++q) {
-            tot.ge[q] += (double)gl.ge[q];
-            tot.gs[q] += (double)gl.gs[q];
-        }
     }
-    for (int q = 0; q < kMaxSpeciesBwd; ++q) {
-        double x = warp_sum(tot.ge[q]), y = warp_sum(tot.gs[q]);
-        if (lane == 0) {
-            red[wib][q] = x;
-            red[wib][kMaxSpeciesBwd + q] = y;
-        }
+    double dg = 0.0;
+    if (MULTI) {
+        __syncwarp();
+        if (lane < kGradSlots)
+            for (int c = 0; c < 32; ++c) dg += gsl[lane][(c + lane) & 31];
+    } else {
+        const double e = warp_sum(ea), s = warp_sum(sa);
+        dg = lane == 0 ? e : lane == kMaxSpecies ? s : 0.0;
     }
-    __syncthreads();
-    if (threadIdx.x < 2 * kMaxSpeciesBwd) {
-        double s = 0;
-        for (int w = 0; w < kWarps; ++w) s += red[w][threadIdx.x];
-        atomicAdd(a.acc + 16 + threadIdx.x, s);
-    }
+    grads_to_stripe(a, gwarp, dg, lane);
 }
 
 template <class T>
@@ -1020,11 +1254,19 @@ __global__ void __launch_bounds__(256) gather_grad(const int *order, int64_t nb,
     }
 }
 
-__global__ void finish_bwd(const double *acc, int S, double *ge, double *gs) {
-    int i = threadIdx.x;
-    if (i < S) {
-        if (ge) ge[i] = acc[16 + i];
-        if (gs) gs[i] = acc[16 + kMaxSpeciesBwd + i];
+// Totals of the species-gradient slots over the stripe rows (one warp per slot).
+__global__ void __launch_bounds__(kGradSlots * 32) finish_bwd(const double *acc, int S, double *ge, double *gs) {
+    const int i = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double v = 0.0;
+    for (int r = lane; r < kStripes; r += 32) v += acc[kAccStripes + r * kParts + i];
+    v = warp_sum(v);
+    const int q = i % kMaxSpecies;
+    if (lane == 0 && q < S) {
+        if (i < kMaxSpecies) {
+            if (ge) ge[q] = v;
+        } else if (gs) {
+            gs[q] = v;
+        }
     }
 }
 
@@ -1151,6 +1393,40 @@ int launch_fwd32(const PairArgs &a, bool multi, bool shift, cudaStream_t st) {
     return a.xf ? launch_fwd32_x<NI_, true>(a, multi, shift, st) : launch_fwd32_x<NI_, false>(a, multi, shift, st);
 }
 
+// Launch the FP32 adjoint on a persistent grid (every SM filled to its
+// occupancy); returns the number of blocks.
+template <int NI_, bool MULTI, bool XF>
+int launch_bwd32_t(const BwdArgs &b, cudaStream_t st) {
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    if (!cache[dev]) {
+        int sms = 0, per = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pair_bwd32<NI_, MULTI, XF>, kThreads32, 0);
+        cache[dev] = std::max(1, sms * std::max(1, per));
+    }
+    const int grid = std::min(cache[dev], std::max(1, (b.p.C + kWarps32 - 1) / kWarps32));
+    pair_bwd32<NI_, MULTI, XF><<<grid, kThreads32, 0, st>>>(b);
+    return grid;
+}
+
+template <int NI_>
+int launch_bwd32(const BwdArgs &b, bool multi, cudaStream_t st) {
+    if (b.p.xf) return multi ? launch_bwd32_t<NI_, true, true>(b, st) : launch_bwd32_t<NI_, false, true>(b, st);
+    return multi ? launch_bwd32_t<NI_, true, false>(b, st) : launch_bwd32_t<NI_, false, false>(b, st);
+}
+
+void launch_bwd64(const BwdArgs &b, bool multi, int grid, cudaStream_t st) {
+    if (b.p.xf) {
+        if (multi) pair_bwd64<true, true><<<grid, kPairThreads, 0, st>>>(b);
+        else pair_bwd64<false, true><<<grid, kPairThreads, 0, st>>>(b);
+    } else {
+        if (multi) pair_bwd64<true, false><<<grid, kPairThreads, 0, st>>>(b);
+        else pair_bwd64<false, false><<<grid, kPairThreads, 0, st>>>(b);
+    }
+}
+
 }  // namespace
 }  // namespace aica
 
@@ -1210,19 +1486,15 @@ extern "C" aica_status aica_forces_backward(aica_mesh *m, const aica_lj *lj, aic
     }
     if (prec != AICA_FP32 && prec != AICA_FP64) { set_error("aica_forces_backward: bad precision"); return AICA_ERR_INVALID_ARG; }
     if (!m->built || !m->binned) { set_error("aica_forces_backward: build the lists and bin the molecules first"); return AICA_ERR_NOT_BUILT; }
-    if (m->n_xf > 0) {
-        set_error("aica_forces_backward: the adjoint supports box periodicity only (general transforms are set)");
-        return AICA_ERR_INVALID_ARG;
-    }
     cudaStream_t st = (cudaStream_t)stream;
     BwdArgs b{};
-    aica_status s = fill_params(m, lj, kMaxSpeciesBwd, b.p);
+    aica_status s = fill_params(m, lj, kMaxSpecies, b.p);
     if (s != AICA_OK) return s;
     fill_common(m, b.p);
     b.S = b.p.S;
     for (int i = 0; i < b.S; ++i)
         for (int j = 0; j < b.S; ++j) {
-            BwdTab &t = b.t[i * kMaxSpeciesBwd + j];
+            BwdTab &t = b.t[i * kMaxSpecies + j];
             double e = sqrt(lj->eps[i] * lj->eps[j]), sg = 0.5 * (lj->sigma[i] + lj->sigma[j]);
             t.eps = e;
             t.sig2 = sg * sg;
@@ -1231,32 +1503,50 @@ extern "C" aica_status aica_forces_backward(aica_mesh *m, const aica_lj *lj, aic
             // d eps_ab / d eps_a = eps_ab / (2 eps_a)  (both halves when a == b)
             t.fa = lj->eps[i] > 0 ? e / (2.0 * lj->eps[i]) : 0.0;
             t.fb = lj->eps[j] > 0 ? e / (2.0 * lj->eps[j]) : 0.0;
+            b.tb[i * kMaxSpecies + j] = make_float4((float)(t.fa * t.inv_eps), (float)(t.fb * t.inv_eps),
+                                                    (float)(0.5 * t.inv_sig), 0.f);
         }
+    b.e1 = lj->eps[0] > 0 ? 1.0 / lj->eps[0] : 0.0;
+    b.s1 = 1.0 / lj->sigma[0];
+    b.p.next_cell = (unsigned *)(m->acc.as<double>() + 24);
     m->launches = 0;
     const int64_t n = m->n_mol;
-    const bool f64 = prec == AICA_FP64;
+    const bool f64 = prec == AICA_FP64, multi = b.S > 1;
     const size_t esz = f64 ? 4 * sizeof(double) : sizeof(float4);
     int nb = 0;
     AICA_CUDA(cudaMemcpyAsync(&nb, m->cell_off.as<int>() + m->n_cells, sizeof(int), cudaMemcpyDeviceToHost, st));
     AICA_CUDA(cudaStreamSynchronize(st));
+    int launches = 0;
     if (n > 0) {
         AICA_CUDA(cudaMemsetAsync(m->facc.p, 0, esz * n, st));
         if (nb > 0) {
             if (f64) gather_grad<double><<<(nb + 255) / 256, 256, 0, st>>>(m->order.as<int>(), nb, (const double *)grad_force, m->vsorted.p, 1);
             else gather_grad<float><<<(nb + 255) / 256, 256, 0, st>>>(m->order.as<int>(), nb, (const float *)grad_force, m->vsorted.p, 0);
+            launches++;
         }
     }
-    AICA_CUDA(cudaMemsetAsync(m->acc.as<double>() + 16, 0, 2 * kMaxSpeciesBwd * sizeof(double), st));
+    AICA_CUDA(cudaMemsetAsync(m->acc.p, 0, (kAccStripes + kStripes * kParts) * sizeof(double), st));
     b.p.vs = m->vsorted.p;
-    const int grid = pair_grid(b.p.C);
-    if (f64) pair_bwd<double><<<grid, kPairThreads, 0, st>>>(b);
-    else pair_bwd<float><<<grid, kPairThreads, 0, st>>>(b);
+    cudaEvent_t tstop;
+    AICA_CUDA(timing_begin(m, st, &tstop));
+    if (f64) {
+        launch_bwd64(b, multi, pair_grid(b.p.C), st);
+    } else {
+        if ((double)n < 5.0 * (double)b.p.C) launch_bwd32<4>(b, multi, st);
+        else launch_bwd32<8>(b, multi, st);
+    }
+    AICA_CUDA(timing_end(tstop, st));
+    launches++;
     if (n > 0) {
         if (f64) unsort_forces<double><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m->inv.as<int>(), n, m->facc.p, (double *)grad_pos, 1);
         else unsort_forces<float><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m->inv.as<int>(), n, m->facc.p, (float *)grad_pos, 0);
+        launches++;
     }
-    if (grad_eps || grad_sigma) finish_bwd<<<1, 32, 0, st>>>(m->acc.as<double>(), b.S, grad_eps, grad_sigma);
-    m->launches = 5;
+    if (grad_eps || grad_sigma) {
+        finish_bwd<<<1, kGradSlots * 32, 0, st>>>(m->acc.as<double>(), b.S, grad_eps, grad_sigma);
+        launches++;
+    }
+    m->launches = launches;
     AICA_CUDA(cudaGetLastError());
     if (!m->deferred) return check_flags(m, st);
     return AICA_OK;

@@ -97,3 +97,67 @@ def test_gradcheck_fp64():
     f = lambda p, e, s: LJForce.apply(p, e, s, m, sp, "fp64")
     # forces are summed with atomics, so repeated backward calls differ in the last bits
     assert torch.autograd.gradcheck(f, (pos, eps, sig), eps=1e-6, atol=1e-6, rtol=1e-5, nondet_tol=1e-12)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 2e-4)])
+@pytest.mark.parametrize("S", [3, 8])
+def test_vjp_up_to_eight_species(S, prec, tol):
+    c = _two_species_small(5 + S)
+    rng = np.random.default_rng(S)
+    c["species"] = rng.integers(0, S, len(c["pos"])).astype(np.int32)
+    c["eps"] = np.linspace(0.8, 1.6, S)
+    c["sigma"] = np.linspace(0.9, 1.1, S)
+    m, *_ = gpu_setup(c)
+    v = rng.normal(size=c["pos"].shape)
+    gx, ge, gs, _ = torch_ref.vjp(c["pos"], c["species"], c["eps"], c["sigma"], c["rc"], c["box"], v)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    gp, ge_g, gs_g = m.forces_backward(c["eps"], c["sigma"], torch.tensor(v, dtype=dt, device="cuda"), prec)
+    assert np.abs(gp.double().cpu().numpy() - gx).max() <= tol * np.abs(gx).max()
+    np.testing.assert_allclose(ge_g.cpu().numpy(), ge, rtol=tol, atol=tol * np.abs(ge).max())
+    np.testing.assert_allclose(gs_g.cpu().numpy(), gs, rtol=tol, atol=tol * np.abs(gs).max())
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 2e-4)])
+@pytest.mark.parametrize("S", [1, 2])
+def test_wedge_adjoint_matches_image_reference(S, prec, tol):
+    """General referring transforms: referred pairs are one-sided and the
+    source molecule's gradient is rotated back."""
+    from oracle import transforms as T
+    c = synth.wedge(3)
+    rng = np.random.default_rng(11)
+    sp = rng.integers(0, S, len(c["pos"])).astype(np.int32)
+    eps, sig = np.linspace(1.0, 1.5, S), np.linspace(1.0, 0.88, S)
+    m = Mesh(c["mesh"], c["box"])
+    m.set_transforms(c["transforms"])
+    m.build_lists(c["rc"], c["skin"])
+    pos = torch.tensor(c["pos"], dtype=torch.float64, device="cuda")
+    m.bin(pos, torch.tensor(sp, dtype=torch.int32, device="cuda"))
+    v = rng.normal(size=c["pos"].shape)
+    gx, ge, gs, _ = torch_ref.image_vjp(c["pos"], sp, eps, sig, c["rc"], T.closure(c["transforms"], 6), v)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    gp, ge_g, gs_g = m.forces_backward(eps, sig, torch.tensor(v, dtype=dt, device="cuda"), prec)
+    assert np.abs(gp.double().cpu().numpy() - gx).max() <= tol * np.abs(gx).max()
+    np.testing.assert_allclose(ge_g.cpu().numpy(), ge, rtol=tol, atol=tol * np.abs(ge).max())
+    np.testing.assert_allclose(gs_g.cpu().numpy(), gs, rtol=tol, atol=tol * np.abs(gs).max())
+    m.close()
+
+
+@pytest.mark.parametrize("cfg", ["c2", "c4"])
+def test_adjoint_full_size_sampled_rows(cfg):
+    """At the full c2 / c4 sizes: sampled rows of dL/dx against the oracle's
+    per-row gradient (both precisions), and the FP32 species sums against the
+    FP64 ones (pinned against the oracle at small sizes above)."""
+    c = synth.make(cfg, 0)
+    m, *_ = gpu_setup(c)
+    rng = np.random.default_rng(4)
+    v = rng.normal(size=c["pos"].shape)
+    idx = rng.choice(len(c["pos"]), 64, replace=False)
+    ref = torch_ref.vjp_rows(c["pos"], c["species"], c["eps"], c["sigma"], c["rc"], c["box"], v, idx)
+    vd = torch.tensor(v, device="cuda")
+    g64, ge64, gs64 = m.forces_backward(c["eps"], c["sigma"], vd, "fp64")
+    g32, ge32, gs32 = m.forces_backward(c["eps"], c["sigma"], vd.float(), "fp32")
+    scale = np.abs(ref).max()
+    assert np.abs(g64.cpu().numpy()[idx] - ref).max() <= 1e-10 * scale
+    assert np.abs(g32.double().cpu().numpy()[idx] - ref).max() <= 2e-4 * scale
+    np.testing.assert_allclose(ge32.cpu().numpy(), ge64.cpu().numpy(), rtol=1e-4)
+    np.testing.assert_allclose(gs32.cpu().numpy(), gs64.cpu().numpy(), rtol=1e-4)
