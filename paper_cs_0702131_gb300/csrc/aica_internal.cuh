@@ -25,6 +25,7 @@ enum : unsigned {
     kFlagOutside = 1u,   // a molecule lies in no cell
     kFlagSpecies = 2u,   // a species index is out of range
     kFlagCapacity = 4u,  // a per-cell capacity of a kernel was exceeded
+    kFlagTimeout = 8u,   // a bounded wait between blocks gave up
 };
 
 cudaError_t timing_begin(aica_mesh *m, cudaStream_t st, cudaEvent_t *stop);
@@ -157,10 +158,12 @@ struct aica_mesh {
     // Binned molecules (device), valid when binned.
     bool binned = false;
     int64_t n_mol = 0, cap_mol = 0;
-    aica::DevBuf cell_of, order, cell_off, fill, xloc, xs64, scratch_i32, inv;
+    aica::DevBuf cell_of, order, cell_off, fill, xloc, xs64, inv;
+    aica::DevBuf unsorted;                   // [n] binned slots before the in-cell sort (cells of a few molecules)
     int max_species = -1;                    // from the last checked binning, -1 if unknown
     aica::DevBuf sph;                        // [C] float4 molecule bounding sphere per cell (local frame)
     aica::DevBuf miss;                       // molecules whose previous cell no longer holds them
+    aica::DevBuf scan_state;                 // single-pass scan of the cell counts: ticket, epoch, tile words
     int64_t n_mol_prev = -1;                 // molecule count of the previous binning
     bool hint_valid = false;                 // cell_of holds that binning (a search hint)
     aica::DevBuf facc, vsorted;              // force / gradient accumulators in binned order

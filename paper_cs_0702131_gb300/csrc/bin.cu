@@ -472,7 +472,149 @@ __global__ void __launch_bounds__(256) bin_cells(BinArgs a, const int *cell_off,
     // largest species index (flags[1]) and out-of-range species (flags[0])
     const int mx = __reduce_max_sync(0xffffffffu, spmax);
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.flags, kFlagSpecies);
-    if (lane == 0) atomicMax((int *)a.flags + 1, mx);
+    if (lane == 0 && mx > 0) atomicMax((int *)a.flags + 1, mx);
+}
+
+// The same per slot, for cells of a few molecules.  Warp w owns the cells
+// whose first slot lies in its window of 32 slots [32 w, 32 w + 32); such a
+// cell ends before the first cell start of the next window, so the warp
+// stages the molecules of both windows (two slots per lane) in shared memory
+// and orders, gathers and bounds its cells there: rank = number of the
+// cell's original indices below the lane's, centre summed in rank order.  A
+// cell that covers the whole next window is done by one lane in global
+// memory.  `un` holds each cell's molecules in any order (bin_scatter_down);
+// `order` gets them sorted.  nbp points at the binned count (cell_off[C]).
+constexpr int kSlotWarps = 8;
+
+__device__ __forceinline__ float4 local_xloc(const BinArgs &a, int k, int c, int slot, double *xs64, int &spmax,
+                                             bool &bad) {
+    const int sp = a.species[k];
+    spmax = max(spmax, sp < 0 ? kMaxSpecies : sp);
+    bad |= (unsigned)sp >= (unsigned)kMaxSpecies;
+    double p[3];
+    for (int d = 0; d < 3; ++d) {
+        p[d] = a.pos[3 * (int64_t)k + d];
+        if (a.per[d]) p[d] = wrap_coord(p[d], a.L[d], a.Lkey[d]);
+        xs64[3 * (int64_t)slot + d] = p[d];
+    }
+    const double *o = a.orgm64 + 3 * c;
+    return make_float4((float)(p[0] - o[0]), (float)(p[1] - o[1]), (float)(p[2] - o[2]),
+                       __int_as_float(sp & (kMaxSpecies - 1)));
+}
+
+__device__ __forceinline__ float4 sphere_of(const float4 *x, int m) {
+    float cx = 0.f, cy = 0.f, cz = 0.f;
+    for (int j = 0; j < m; ++j) {
+        cx += x[j].x;
+        cy += x[j].y;
+        cz += x[j].z;
+    }
+    const float im = 1.f / (float)m;
+    cx *= im;
+    cy *= im;
+    cz *= im;
+    float rr = 0.f;
+    for (int j = 0; j < m; ++j) {
+        const float dx = x[j].x - cx, dy = x[j].y - cy, dz = x[j].z - cz;
+        rr = fmaxf(rr, dx * dx + dy * dy + dz * dz);
+    }
+    return make_float4(cx, cy, cz, sqrtf(rr) * (1.f + 1e-5f) + 1e-5f);
+}
+
+__global__ void __launch_bounds__(kSlotWarps * 32) bin_slots(BinArgs a, const int *cell_off, const int *nbp,
+                                                             const int *un, int *order, double *xs64, float4 *xloc,
+                                                             float4 *sph) {
+    __shared__ int sk[kSlotWarps][64];
+    __shared__ float4 sx[kSlotWarps][64];
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t w0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane;   // first slot of the window
+    const int nb = *nbp;
+    if (w0 >= nb) return;                 // whole warp
+    int k[2], c[2], s0[2], m[2];
+    bool st[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int64_t S = w0 + 32 * h + lane;
+        if (S < nb) {
+            k[h] = un[S];
+            c[h] = a.cell_of[k[h]];
+            s0[h] = cell_off[c[h]];
+            m[h] = cell_off[c[h] + 1] - s0[h];
+            st[h] = s0[h] == S;
+        } else {                          // past the binned slots: every slot is a boundary
+            k[h] = 0x7fffffff;
+            c[h] = -1;
+            s0[h] = (int)S;
+            m[h] = 0;
+            st[h] = true;
+        }
+    }
+    const unsigned b0 = __ballot_sync(FULL, st[0]), b1 = __ballot_sync(FULL, st[1]);
+    if (!b0) return;                      // the window lies inside a cell that starts earlier
+    const int bw = __ffs(b0) - 1;         // first cell start (window-local index)
+    const int last = 31 - __clz(b0);      // last cell start in the window
+    const bool tail = b1 == 0;            // that cell covers the whole next window
+    const int ew = tail ? last : 32 + __ffs(b1) - 1;
+    sk[wib][lane] = k[0];
+    sk[wib][32 + lane] = k[1];
+    __syncwarp();
+    int spmax = 0;
+    bool bad = false;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int i = 32 * h + lane;
+        if (i >= bw && i < ew && w0 + i < nb) {
+            const int ls = (int)(s0[h] - w0);
+            int rank = 0;
+            for (int j = 0; j < m[h]; ++j) rank += sk[wib][ls + j] < k[h] ? 1 : 0;
+            const int slot = s0[h] + rank;
+            order[slot] = k[h];
+            a.inv[k[h]] = slot;
+            const float4 x = local_xloc(a, k[h], c[h], slot, xs64, spmax, bad);
+            xloc[slot] = x;
+            sx[wib][ls + rank] = x;
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int i = 32 * h + lane;
+        if (i >= bw && i < ew && w0 + i < nb && st[h]) sph[c[h]] = sphere_of(&sx[wib][i], m[h]);
+    }
+    if (tail && lane == last && w0 + last < nb) {
+        // one lane: copy, sort by original index, gather and bound the cell
+        const int cs = s0[0], cm = m[0], cc = c[0];
+        for (int i = cs; i < cs + cm; ++i) {
+            const int v = un[i];
+            int j = i - 1;
+            while (j >= cs && order[j] > v) {
+                order[j + 1] = order[j];
+                --j;
+            }
+            order[j + 1] = v;
+        }
+        float sxs = 0.f, sys = 0.f, szs = 0.f;
+        for (int slot = cs; slot < cs + cm; ++slot) {
+            const int kk = order[slot];
+            a.inv[kk] = slot;
+            const float4 y = local_xloc(a, kk, cc, slot, xs64, spmax, bad);
+            xloc[slot] = y;
+            sxs += y.x; sys += y.y; szs += y.z;
+        }
+        const float im = 1.f / (float)cm;
+        sxs *= im; sys *= im; szs *= im;
+        float rr = 0.f;
+        for (int slot = cs; slot < cs + cm; ++slot) {
+            const float4 y = xloc[slot];
+            const float dx = y.x - sxs, dy = y.y - sys, dz = y.z - szs;
+            rr = fmaxf(rr, dx * dx + dy * dy + dz * dz);
+        }
+        sph[cc] = make_float4(sxs, sys, szs, sqrtf(rr) * (1.f + 1e-5f) + 1e-5f);
+    }
+    const int mx = __reduce_max_sync(FULL, spmax);
+    if (__any_sync(FULL, bad) && lane == 0) atomicOr(a.flags, kFlagSpecies);
+    if (lane == 0 && mx > 0) atomicMax((int *)a.flags + 1, mx);
 }
 
 }  // namespace
@@ -497,6 +639,7 @@ extern "C" aica_status aica_bin_molecules(aica_mesh *m, const double *pos, const
         int64_t cap = std::max<int64_t>(n, 1024);
         AICA_CUDA(m->cell_of.reserve(sizeof(int) * cap));
         AICA_CUDA(m->order.reserve(sizeof(int) * cap));
+        AICA_CUDA(m->unsorted.reserve(sizeof(int) * cap));
         AICA_CUDA(m->xloc.reserve(sizeof(float4) * cap));
         AICA_CUDA(m->inv.reserve(sizeof(int) * cap));
         AICA_CUDA(m->xs64.reserve(sizeof(double) * 3 * cap));
@@ -508,7 +651,6 @@ extern "C" aica_status aica_bin_molecules(aica_mesh *m, const double *pos, const
     AICA_CUDA(m->fill.reserve(sizeof(int) * (C + 1)));
     AICA_CUDA(m->sph.reserve(sizeof(float4) * C));
     AICA_CUDA(m->miss.reserve(sizeof(int) * (std::max<int64_t>(n, 1) + 1)));
-    AICA_CUDA(m->scratch_i32.reserve(sizeof(int) * (scan_work_items(C) + 8)));
     m->n_mol = n;
     BinArgs a{};
     a.n = n;
@@ -571,18 +713,24 @@ extern "C" aica_status aica_bin_molecules(aica_mesh *m, const double *pos, const
             m->launches += 1;
         }
     }
-    m->launches += exclusive_scan<int, int>(cnt, C, off, m->scratch_i32.as<int>(), st);
+    m->launches += exclusive_scan_1pass(cnt, C, off, m->scan_state.as<unsigned long long>(), m->flags.as<unsigned>(),
+                                        kFlagTimeout, st);
+    // wide cells are sorted in place in `order`; narrow ones go from `unsorted` to `order`
+    const bool wide = (double)n > 6.0 * (double)C;
+    int *slots_out = wide ? m->order.as<int>() : m->unsorted.as<int>();
     if (n > 0) {
-        bin_scatter_down<<<nb, 256, 0, st>>>(a.cell_of, n, off, cnt, m->order.as<int>());
+        bin_scatter_down<<<nb, 256, 0, st>>>(a.cell_of, n, off, cnt, slots_out);
         m->launches += 1;
     }
-    // per cell: order by original index, gather, bounding sphere (lane groups sized to the mean occupancy)
-    if (C > 0) {
-        const bool wide = (double)n > 6.0 * (double)C;
-        const int64_t lanes = (int64_t)C * (wide ? 32 : 8);
-        const unsigned gc = (unsigned)std::min<int64_t>((lanes + 255) / 256, 152 * 16);
-        if (wide) bin_cells<32><<<gc, 256, 0, st>>>(a, off, C, m->order.as<int>(), m->xs64.as<double>(), m->xloc.as<float4>(), m->sph.as<float4>());
-        else bin_cells<8><<<gc, 256, 0, st>>>(a, off, C, m->order.as<int>(), m->xs64.as<double>(), m->xloc.as<float4>(), m->sph.as<float4>());
+    // order by original index, gather, bounding spheres: per slot for cells of
+    // a few molecules, else per cell with a warp each
+    if (C > 0 && n > 0) {
+        if (wide) {
+            const unsigned gc = (unsigned)std::min<int64_t>(((int64_t)C * 32 + 255) / 256, 152 * 16);
+            bin_cells<32><<<gc, 256, 0, st>>>(a, off, C, m->order.as<int>(), m->xs64.as<double>(), m->xloc.as<float4>(), m->sph.as<float4>());
+        } else {
+            bin_slots<<<nb, kSlotWarps * 32, 0, st>>>(a, off, off + C, slots_out, m->order.as<int>(), m->xs64.as<double>(), m->xloc.as<float4>(), m->sph.as<float4>());
+        }
         m->launches += 1;
     }
     m->n_mol_prev = n;
@@ -605,6 +753,10 @@ extern "C" aica_status aica_bin_molecules(aica_mesh *m, const double *pos, const
         if (flags[0] & kFlagOutside) {
             set_error("aica_bin_molecules: some molecules lie in no cell (cell_of = -1)");
             return AICA_ERR_OUTSIDE_MESH;
+        }
+        if (flags[0] & kFlagTimeout) {
+            set_error("aica_bin_molecules: a wait between blocks of the cell-offset scan timed out");
+            return AICA_ERR_CUDA;
         }
     }
     return AICA_OK;

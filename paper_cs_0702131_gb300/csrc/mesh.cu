@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "aica_internal.cuh"
+#include "scan.cuh"
 #include "predicates.cuh"
 
 namespace {
@@ -403,6 +404,11 @@ extern "C" aica_status aica_mesh_create(const double *points, int64_t n_points, 
     if (e == cudaSuccess) { e = m->flags.reserve(16); what = "flags"; }
     if (e == cudaSuccess) e = cudaMemset(m->flags.p, 0, 16);
     if (e == cudaSuccess) { e = m->acc.reserve(sizeof(double) * (64 + 64 * 16)); what = "acc"; }
+    if (e == cudaSuccess) {
+        e = m->scan_state.reserve(sizeof(unsigned long long) * aica::scan_lookback_words(m->n_cells));
+        what = "scan state";
+    }
+    if (e == cudaSuccess) e = cudaMemset(m->scan_state.p, 0, m->scan_state.bytes);
     if (e != cudaSuccess) {
         aica_status s = e == cudaErrorMemoryAllocation ? AICA_ERR_OOM : AICA_ERR_CUDA;
         cuda_fail(e, what);
@@ -420,9 +426,9 @@ extern "C" void aica_mesh_destroy(aica_mesh *m) {
     aica::DevBuf *bufs[] = {&m->tri_off, &m->tri, &m->vtx_off, &m->vtx, &m->edg_off, &m->edg, &m->ctr, &m->rad,
                             &m->lo, &m->hi, &m->org, &m->ntri, &m->orgk, &m->orgm, &m->orgm64, &m->tri32, &m->vtx32, &m->edg32, &m->ctr32, &m->rad32, &m->box32, &m->bkt_off, &m->bkt_cells, &m->nbr_off, &m->nbr, &m->dil_off,
                             &m->dil_ids, &m->ref_src, &m->ref_n, &m->ref_off, &m->ref_ids, &m->run_off, &m->runs, &m->xf_dev, &m->run_d, &m->work_off,
-                            &m->work, &m->work_split, &m->proc_order, &m->cell_of, &m->order,
-                            &m->cell_off, &m->fill, &m->inv, &m->sph, &m->xloc, &m->xs64, &m->scratch_i32, &m->facc,
-                            &m->vsorted, &m->acc, &m->flags, &m->params, &m->tmp};
+                            &m->work, &m->work_split, &m->proc_order, &m->cell_of, &m->order, &m->unsorted,
+                            &m->cell_off, &m->fill, &m->inv, &m->sph, &m->xloc, &m->xs64, &m->facc,
+                            &m->vsorted, &m->acc, &m->flags, &m->params, &m->tmp, &m->scan_state};
     for (auto *b : bufs) b->release();
     for (auto *v : {&m->tev, &m->tfree})
         for (auto &p : *v) {
