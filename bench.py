@@ -49,11 +49,11 @@ def parse():
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--fp64-steps", type=int, default=0, help="timed FP64 steps (default steps/10)")
     p.add_argument("--no-extras", action="store_true", help="skip FP64, e2e, accuracy and CPU legs")
-    p.add_argument("--study", choices=["cost", "vertex", "nve", "wedge"], default=None,
+    p.add_argument("--study", choices=["cost", "vertex", "nve", "wedge", "adjoint"], default=None,
                    help="instead of the step: the cost-versus-mesh-size study of §2.4 (cost) or the "
                         "vertex-vertex list criterion of §2.2 against the minimum distance (vertex), or the "
                         "paper's verification run of §3 on two meshes (nve), or rotational periodicity through "
-                        "general referring transforms (wedge)")
+                        "general referring transforms (wedge), or the adjoint alone on --config (adjoint)")
     return p.parse_args()
 
 
@@ -779,6 +779,18 @@ def run_study(args):
         out = nve_study(args)
     elif args.study == "wedge":
         out = wedge_study(args)
+    elif args.study == "adjoint":
+        cfg = synth.make(args.config, args.seed)
+        mesh = Mesh(cfg["mesh"], cfg["box"])
+        mesh.build_lists(cfg["rc"], cfg["skin"])
+        pos = torch.tensor(cfg["pos"], dtype=torch.float64, device=dev)
+        sp = torch.tensor(cfg["species"], dtype=torch.int32, device=dev)
+        mesh.bin(pos, sp)
+        _, _, cnt = mesh.forces(cfg["eps"], cfg["sigma"], "fp32")
+        pairs = int(cnt[3:6].sum().item())
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        out = {"study": "adjoint", "config": args.config, "molecules": len(cfg["pos"]), "pairs_within_rc": pairs,
+               "adjoint": adjoint_timing(cfg, mesh, flush, dev, pairs)}
     else:
         # the paper's vertex-vertex criterion against the minimum distance on
         # jittered meshes: pairs within rc it misses, and the error they make

@@ -119,6 +119,7 @@ struct aica_mesh {
 
     // Geometry (device, FP64).  Triangles are oriented out of their cell.
     aica::DevBuf tri_off, tri, vtx_off, vtx, edg_off, edg;  // int32 offsets, double coords
+    aica::DevBuf tri_nbr;                                    // [T] int32 cell across each triangle (-1: boundary)
     aica::DevBuf ctr, rad, lo, hi, org;                      // [C*3] vertex mean, [C] radius, AABB, origin
     aica::DevBuf ntri;                                       // [C] int32 triangle count | convex << 16
     aica::DevBuf box32;                                      // [C*6] float local AABB (lo, hi), rounded outward

@@ -13,9 +13,11 @@
 //                coordinates, FP64 and exact slow paths (predicates.cuh).
 //   bin_locate_hint / bin_locate_miss   when the same molecules were binned
 //                before: test each molecule's previous cell with the FP32
-//                filter alone, collect the ones that left it (or that the
-//                filter could not decide), then search those exactly in the
-//                previous cell, its face neighbours and finally the grid.
+//                filter alone (and, when it left a convex cell, the cell
+//                across the face it crossed), collect the ones still not
+//                located (or that the filter could not decide), then search
+//                those exactly in the previous cell, its face neighbours and
+//                finally the grid.
 //                The previous cell is only a search order: the test is exact.
 //   (scan)       cell offsets from the counts
 //   bin_scatter_down  warp-aggregated slot claims, counting the counts down
@@ -53,6 +55,7 @@ struct BinArgs {
     double glo[3], gh[3], ghi[3];
     const int *bkt_off, *bkt_cells;
     const int *tri_off, *ntri, *orgk;
+    const int *tri_nbr;       // cell across each triangle (-1: boundary)
     const double *org;        // cell origins orgk * 2^-10 (FP64, exact): frame of the cell tests
     const double *orgm64;     // molecule-frame origins (FP64, exact): frame of the binned coordinates
     long long Lkey[3], glo_key[3], ghi_key[3];
@@ -110,8 +113,11 @@ __device__ __forceinline__ int orient(float3 a, float3 b, float3 c, float3 q, fl
 // of); for a convex cell, in front of one face means outside.  Other cells
 // take the cone test: find the triangle whose cone from the centre holds q,
 // then q must lie behind that triangle.
+// exit_t (optional): for a convex cell found outside, the triangle whose
+// plane q lies in front of, else -1.
 template <bool EXACT>
-__device__ int cell_test(const BinArgs &a, int c, float3 q, const double *p64) {
+__device__ int cell_test(const BinArgs &a, int c, float3 q, const double *p64, int *exit_t = nullptr) {
+    if (exit_t) *exit_t = -1;
     const float *B = a.box32 + 6 * c;
     const float scale = fmaxf(a.max_local, fmaxf(fabsf(q.x), fmaxf(fabsf(q.y), fabsf(q.z))));
     const float tol = 1e-5f * scale;
@@ -127,11 +133,13 @@ __device__ int cell_test(const BinArgs &a, int c, float3 q, const double *p64) {
         if (!EXACT && s == 0) return -1;
         if (s > 0) {
             behind = false;
+            if (exit_t) *exit_t = t;
             break;
         }
     }
     if (behind) return 1;
     if (code >> 16) return 0;
+    if (exit_t) *exit_t = -1;
     float3 C = ld3f(a.ctr32 + 3 * c);
     const double *C64 = a.ctr + 3 * c;
     for (int t = t0; t < t0 + nt; ++t) {
@@ -226,10 +234,17 @@ __global__ void __launch_bounds__(256) bin_locate_hint(BinArgs a) {
         bool ok;
         wrapped_position(a, k, p, ok);
         const int h = a.hint[k];
-        const int r = (ok && h >= 0) ? cell_test<false>(a, h, local_to(a, p, h), p) : 0;
+        int ex = -1;
+        const int r = (ok && h >= 0) ? cell_test<false>(a, h, local_to(a, p, h), p, &ex) : 0;
+        // a molecule that left a convex cell: first the cell across the face it crossed
+        const int h2 = (ok && r == 0 && ex >= 0) ? a.tri_nbr[ex] : -1;
+        const int r2 = h2 >= 0 ? cell_test<false>(a, h2, local_to(a, p, h2), p) : 0;
         if (r == 1) {
             a.cell_of[k] = h;
             located = h;
+        } else if (r2 == 1) {
+            a.cell_of[k] = h2;
+            located = h2;
         } else if (ok) {
             miss = true;
             undecided = r < 0;
@@ -669,6 +684,7 @@ extern "C" aica_status aica_bin_molecules(aica_mesh *m, const double *pos, const
     a.tri_off = m->tri_off.as<int>();
     a.ntri = m->ntri.as<int>();
     a.orgk = m->orgk.as<int>();
+    a.tri_nbr = m->tri_nbr.as<int>();
     a.org = m->org.as<double>();
     a.orgm64 = m->orgm64.as<double>();
     for (int d = 0; d < 3; ++d) {

@@ -88,6 +88,7 @@ extern "C" aica_status aica_mesh_create(const double *points, int64_t n_points, 
     for (int64_t c = 0; c < n_cells; ++c) tcount[c + 1] += tcount[c];
     int64_t T = tcount[n_cells];
     std::vector<int64_t> tv(3 * T);
+    std::vector<int32_t> h_tri_nbr(T);      // the cell on the other side of each triangle (-1: boundary)
     std::vector<int64_t> fillc(n_cells, 0);
     for (int64_t f = 0; f < n_faces; ++f) {
         const int64_t *v = face_vertices + face_offsets[f];
@@ -101,9 +102,11 @@ extern "C" aica_status aica_mesh_create(const double *points, int64_t n_points, 
             int64_t a = v[r], b = v[(r + i) % k], c = v[(r + i + 1) % k];
             int64_t o = tcount[owner[f]] + fillc[owner[f]]++;
             tv[3 * o] = a; tv[3 * o + 1] = b; tv[3 * o + 2] = c;
+            h_tri_nbr[o] = (int32_t)neighbour[f];
             if (neighbour[f] >= 0) {
                 int64_t q = tcount[neighbour[f]] + fillc[neighbour[f]]++;
                 tv[3 * q] = a; tv[3 * q + 1] = c; tv[3 * q + 2] = b;
+                h_tri_nbr[q] = (int32_t)owner[f];
             }
         }
     }
@@ -378,6 +381,7 @@ extern "C" aica_status aica_mesh_create(const double *points, int64_t n_points, 
     const char *what = "upload";
     if (e == cudaSuccess) e = upload(m->tri_off, h_tri_off);
     if (e == cudaSuccess) e = upload(m->tri, h_tri);
+    if (e == cudaSuccess) e = upload(m->tri_nbr, h_tri_nbr);
     if (e == cudaSuccess) e = upload(m->ntri, h_ntri);
     if (e == cudaSuccess) e = upload(m->box32, h_box32);
     if (e == cudaSuccess) e = upload(m->vtx_off, h_vtx_off);
@@ -423,7 +427,7 @@ extern "C" aica_status aica_mesh_create(const double *points, int64_t n_points, 
 
 extern "C" void aica_mesh_destroy(aica_mesh *m) {
     if (!m) return;
-    aica::DevBuf *bufs[] = {&m->tri_off, &m->tri, &m->vtx_off, &m->vtx, &m->edg_off, &m->edg, &m->ctr, &m->rad,
+    aica::DevBuf *bufs[] = {&m->tri_off, &m->tri, &m->tri_nbr, &m->vtx_off, &m->vtx, &m->edg_off, &m->edg, &m->ctr, &m->rad,
                             &m->lo, &m->hi, &m->org, &m->ntri, &m->orgk, &m->orgm, &m->orgm64, &m->tri32, &m->vtx32, &m->edg32, &m->ctr32, &m->rad32, &m->box32, &m->bkt_off, &m->bkt_cells, &m->nbr_off, &m->nbr, &m->dil_off,
                             &m->dil_ids, &m->ref_src, &m->ref_n, &m->ref_off, &m->ref_ids, &m->run_off, &m->runs, &m->xf_dev, &m->run_d, &m->work_off,
                             &m->work, &m->work_split, &m->proc_order, &m->cell_of, &m->order, &m->unsorted,

@@ -76,13 +76,16 @@ def test_outside_molecules_reported():
 
 
 def test_repeated_binning_stays_exact():
-    """Several binnings in a row of moving molecules (the single-pass scan of
-    the cell counts runs once per call, 41 tiles on this mesh)."""
-    c = synth.make("c2", 5)
+    """Several binnings in a row of moving molecules: the single-pass scan of
+    the cell counts (6 tiles of cells here) runs once per call, and molecules
+    that left their cell are found across the face they crossed or by the
+    exact search."""
+    c = synth._lj_fluid((16, 16, 16), synth.A_FCC_08, (12, 12, 12), True, 2.5, 5)
+    c["skin"] = 1e-3
     m, pos, sp, _ = gpu_setup(c)
     rng = np.random.default_rng(9)
-    for _ in range(4):
-        c["pos"] = synth.random_displacement(c["pos"], 0.05, rng, c["box"]["L"], c["box"]["periodic"])
+    for dist in (0.02, 0.05, 0.3, 0.02):
+        c["pos"] = synth.random_displacement(c["pos"], dist, rng, c["box"]["L"], c["box"]["periodic"])
         cell_of, order, cell_off = m.bin(torch.tensor(c["pos"], device="cuda"), sp)
         o = oracle_all(c, lists=False)
         np.testing.assert_array_equal(cell_of.cpu().numpy(), o["cell"])
