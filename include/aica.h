@@ -289,8 +289,9 @@ aica_status aica_sort_by_cell_noalloc(const int32_t *cell_of, int64_t n, int64_t
                                       int32_t *cell_off, void *stream);
 
 /* With deferred != 0, aica_bin_molecules and aica_forces do not synchronize
- * to check device-side error flags; errors are reported by
- * aica_check_status (which synchronizes `stream`). */
+ * to check device-side error flags; the errors of all calls since the last
+ * check accumulate and are reported (then cleared) by aica_check_status,
+ * which synchronizes `stream`. */
 aica_status aica_set_deferred_checks(aica_mesh *mesh, int deferred);
 aica_status aica_check_status(aica_mesh *mesh, void *stream);
 

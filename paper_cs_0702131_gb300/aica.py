@@ -319,6 +319,7 @@ class Mesh:
         self.n = 0
         self.rc = None
         self.generation = 0
+        self.deferred = False
 
     def close(self):
         if getattr(self, "h", None):
@@ -391,7 +392,9 @@ class Mesh:
         aica_verlet_step(self.h, eps, sigma, p, mass, dt, species, pos, vel, force, ev, kin, shift)
 
     def set_deferred(self, deferred=True):
+        """Deferred device-side checks: errors accumulate until check()."""
         aica_set_deferred_checks(self.h, deferred)
+        self.deferred = bool(deferred)
 
     def set_kernel_timing(self, enable=True):
         aica_set_kernel_timing(self.h, enable)

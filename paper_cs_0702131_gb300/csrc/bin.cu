@@ -714,7 +714,9 @@ extern "C" aica_status aica_bin_molecules(aica_mesh *m, const double *pos, const
     int *off = m->cell_off.as<int>();
     a.cnt = cnt;
     a.inv = m->inv.as<int>();
-    AICA_CUDA(cudaMemsetAsync(m->flags.p, 0, 16, st));
+    // with deferred checks the error bits (flags[0]) accumulate until aica_check_status
+    if (m->deferred) AICA_CUDA(cudaMemsetAsync(m->flags.as<unsigned>() + 1, 0, 12, st));
+    else AICA_CUDA(cudaMemsetAsync(m->flags.p, 0, 16, st));
     AICA_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (C + 1), st));
     unsigned nb = (unsigned)((n + 255) / 256);
     if (n > 0) {

@@ -51,9 +51,12 @@ extern "C" aica_status aica_check_status(aica_mesh *m, void *stream) {
     AICA_CUDA(cudaMemcpyAsync(flags, m->flags.p, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, st));
     AICA_CUDA(cudaStreamSynchronize(st));
     AICA_CUDA(cudaGetLastError());
+    // reported once: the error bits start again from zero
+    if (flags[0]) AICA_CUDA(cudaMemsetAsync(m->flags.p, 0, sizeof(unsigned), st));
     if (flags[0] & aica::kFlagSpecies) { aica::set_error("species index out of range"); return AICA_ERR_INVALID_ARG; }
     if (flags[0] & aica::kFlagOutside) { aica::set_error("some molecules lie in no cell"); return AICA_ERR_OUTSIDE_MESH; }
     if (flags[0] & aica::kFlagCapacity) { aica::set_error("a kernel capacity was exceeded"); return AICA_ERR_CAPACITY; }
+    if (flags[0] & aica::kFlagTimeout) { aica::set_error("a bounded wait between blocks timed out"); return AICA_ERR_CUDA; }
     return AICA_OK;
 }
 

@@ -1003,8 +1003,8 @@ struct WarpB32 {
 // FP32 adjoint: the forward kernel's schedule walk (persistent grid, cells
 // claimed from a counter, runs culled and queued, one partner per lane
 // against the chunk), with the adjoint pair body.
-template <int NI_, bool MULTI, bool XF>
-__global__ void __launch_bounds__(kThreads32, 4) pair_bwd32(BwdArgs b) {
+template <int NI_, bool MULTI, bool XF, int MINB>
+__global__ void __launch_bounds__(kThreads32, MINB) pair_bwd32(BwdArgs b) {
     const PairArgs &a = b.p;
     __shared__ float4 tab[kMaxSpecies * kMaxSpecies];
     __shared__ float4 tbs[MULTI ? kMaxSpecies * kMaxSpecies : 1];
@@ -1394,20 +1394,23 @@ int launch_fwd32(const PairArgs &a, bool multi, bool shift, cudaStream_t st) {
 }
 
 // Launch the FP32 adjoint on a persistent grid (every SM filled to its
-// occupancy); returns the number of blocks.
+// occupancy: 7 blocks of 4 warps at 72 registers for chunks of 4, 6 at 80
+// for chunks of 8, the most that keep the pair loop free of spills);
+// returns the number of blocks.
 template <int NI_, bool MULTI, bool XF>
 int launch_bwd32_t(const BwdArgs &b, cudaStream_t st) {
+    constexpr int MINB = NI_ == 4 ? 7 : 6;
     static int cache[64] = {0};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
     if (!cache[dev]) {
         int sms = 0, per = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pair_bwd32<NI_, MULTI, XF>, kThreads32, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pair_bwd32<NI_, MULTI, XF, MINB>, kThreads32, 0);
         cache[dev] = std::max(1, sms * std::max(1, per));
     }
     const int grid = std::min(cache[dev], std::max(1, (b.p.C + kWarps32 - 1) / kWarps32));
-    pair_bwd32<NI_, MULTI, XF><<<grid, kThreads32, 0, st>>>(b);
+    pair_bwd32<NI_, MULTI, XF, MINB><<<grid, kThreads32, 0, st>>>(b);
     return grid;
 }
 

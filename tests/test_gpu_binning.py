@@ -73,6 +73,16 @@ def test_outside_molecules_reported():
         m.check()
     F, ev, cnt = m.forces([1.0], [1.0], "fp64")
     assert torch.all(F[5] == 0)
+    # deferred errors accumulate over calls until check() reports and clears them
+    m.bin(P, S)
+    Q = P.clone()
+    Q[5] = Q[4]
+    m.bin(Q, S)
+    with pytest.raises(AicaError) as e:
+        m.check()
+    assert e.value.name == "AICA_ERR_OUTSIDE_MESH"
+    m.bin(Q, S)
+    m.check()
 
 
 def test_repeated_binning_stays_exact():
