@@ -19,14 +19,15 @@
 //                those exactly in the previous cell, its face neighbours and
 //                finally the grid.
 //                The previous cell is only a search order: the test is exact.
-//   (scan)       cell offsets from the counts
+//   scan_lookback  cell offsets from the counts (single pass, scan.cuh)
 //   bin_scatter_down  warp-aggregated slot claims, counting the counts down
-//   bin_cells    per cell (groups of 8 or 32 lanes): order the cell's slots by
-//                original index (the stable counting sort by (cell, original
-//                index)), gather FP64 positions and float4 cell-local
-//                coordinates with the species in .w (the pair kernels' input
-//                layout), the inverse permutation, and the cell's bounding
-//                sphere
+//   bin_slots / bin_cells   order each cell's slots by original index (the
+//                stable counting sort by (cell, original index)), gather FP64
+//                positions and float4 cell-local coordinates with the species
+//                in .w (the pair kernels' input layout), the inverse
+//                permutation, and the cell's bounding sphere: per slot with
+//                window-owned cells for cells of a few molecules, a warp per
+//                cell otherwise
 //   bin_count, bin_scatter, bin_fixup   the same sort for caller-given cells
 //                (aica_sort_by_cell_noalloc)
 #include <math.h>
