@@ -72,3 +72,29 @@ def test_bad_meshes_rejected_on_host(L):
     # a cell outside its periodic box
     box_p = dict(L=np.array([2.5, 10, 10]), periodic=np.array([1, 0, 0], np.int32))
     assert _create(L, good, box_p) == "AICA_ERR_BAD_MESH"
+
+
+def test_coupling_transform_on_host(L):
+    """aica_coupling_transform (host arithmetic, §2.2.2) against the oracle's
+    own construction; antiparallel normals give R = I, parallel ones are
+    rejected."""
+    from oracle import transforms as T
+    from paper_cs_0702131_gb300.aica import AicaError, aica_coupling_transform
+    rng = np.random.default_rng(12)
+    for _ in range(25):
+        na, nb = rng.normal(size=3), rng.normal(size=3)
+        ca, cb = rng.normal(size=3) * 5, rng.normal(size=3) * 5
+        R, y = aica_coupling_transform(na, ca, nb, cb)
+        Ro, yo = T.coupling(na, ca, nb, cb)
+        np.testing.assert_allclose(R, Ro, atol=1e-13)
+        np.testing.assert_allclose(y, yo, atol=1e-12)
+        np.testing.assert_allclose(R.T @ R, np.eye(3), atol=1e-13)
+        assert abs(np.linalg.det(R) - 1.0) < 1e-13
+        np.testing.assert_allclose(R @ (-na / np.linalg.norm(na)), nb / np.linalg.norm(nb), atol=1e-13)
+    R, y = aica_coupling_transform(np.array([1.0, 0, 0]), np.array([3.0, 0, 0]), np.array([-1.0, 0, 0]),
+                                   np.array([0.0, 0, 0]))
+    np.testing.assert_array_equal(R, np.eye(3))
+    np.testing.assert_allclose(y, [-3.0, 0, 0])
+    with pytest.raises(AicaError) as e:
+        aica_coupling_transform(np.array([0.0, 0, 1]), np.zeros(3), np.array([0.0, 0, 2]), np.zeros(3))
+    assert e.value.name == "AICA_ERR_INVALID_ARG"
