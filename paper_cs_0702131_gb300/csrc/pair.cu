@@ -42,6 +42,10 @@
 // origin cancels).  Energy and virial are summed per lane in FP32 over at
 // most four cells, then in FP64 per warp; warps add their totals to striped
 // FP64 rows that a small kernel sums.
+//
+// Adjoint (step a10).  pair_bwd32 runs the FP32 kernel's schedule walk
+// (walk_runs) with the adjoint pair body, so it recomputes exactly the
+// forward's pair set; pair_bwd64 is its FP64 comparison path.
 #include <math.h>
 #include <string.h>
 
