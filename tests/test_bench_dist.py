@@ -34,7 +34,7 @@ def _worker(rank, world, port, out):
 
 
 def test_two_rank_aggregation():
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     mp.spawn(_worker, args=(2, _free_port(), out), nprocs=2, join=True)
     for r in range(2):
