@@ -185,7 +185,10 @@ aica_status aica_get_lists(const aica_mesh *mesh, int64_t *dil_off, int32_t *dil
  * one cell.  The binned state stays in the mesh for the force calls.  A
  * molecule in no cell gets cell -1, no slot and zero force; the call then
  * returns AICA_ERR_OUTSIDE_MESH (after synchronizing the stream) unless
- * deferred checking is on (aica_set_deferred_checks). */
+ * deferred checking is on (aica_set_deferred_checks).  A species index
+ * outside [0, 8) gives AICA_ERR_INVALID_ARG.  The cell offsets come from a
+ * single-pass scan whose blocks wait on one another with a bounded wait; if
+ * a wait gives up the result is wrong and the call returns AICA_ERR_CUDA. */
 aica_status aica_bin_molecules(aica_mesh *mesh, const double *pos, const int32_t *species, int64_t n,
                                int32_t *cell_of, int32_t *order, int32_t *cell_off, void *stream);
 
