@@ -80,6 +80,19 @@ def test_forces_c5_sampled():
         assert 41.0 < n_in / len(c["pos"]) < 44.0      # the 6th shell lies 0.04 sigma inside rc
 
 
+def test_forces_c3_sampled():
+    """The full-size nanochannel (fixed wall layers, removed posts, open y
+    axis): sampled rows against the oracle in both precisions."""
+    c = synth.make("c3", 0)
+    m, *_ = gpu_setup(c)
+    rng = np.random.default_rng(1)
+    idx = np.sort(rng.choice(len(c["pos"]), 256, replace=False))
+    ref = oracle.lj(c["pos"], c["species"], c["eps"], c["sigma"], c["rc"], c["box"], idx=idx)
+    for prec in ("fp32", "fp64"):
+        F, ev, cnt = m.forces(c["eps"], c["sigma"], prec)
+        assert_forces(F.double().cpu().numpy(), ref, TOL[prec][0], idx=idx)
+
+
 def test_repeat_calls_stable():
     c = synth.make("t0", 4)
     m, *_ = gpu_setup(c)
