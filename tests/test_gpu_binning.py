@@ -1,11 +1,8 @@
 """GPU binning against the oracle: cell ids, binned order and offsets bit-exact."""
-import itertools
-
 import numpy as np
 import pytest
 import torch
 
-import oracle
 from paper_cs_0702131_gb300 import synth
 from paper_cs_0702131_gb300.aica import AicaError, Mesh
 from gpu_helpers import gpu_setup, oracle_all

@@ -1,6 +1,5 @@
 """Error statuses from the GPU path (host-detected and device flags; no
 kernel traps or hangs)."""
-import numpy as np
 import pytest
 import torch
 

@@ -7,7 +7,6 @@ FP32 path re-decides pairs near the cut-off in FP64.
 """
 import numpy as np
 import pytest
-import torch
 
 import oracle
 from paper_cs_0702131_gb300 import synth

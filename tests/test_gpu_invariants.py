@@ -3,7 +3,6 @@
 of the serial = parallel criterion of §3), Newton's third law."""
 import numpy as np
 import pytest
-import torch
 
 from paper_cs_0702131_gb300 import synth
 from gpu_helpers import gpu_setup
