@@ -72,8 +72,6 @@ bool xf_same(const Xform &a, const Xform &b, double ytol) {
     return true;
 }
 
-bool xf_is_identity(const Xform &a, double ytol) { return xf_same(a, xf_identity(), ytol); }
-
 // y + R p in the operation order of the oracle's image sum
 V3<double> xf_apply(const Xform &t, V3<double> p) {
     return {t.y[0] + ((t.R[0] * p.x + t.R[1] * p.y) + t.R[2] * p.z),
