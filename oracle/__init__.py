@@ -34,8 +34,6 @@ from __future__ import annotations
 import ctypes
 import os
 import subprocess
-from fractions import Fraction
-
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -320,11 +318,20 @@ def _exact_sign(x):
 
 def _inside_exact(tris, p):
     """Ray-parity membership of p + (e, e^2, e^3) in a closed triangulated
-    surface, in exact rational arithmetic (slow path for uncertain cases)."""
-    P = [Fraction(float(v)) for v in p]
+    surface, in exact rational arithmetic (slow path for uncertain cases).
+    Every FP64 value is a dyadic rational, so all coordinates are scaled to
+    integers over one common power-of-two denominator (exactly); the signs of
+    the determinants below are those of the rational ones."""
+    vals = [float(v) for v in p] + [float(v) for v in np.asarray(tris).reshape(-1)]
+    rat = [v.as_integer_ratio() for v in vals]
+    D = max(d for _, d in rat)
+    ints = [n * (D // d) for n, d in rat]
+    P = ints[:3]
+    T = ints[3:]
     parity = 0
-    for t in tris:
-        a, b, c = ([Fraction(float(v)) for v in t[3 * i:3 * i + 3]] for i in range(3))
+    for t in range(len(T) // 9):
+        q = T[9 * t:9 * t + 9]
+        a, b, c = q[0:3], q[3:6], q[6:9]
         nx = _exact_sign((b[1] - a[1]) * (c[2] - a[2]) - (b[2] - a[2]) * (c[1] - a[1]))
         if nx == 0:
             continue
@@ -347,6 +354,30 @@ def _inside_exact(tris, p):
     return parity
 
 
+def _aabb_buckets(lo, hi):
+    """Bucket grid over cell bounding boxes (buckets at least as wide as the
+    widest box, so a box meets at most 2 buckets per axis): returns
+    (origin, width, shape, offsets, cells) with cells[offsets[b]:offsets[b+1]]
+    the cells whose box meets bucket b.  A point's bucket lists every cell
+    whose box holds the point (floor is monotone)."""
+    g0 = lo.min(0)
+    h = np.maximum((hi - lo).max(0), 1e-12)
+    shape = np.maximum(np.floor((hi.max(0) - g0) / h).astype(np.int64) + 1, 1)
+    i0 = np.clip(np.floor((lo - g0) / h).astype(np.int64), 0, shape - 1)
+    i1 = np.clip(np.floor((hi - g0) / h).astype(np.int64), 0, shape - 1)
+    keys, ids = [], []
+    for off in np.ndindex(2, 2, 2):
+        b = i0 + np.asarray(off)
+        ok = np.all(b <= i1, axis=1)
+        keys.append(np.ravel_multi_index(b[ok].T, shape))
+        ids.append(np.flatnonzero(ok))
+    keys, ids = np.concatenate(keys), np.concatenate(ids)
+    srt = np.argsort(keys, kind="stable")
+    offsets = np.zeros(int(np.prod(shape)) + 1, np.int64)
+    np.add.at(offsets, keys + 1, 1)
+    return g0, h, shape, np.cumsum(offsets), ids[srt]
+
+
 def locate(geo, box, pos):
     """Containing cell of each molecule after wrapping periodic coordinates
     into [0, L).  Returns (cell [n] int32, -1 = outside every cell; wrapped
@@ -357,14 +388,23 @@ def locate(geo, box, pos):
     wrapped = np.zeros_like(pos)
     lib().oracle_locate(geo["tri_off"], geo["tri"], geo["lo"], geo["hi"], geo["n_cells"], pos, n,
                         _c(box["L"], np.float64), _c(box["periodic"], np.int32), cell, wrapped)
-    for k in np.flatnonzero(cell == -2):
-        p = wrapped[k]
-        cand = np.flatnonzero(np.all((geo["lo"] <= p) & (p <= geo["hi"]), axis=1))
-        hits = [c for c in cand
-                if _inside_exact(geo["tri"][geo["tri_off"][c]:geo["tri_off"][c + 1]], p)]
-        if len(hits) > 1:
-            raise RuntimeError(f"molecule {k} claimed by cells {hits}")
-        cell[k] = hits[0] if hits else -1
+    undecided = np.flatnonzero(cell == -2)
+    if len(undecided):
+        g0, h, shape, boff, bcells = _aabb_buckets(geo["lo"], geo["hi"])
+        bidx = np.floor((wrapped[undecided] - g0) / h).astype(np.int64)
+        inside_grid = np.all((bidx >= 0) & (bidx < shape), axis=1)
+        for k, b, ok in zip(undecided, bidx, inside_grid):
+            p = wrapped[k]
+            cand = []
+            if ok:
+                bb = np.ravel_multi_index(tuple(b), shape)
+                cc = bcells[boff[bb]:boff[bb + 1]]
+                cand = cc[np.all((geo["lo"][cc] <= p) & (p <= geo["hi"][cc]), axis=1)]
+            hits = [c for c in sorted(cand)
+                    if _inside_exact(geo["tri"][geo["tri_off"][c]:geo["tri_off"][c + 1]], p)]
+            if len(hits) > 1:
+                raise RuntimeError(f"molecule {k} claimed by cells {hits}")
+            cell[k] = hits[0] if hits else -1
     return cell, wrapped
 
 
