@@ -63,6 +63,7 @@ struct BinArgs {
     const float *tri32, *ctr32, *box32;
     const double *tri, *ctr;
     float max_local;
+    float4 *xlo;              // remainders x - o_m - xloc (binned order)
     int *cell_of;
     int *cnt;              // molecules per cell (counted as they are located)
     int *inv;              // original -> binned index; -1 for molecules in no cell
@@ -335,18 +336,26 @@ __global__ void __launch_bounds__(256) bin_locate_miss(BinArgs a) {
     }
 }
 
-__global__ void __launch_bounds__(256) bin_count(const int *cell_of, int64_t n, int *cnt) {
+// Counting sort of caller-given cells (aica_sort_by_cell_noalloc).  A cell
+// id outside [0, C) is left out like -1; ids >= C are counted in *bad, so
+// no access ever leaves cnt[0, C), cell_off[0, C] or order[0, n).
+__global__ void __launch_bounds__(256) bin_count(const int *cell_of, int64_t n, int C, int *cnt, int *bad) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int c = k < n ? cell_of[k] : -1;
+    if (c >= C) {
+        atomicAdd(bad, 1);
+        c = -1;
+    }
     unsigned same = __match_any_sync(0xffffffffu, c);
     int lane = threadIdx.x & 31;
     if (c >= 0 && lane == __ffs(same) - 1) atomicAdd(cnt + c, __popc(same));
 }
 
-__global__ void __launch_bounds__(256) bin_scatter(const int *cell_of, int64_t n, const int *cell_off, int *fill,
-                                                   int *order) {
+__global__ void __launch_bounds__(256) bin_scatter(const int *cell_of, int64_t n, int C, const int *cell_off,
+                                                   int *fill, int *order) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int c = k < n ? cell_of[k] : -1;
+    if (c >= C) c = -1;
     unsigned same = __match_any_sync(0xffffffffu, c);
     int lane = threadIdx.x & 31;
     int leader = __ffs(same) - 1;
@@ -356,18 +365,48 @@ __global__ void __launch_bounds__(256) bin_scatter(const int *cell_of, int64_t n
     if (c >= 0) order[cell_off[c] + base + __popc(same & ((1u << lane) - 1u))] = (int)k;
 }
 
-__global__ void __launch_bounds__(256) bin_fixup(const int *cell_off, int C, int *order) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
+// Each cell's slots in ascending original index: a warp per cell, bitonic
+// sort in shared memory for cells of up to kFixCap molecules (padded to a
+// power of two with INT_MAX), a serial insertion sort beyond that.
+constexpr int kFixWarps = 4, kFixCap = 2048;
+__global__ void __launch_bounds__(kFixWarps * 32) bin_fixup(const int *cell_off, int C, int *order) {
+    __shared__ int buf[kFixWarps][kFixCap];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int c = blockIdx.x * kFixWarps + w;
     if (c >= C) return;
-    int s = cell_off[c], e = cell_off[c + 1];
-    for (int i = s + 1; i < e; ++i) {
-        int v = order[i], j = i - 1;
-        while (j >= s && order[j] > v) {
-            order[j + 1] = order[j];
-            --j;
-        }
-        order[j + 1] = v;
+    const int s = cell_off[c], m = cell_off[c + 1] - s;
+    if (m < 2) return;
+    if (m > kFixCap) {
+        if (lane == 0)
+            for (int i = s + 1; i < s + m; ++i) {
+                int v = order[i], j = i - 1;
+                while (j >= s && order[j] > v) {
+                    order[j + 1] = order[j];
+                    --j;
+                }
+                order[j + 1] = v;
+            }
+        return;
     }
+    int P = 2;
+    while (P < m) P <<= 1;
+    int *b = buf[w];
+    for (int i = lane; i < P; i += 32) b[i] = i < m ? order[s + i] : 0x7fffffff;
+    __syncwarp();
+    for (int size = 2; size <= P; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = lane; i < P / 2; i += 32) {
+                const int lo = 2 * i - (i & (stride - 1)), hi = lo + stride;
+                const bool up = (lo & size) == 0;
+                const int x = b[lo], y = b[hi];
+                if ((x > y) == up) {
+                    b[lo] = y;
+                    b[hi] = x;
+                }
+            }
+            __syncwarp();
+        }
+    for (int i = lane; i < m; i += 32) order[s + i] = b[i];
 }
 
 // Slots of located molecules: cell c's count (from the locate kernels) is
@@ -383,6 +422,21 @@ __global__ void __launch_bounds__(256) bin_scatter_down(const int *cell_of, int6
     if (c >= 0 && lane == leader) top = atomicSub(cnt + c, m);
     top = __shfl_sync(0xffffffffu, top, leader);
     if (c >= 0) order[cell_off[c] + top - m + __popc(same & ((1u << lane) - 1u))] = (int)k;
+}
+
+// Coordinates of p in the molecule frame o: the nearest FP32 values and the
+// FP32 remainders (hi + lo equals p - o to about 2^-48 |p - o|).  The FP32
+// cluster pair kernel rebuilds exactly rounded separations from both.
+__device__ __forceinline__ void frame_split(const BinArgs &a, const double *p, const double *o, int sp,
+                                            float4 &hi, float4 &lo) {
+    float h[3], l[3];
+    for (int d = 0; d < 3; ++d) {
+        const double x = p[d] - o[d];
+        h[d] = (float)x;
+        l[d] = (float)(x - (double)h[d]);
+    }
+    hi = make_float4(h[0], h[1], h[2], __int_as_float(sp & (kMaxSpecies - 1)));
+    lo = make_float4(l[0], l[1], l[2], 0.f);
 }
 
 // Per cell, by groups of G lanes: order the cell's molecules by original
@@ -423,10 +477,10 @@ __global__ void __launch_bounds__(256) bin_cells(BinArgs a, const int *cell_off,
                 if (a.per[d]) p[d] = wrap_coord(p[d], a.L[d], a.Lkey[d]);
                 xs64[3 * (int64_t)slot + d] = p[d];
             }
-            const double *o = a.orgm64 + 3 * c;
-            x = make_float4((float)(p[0] - o[0]), (float)(p[1] - o[1]), (float)(p[2] - o[2]),
-                            __int_as_float(sp & (kMaxSpecies - 1)));
+            float4 lo;
+            frame_split(a, p, a.orgm64 + 3 * c, sp, x, lo);
             xloc[slot] = x;
+            a.xlo[slot] = lo;
         }
         float cx = mine ? x.x : 0.f, cy = mine ? x.y : 0.f, cz = mine ? x.z : 0.f;
 #pragma unroll
@@ -469,10 +523,10 @@ __global__ void __launch_bounds__(256) bin_cells(BinArgs a, const int *cell_off,
                     if (a.per[d]) p[d] = wrap_coord(p[d], a.L[d], a.Lkey[d]);
                     xs64[3 * (int64_t)slot + d] = p[d];
                 }
-                const double *o = a.orgm64 + 3 * c;
-                const float4 y = make_float4((float)(p[0] - o[0]), (float)(p[1] - o[1]), (float)(p[2] - o[2]),
-                                             __int_as_float(sp & (kMaxSpecies - 1)));
+                float4 y, lo;
+                frame_split(a, p, a.orgm64 + 3 * c, sp, y, lo);
                 xloc[slot] = y;
+                a.xlo[slot] = lo;
                 sx += y.x; sy += y.y; sz += y.z;
             }
             sx /= (float)m; sy /= (float)m; sz /= (float)m;
@@ -513,9 +567,10 @@ __device__ __forceinline__ float4 local_xloc(const BinArgs &a, int k, int c, int
         if (a.per[d]) p[d] = wrap_coord(p[d], a.L[d], a.Lkey[d]);
         xs64[3 * (int64_t)slot + d] = p[d];
     }
-    const double *o = a.orgm64 + 3 * c;
-    return make_float4((float)(p[0] - o[0]), (float)(p[1] - o[1]), (float)(p[2] - o[2]),
-                       __int_as_float(sp & (kMaxSpecies - 1)));
+    float4 hi, lo;
+    frame_split(a, p, a.orgm64 + 3 * c, sp, hi, lo);
+    a.xlo[slot] = lo;
+    return hi;
 }
 
 __device__ __forceinline__ float4 sphere_of(const float4 *x, int m) {
@@ -657,6 +712,8 @@ extern "C" aica_status aica_bin_molecules(aica_mesh *m, const double *pos, const
         AICA_CUDA(m->order.reserve(sizeof(int) * cap));
         AICA_CUDA(m->unsorted.reserve(sizeof(int) * cap));
         AICA_CUDA(m->xloc.reserve(sizeof(float4) * cap));
+        AICA_CUDA(m->xlo.reserve(sizeof(float4) * cap));
+        AICA_CUDA(m->flag_list.reserve(sizeof(int) * (cap + 1)));
         AICA_CUDA(m->inv.reserve(sizeof(int) * cap));
         AICA_CUDA(m->xs64.reserve(sizeof(double) * 3 * cap));
         AICA_CUDA(m->facc.reserve(sizeof(double) * 4 * cap));
@@ -699,6 +756,7 @@ extern "C" aica_status aica_bin_molecules(aica_mesh *m, const double *pos, const
     a.tri = m->tri.as<double>();
     a.ctr = m->ctr.as<double>();
     a.max_local = (float)(m->max_local * (1 + 1e-6));
+    a.xlo = m->xlo.as<float4>();
     for (int d = 0; d < 3; ++d) {
         a.glo_f[d] = (float)m->glo[d];
         a.gh_f[d] = (float)m->gh[d];
@@ -824,14 +882,16 @@ extern "C" aica_status aica_sort_by_cell_noalloc(const int32_t *cell_of, int64_t
     const int C = (int)n_cells;
     int *cnt = g_noalloc_dev[dev];
     int *work = cnt + (kNoAllocMaxCells + 1);
+    int *bad = cnt + (kNoAllocWords - 1);      // ids >= n_cells seen by this call (left out)
     AICA_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (C + 1), st));
+    AICA_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), st));
     const unsigned nb = (unsigned)((n + 255) / 256);
-    if (n > 0) bin_count<<<nb, 256, 0, st>>>(cell_of, n, cnt);
+    if (n > 0) bin_count<<<nb, 256, 0, st>>>(cell_of, n, C, cnt, bad);
     exclusive_scan<int, int>(cnt, C, cell_off, work, st);
     AICA_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (C + 1), st));
     if (n > 0) {
-        bin_scatter<<<nb, 256, 0, st>>>(cell_of, n, cell_off, cnt, order);
-        bin_fixup<<<(C + 255) / 256, 256, 0, st>>>(cell_off, C, order);
+        bin_scatter<<<nb, 256, 0, st>>>(cell_of, n, C, cell_off, cnt, order);
+        bin_fixup<<<(C + kFixWarps - 1) / kFixWarps, kFixWarps * 32, 0, st>>>(cell_off, C, order);
     }
     AICA_CUDA(cudaGetLastError());
     return AICA_OK;
