@@ -272,12 +272,19 @@ aica_status aica_kinetic(const double *mass, int32_t n_species, const int32_t *s
  * caller already knows, with its workspace in a fixed device array inside
  * the library instead of allocated memory.
  *   cell_of  device [n] int32: cell of each molecule in [0, n_cells), or -1
- *            (the molecule is left out)
+ *            (the molecule is left out).  An id >= n_cells is left out the
+ *            same way (nothing is read or written outside the arrays given
+ *            and the workspace); the call does not synchronize to report
+ *            it, so a caller that may pass such ids compares cell_off[n_cells]
+ *            with the number of ids >= 0 it passed.
  *   order    device [n] out: order[s] = original index of slot s for
  *            s < cell_off[n_cells]; later entries are not written
  *   cell_off device [n_cells+1] out: cell c holds slots cell_off[c] ..
  *            cell_off[c+1]
- * The results equal those of aica_bin_molecules for the same cells.
+ * The results equal those of aica_bin_molecules for the same cells.  Each
+ * cell's slots are put in order by a bitonic sort in shared memory for
+ * cells of up to 2048 molecules and by a serial insertion sort (time
+ * growing with the square of the occupancy) above that.
  * Limits: n_cells <= 1048576 and n <= 2^30, else AICA_ERR_CAPACITY /
  * AICA_ERR_INVALID_ARG before any device work.  The workspace is about 4 MiB
  * of static device memory that every GPU loading this library holds until
@@ -305,6 +312,36 @@ aica_status aica_check_status(aica_mesh *mesh, void *stream);
  * to the number written and forgets them.  Not for use under stream capture. */
 aica_status aica_set_kernel_timing(aica_mesh *mesh, int enable);
 aica_status aica_take_kernel_times(aica_mesh *mesh, float *ms, int64_t cap, int64_t *n);
+
+/* Options of a mesh (no counterpart in the paper: precision policy and
+ * measurement switches of this implementation).
+ *   AICA_OPT_FP32_REFINE_TOL  (default 1e-5) FP32 forces: the per-component
+ *       error bound aica_forces guarantees relative to max(|F_ic|, ||F_i||)
+ *       on the box-periodic cluster path.  After the FP32 pass, a molecule
+ *       whose force is too small against the FP32 error scale of its pair
+ *       forces (|F_i| < 1e-6 sqrt(sum_l |f_kl|^2) / tol) is recomputed in FP64
+ *       with the exact pair set.  <= 0 turns the recomputation off.
+ *   AICA_OPT_COUNT_EVALUATED  (default 1) aica_forces fills counts_out[0..2]
+ *       (pairs of every listed cell pair, §2.3) with an extra pass over the
+ *       cell schedule when the FP32 cluster kernel runs; 0 skips that pass
+ *       and reports 0 there.  The within-rc counts [3..5] are always exact.
+ *   AICA_OPT_FP32_KERNEL      (default 0) FP32 box-periodic pair kernel:
+ *       0 the cluster kernel when the lists have a cluster schedule, 1 the
+ *       cell kernel (for comparison; its forces are not refined).
+ *   AICA_OPT_REFINED          (read only) molecules the last FP32
+ *       aica_forces call recomputed in FP64 (synchronizes `stream`).
+ *   AICA_OPT_CLUSTER_PATH     (read only) 1 when the built lists have a
+ *       cluster schedule (box periodicity, exact-separation bound met).
+ * AICA_ERR_INVALID_ARG for an unknown option or a read-only one set. */
+typedef enum {
+    AICA_OPT_FP32_REFINE_TOL = 0,
+    AICA_OPT_COUNT_EVALUATED = 1,
+    AICA_OPT_FP32_KERNEL = 2,
+    AICA_OPT_REFINED = 3,
+    AICA_OPT_CLUSTER_PATH = 4
+} aica_option;
+aica_status aica_set_option(aica_mesh *mesh, aica_option option, double value);
+aica_status aica_get_option(aica_mesh *mesh, aica_option option, double *value, void *stream);
 
 /* Work the last aica_forces call actually performed (host int64 out[2]):
  * out[0] pair distance tests, out[1] bounding-sphere tests of partner cells

@@ -86,6 +86,9 @@ SIGNATURES = {
                                     ctypes.c_void_p, ctypes.c_void_p]),
     "aica_mesh_set_transforms": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
     "aica_coupling_transform": (ctypes.c_int, [ctypes.c_void_p] * 6),
+    "aica_set_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]),
+    "aica_get_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.c_void_p]),
     "aica_last_error": (ctypes.c_char_p, []),
     "aica_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -258,6 +261,19 @@ def aica_sort_by_cell_noalloc(cell_of, n_cells, order, cell_off):
     _check(lib().aica_sort_by_cell_noalloc(_ptr(cell_of), n, int(n_cells), _ptr(order), _ptr(cell_off), _stream()))
 
 
+OPTIONS = {"fp32_refine_tol": 0, "count_evaluated": 1, "fp32_kernel": 2, "refined": 3, "cluster_path": 4}
+
+
+def aica_set_option(h, name, value):
+    _check(lib().aica_set_option(h, OPTIONS[name], float(value)))
+
+
+def aica_get_option(h, name):
+    v = ctypes.c_double(0)
+    _check(lib().aica_get_option(h, OPTIONS[name], ctypes.byref(v), _stream()))
+    return v.value
+
+
 def aica_set_deferred_checks(h, deferred):
     _check(lib().aica_set_deferred_checks(h, int(bool(deferred))))
 
@@ -395,6 +411,12 @@ class Mesh:
         """Deferred device-side checks: errors accumulate until check()."""
         aica_set_deferred_checks(self.h, deferred)
         self.deferred = bool(deferred)
+
+    def set_option(self, name, value):
+        aica_set_option(self.h, name, value)
+
+    def get_option(self, name):
+        return aica_get_option(self.h, name)
 
     def set_kernel_timing(self, enable=True):
         aica_set_kernel_timing(self.h, enable)

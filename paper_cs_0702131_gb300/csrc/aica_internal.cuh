@@ -19,6 +19,7 @@ constexpr int kMaxTri = 32;
 constexpr int kMaxVtx = 24;
 constexpr int kMaxEdg = 48;
 constexpr int kMaxSpecies = 8;
+constexpr int kMaxClusterCells = 16;   // cells of one pair-kernel cluster (see mesh.cu)
 
 // Device-side error flags (bitwise OR into mesh->d_flags[0]).
 enum : unsigned {
@@ -86,6 +87,15 @@ struct RunEntry {
     int32_t n;      // image vector in bits 0-23 (as WorkEntry), len - 1 in bits 24-31
 };
 
+// One run of the FP32 cluster kernel's schedule: partner molecules of the
+// cells c0 .. c0 + ncells - 1 (consecutive clusters under one image and one
+// molecule frame), shifted into the owner cluster's frame by dh + dl (dh a
+// multiple of 2^-qexp, exact in FP32; dl the FP32 remainder).
+//   dh.w: c0 (int bits);  dl.w: ncells | (image n, 3 x 4-bit fields) << 12
+struct ClRun {
+    float4 dh, dl;
+};
+
 // A referring transform P' = y + R.P (§2.2.2), R row-major.
 struct Xform {
     double R[9], y[3];
@@ -128,6 +138,12 @@ struct aica_mesh {
     // Molecule frame: binned FP32 coordinates are local to orgm_c * 2^-10, an
     // origin shared by runs of consecutive cells (see mesh.cu).
     aica::DevBuf orgm, orgm64;                               // [C*3] int32, double (exact)
+    double max_mlocal = 0;                                   // largest |cell bound - its molecule origin|
+    // Clusters (runs of consecutive cells, see mesh.cu): first cell of each
+    // cluster [n_cl+1] and cluster of each cell [C].
+    int64_t n_cl = 0;
+    int max_cl_cells = 0;
+    aica::DevBuf cl_first, cl_of;
     aica::DevBuf tri32, vtx32, edg32, ctr32;                 // float, minus org_c
     aica::DevBuf rad32;                                      // [C] float, rad rounded up
     double max_local = 0;                                    // largest |local coordinate|
@@ -146,6 +162,14 @@ struct aica_mesh {
     int64_t n_dil = 0, n_ref = 0, n_ref_ids = 0, n_ties = 0, n_work = 0, n_runs = 0;
     aica::DevBuf dil_off, dil_ids, ref_src, ref_n, ref_off, ref_ids;   // int32 (ref_n: 3 int32)
     aica::DevBuf run_off, runs;              // [C+1] int32 first run of each cell; RunEntry
+    // Cluster schedule of the FP32 box-periodic kernel: per cluster A the runs
+    // of partner clusters B > A (any image) and B = A (lexicographically
+    // positive image), as RunEntry over clusters; and the full (symmetric)
+    // partner list of every cluster for the FP64 refinement, one entry per
+    // (partner cluster, image).
+    aica::DevBuf cl_run_off, cl_runs, cl_full_off, cl_full;
+    int64_t n_cl_runs = -1, n_cl_full = 0;    // n_cl_runs < 0: no cluster schedule
+    int qexp = 20;                           // cluster kernel: hi parts are multiples of 2^-qexp
     // General referring transforms (empty: box periodicity).  With them the
     // image field of work entries and runs holds a transform index (0 = none).
     std::vector<aica::Xform> xf_gen;         // generators given by the caller
@@ -160,6 +184,12 @@ struct aica_mesh {
     bool binned = false;
     int64_t n_mol = 0, cap_mol = 0;
     aica::DevBuf cell_of, order, cell_off, fill, xloc, xs64, inv;
+    aica::DevBuf xlo;                        // [n] float4: x - o_m - xloc (FP32 remainder), binned order
+    aica::DevBuf flag_list;                  // FP32 forces: [0] count, [1..] binned molecules to refine in FP64
+    double refine_tol = 1e-5;                // FP32 forces: refine a molecule whose error bound exceeds this (0: off)
+    bool count_evaluated = true;             // aica_forces: count the AICA-evaluated pairs (an extra pass)
+    int fp32_kernel = 0;                     // 0: cluster kernel when available, 1: the cell kernel
+    int64_t n_refined = 0;                   // molecules the last FP32 call recomputed in FP64 (host copy on demand)
     aica::DevBuf unsorted;                   // [n] binned slots before the in-cell sort (cells of a few molecules)
     int max_species = -1;                    // from the last checked binning, -1 if unknown
     aica::DevBuf sph;                        // [C] float4 molecule bounding sphere per cell (local frame)

@@ -72,6 +72,44 @@ extern "C" aica_status aica_get_work_counters(aica_mesh *m, int64_t *out, void *
     return AICA_OK;
 }
 
+extern "C" aica_status aica_set_option(aica_mesh *m, aica_option opt, double v) {
+    if (!m) { aica::set_error("aica_set_option: mesh is NULL"); return AICA_ERR_INVALID_ARG; }
+    switch (opt) {
+    case AICA_OPT_FP32_REFINE_TOL: m->refine_tol = v; return AICA_OK;
+    case AICA_OPT_COUNT_EVALUATED: m->count_evaluated = v != 0; return AICA_OK;
+    case AICA_OPT_FP32_KERNEL:
+        if (v != 0 && v != 1) break;
+        m->fp32_kernel = (int)v;
+        return AICA_OK;
+    default: break;
+    }
+    aica::set_error("aica_set_option: unknown, read-only or invalid option %d = %g", (int)opt, v);
+    return AICA_ERR_INVALID_ARG;
+}
+
+extern "C" aica_status aica_get_option(aica_mesh *m, aica_option opt, double *v, void *stream) {
+    if (!m || !v) { aica::set_error("aica_get_option: NULL argument"); return AICA_ERR_INVALID_ARG; }
+    switch (opt) {
+    case AICA_OPT_FP32_REFINE_TOL: *v = m->refine_tol; return AICA_OK;
+    case AICA_OPT_COUNT_EVALUATED: *v = m->count_evaluated ? 1 : 0; return AICA_OK;
+    case AICA_OPT_FP32_KERNEL: *v = m->fp32_kernel; return AICA_OK;
+    case AICA_OPT_CLUSTER_PATH: *v = m->built && m->n_cl_runs >= 0 ? 1 : 0; return AICA_OK;
+    case AICA_OPT_REFINED: {
+        int n = 0;
+        if (m->flag_list.p) {
+            cudaStream_t st = (cudaStream_t)stream;
+            AICA_CUDA(cudaMemcpyAsync(&n, m->flag_list.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+            AICA_CUDA(cudaStreamSynchronize(st));
+        }
+        *v = n;
+        return AICA_OK;
+    }
+    default: break;
+    }
+    aica::set_error("aica_get_option: unknown option %d", (int)opt);
+    return AICA_ERR_INVALID_ARG;
+}
+
 extern "C" int64_t aica_last_launch_count(const aica_mesh *m) { return m ? m->launches : 0; }
 
 extern "C" aica_status aica_set_kernel_timing(aica_mesh *m, int enable) {

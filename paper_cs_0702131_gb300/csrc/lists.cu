@@ -421,7 +421,281 @@ __global__ void lst_runs(const int *work_off, const WorkEntry *work, const int *
     if (run_cnt) run_cnt[A] = nr;
 }
 
+// ------------------------------------------------------------ cluster schedule
+// The FP32 box-periodic pair kernel works on clusters (runs of consecutive
+// cells, mesh.cu).  Every cell-level schedule entry (I -> J, n) has J >= I
+// (the DIL half rule and the canonical image rule), so with contiguous
+// clusters the cluster pair (cl(I), cl(J), n) has cl(J) >= cl(I): each owner
+// cluster A collects its own cells' entries only.  For B = A with n != 0 the
+// pairs of (A, A, n) and (A, A, -n) are mirror images; the lexicographically
+// positive image is kept.  B = A with n = 0 (pairs inside the cluster) is
+// implicit.  Keys (n << 32 | B) are sorted and made unique per cluster; runs
+// are consecutive partner clusters under one image and one molecule frame.
+// The full list (for the FP64 refinement of single molecules) holds, for each
+// cluster, every (partner cluster, image) whose molecules can lie within the
+// cut-off of its molecules: its own keys and the mirrors of the keys that
+// name it.
+constexpr int kClKeys = 2048, kClWarps = 4;
+constexpr unsigned long long kNoKey = ~0ull;
+
+__device__ __forceinline__ int32_t neg_n(int32_t p) {
+    return pack_n(-unpack_n(p, 0), -unpack_n(p, 1), -unpack_n(p, 2));
+}
+__device__ __forceinline__ unsigned long long cl_key(int B, int32_t n) {
+    return ((unsigned long long)(n & 0xffffff) << 32) | (unsigned)B;
+}
+
+// Ascending bitonic sort of b[0, P), P a power of two, by one warp.
+__device__ void warp_bitonic(unsigned long long *b, int P, int lane) {
+    for (int size = 2; size <= P; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = lane; i < P / 2; i += 32) {
+                const int lo = 2 * i - (i & (stride - 1)), hi = lo + stride;
+                const bool up = (lo & size) == 0;
+                const unsigned long long x = b[lo], y = b[hi];
+                if ((x > y) == up) {
+                    b[lo] = y;
+                    b[hi] = x;
+                }
+            }
+            __syncwarp();
+        }
+}
+
+struct ClArgs {
+    int ncl;
+    const int *cl_first, *cl_of, *work_off, *orgm;
+    const WorkEntry *work;
+    int *run_cnt, *own_cnt, *rev_cnt;            // pass 0
+    const int *run_off, *full_off;               // pass 1
+    int *cursor;
+    ClRun *runs;
+    unsigned long long *full;
+    unsigned *flags;
+    const double *orgm64;
+    double L[3];
+    double qs, qsi, dmax;        // 2^q, 2^-q, largest |shift| with an exact FP32 hi part
+};
+
+// The run of clusters B0 .. B0 + len - 1 under image n, seen from cluster A.
+__device__ ClRun make_clrun(const ClArgs &a, int A, int B0, int len, int32_t n) {
+    const int c0 = a.cl_first[B0], c1 = a.cl_first[B0 + len], cA = a.cl_first[A];
+    const double *oB = a.orgm64 + 3 * c0, *oA = a.orgm64 + 3 * cA;
+    float h[3], l[3];
+    int code = 0;
+    for (int d = 0; d < 3; ++d) {
+        const int nd = unpack_n(n, d);
+        const double D = (oB[d] - oA[d]) + (double)nd * a.L[d];
+        if (!(fabs(D) < a.dmax)) atomicOr(a.flags, kFlagCapacity);
+        const double hi = rint(D * a.qs) * a.qsi;
+        h[d] = (float)hi;
+        l[d] = (float)(D - hi);
+        if (nd < -8 || nd > 7) atomicOr(a.flags, kFlagCapacity);
+        code |= (nd & 15) << (4 * d);
+    }
+    if (c1 - c0 > 4095) atomicOr(a.flags, kFlagCapacity);
+    ClRun r;
+    r.dh = make_float4(h[0], h[1], h[2], __int_as_float(c0));
+    r.dl = make_float4(l[0], l[1], l[2], __int_as_float((c1 - c0) | (code << 12)));
+    return r;
+}
+
+__device__ __forceinline__ bool same_frame(const int *orgm, const int *cl_first, int B0, int B1) {
+    const int *a = orgm + 3 * cl_first[B0], *b = orgm + 3 * cl_first[B1];
+    return a[0] == b[0] && a[1] == b[1] && a[2] == b[2];
+}
+
+template <int PASS>
+__global__ void __launch_bounds__(kClWarps * 32) cl_sched(ClArgs a) {
+    extern __shared__ unsigned long long cl_sh[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned long long *b = cl_sh + (size_t)w * kClKeys;
+    for (int A = blockIdx.x * kClWarps + w; A < a.ncl; A += gridDim.x * kClWarps) {
+        const int e0 = a.work_off[a.cl_first[A]], e1 = a.work_off[a.cl_first[A + 1]], m = e1 - e0;
+        if (m > kClKeys) {
+            if (lane == 0) atomicOr(a.flags, kFlagCapacity);
+            continue;
+        }
+        int P = 2;
+        while (P < m) P <<= 1;
+        for (int i = lane; i < P; i += 32) {
+            unsigned long long key = kNoKey;
+            if (i < m) {
+                const WorkEntry e = a.work[e0 + i];
+                const int B = a.cl_of[e.j];
+                int32_t n = e.n & 0xffffff;
+                if (B != A) key = cl_key(B, n);
+                else if (n != 0) {
+                    const int x = unpack_n(n, 0), y = unpack_n(n, 1), z = unpack_n(n, 2);
+                    const bool pos = x > 0 || (x == 0 && (y > 0 || (y == 0 && z > 0)));
+                    key = cl_key(A, pos ? n : neg_n(n));
+                }
+            }
+            b[i] = key;
+        }
+        __syncwarp();
+        warp_bitonic(b, P, lane);
+        if (lane == 0) {
+            int nu = 0, nr = 0, len = 0, B0 = 0, Bp = 0;
+            int32_t np = 0;
+            const int r0 = PASS == 1 ? a.run_off[A] : 0, f0 = PASS == 1 ? a.full_off[A] : 0;
+            for (int i = 0; i < m && b[i] != kNoKey; ++i) {
+                if (i > 0 && b[i] == b[i - 1]) continue;
+                const int B = (int)(b[i] & 0xffffffffu);
+                const int32_t n = (int32_t)(b[i] >> 32);
+                if (PASS == 0) {
+                    atomicAdd(a.rev_cnt + B, 1);
+                } else {
+                    a.full[f0 + nu] = b[i];
+                    a.full[atomicAdd(a.cursor + B, 1)] = cl_key(A, neg_n(n));
+                }
+                ++nu;
+                const bool cont = len > 0 && n == np && B == Bp + 1 && len < 255 && same_frame(a.orgm, a.cl_first, B0, B);
+                if (cont) {
+                    ++len;
+                } else {
+                    if (len > 0) {
+                        if (PASS == 1) a.runs[r0 + nr] = make_clrun(a, A, B0, len, np);
+                        ++nr;
+                    }
+                    B0 = B;
+                    len = 1;
+                }
+                Bp = B;
+                np = n;
+            }
+            if (len > 0) {
+                if (PASS == 1) a.runs[r0 + nr] = make_clrun(a, A, B0, len, np);
+                ++nr;
+            }
+            if (PASS == 0) {
+                a.run_cnt[A] = nr;
+                a.own_cnt[A] = nu;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// rev_cnt[A] += own_cnt[A]: the full list of A holds its own keys and the mirrors naming it
+__global__ void add_counts(int ncl, const int *own_cnt, int *rev_cnt) {
+    const int A = blockIdx.x * blockDim.x + threadIdx.x;
+    if (A < ncl) rev_cnt[A] += own_cnt[A];
+}
+
+__global__ void cl_cursor(int ncl, const int *full_off, const int *own_cnt, int *cursor) {
+    const int A = blockIdx.x * blockDim.x + threadIdx.x;
+    if (A < ncl) cursor[A] = full_off[A] + own_cnt[A];
+}
+
+// Sort each cluster's full list (its reverse entries arrive in any order).
+__global__ void __launch_bounds__(kClWarps * 32) cl_sort_full(int ncl, const int *full_off, unsigned long long *full,
+                                                               unsigned *flags) {
+    extern __shared__ unsigned long long cl_sh[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned long long *b = cl_sh + (size_t)w * kClKeys;
+    for (int A = blockIdx.x * kClWarps + w; A < ncl; A += gridDim.x * kClWarps) {
+        const int f0 = full_off[A], m = full_off[A + 1] - f0;
+        if (m > kClKeys) {
+            if (lane == 0) atomicOr(flags, kFlagCapacity);
+            continue;
+        }
+        int P = 2;
+        while (P < m) P <<= 1;
+        for (int i = lane; i < P; i += 32) b[i] = i < m ? full[f0 + i] : kNoKey;
+        __syncwarp();
+        warp_bitonic(b, P, lane);
+        for (int i = lane; i < m; i += 32) full[f0 + i] = b[i];
+        __syncwarp();
+    }
+}
+
 }  // namespace
+}  // namespace aica
+
+namespace aica {
+// Build the cluster schedule of the FP32 box-periodic kernel (see cl_sched)
+// from the cell-level work entries.  Leaves n_cl_runs = -1 (the FP32 forces
+// then use the cell kernel) under general referring transforms or the
+// vertex criterion, when a cluster has more entries than a warp sorts in
+// shared memory, or when the exact-separation bound of the binned
+// coordinates does not cover the cut-off.
+aica_status build_cluster_schedule(aica_mesh *m, cudaStream_t st) {
+    m->n_cl_runs = -1;
+    m->n_cl_full = 0;
+    const int ncl = (int)m->n_cl;
+    // the cluster kernel evaluates every pair within rc of two partner
+    // clusters: that is the method's pair set only when the cell lists are
+    // complete (minimum-distance criterion), not under the vertex criterion
+    if (ncl < 1 || !m->xf_gen.empty() || m->criterion != AICA_DIL_MIN_DISTANCE) return AICA_OK;
+    if (!(m->max_mlocal + m->rc + m->skin < ldexp(1.0, 24 - m->qexp) * 0.999)) return AICA_OK;
+    DevBuf cnt, sw;
+    AICA_CUDA(cnt.reserve(sizeof(int) * 4 * (size_t)(ncl + 1)));
+    AICA_CUDA(sw.reserve(sizeof(int) * (scan_work_items(ncl) + 8)));
+    int *run_cnt = cnt.as<int>(), *own_cnt = run_cnt + (ncl + 1), *rev_cnt = own_cnt + (ncl + 1),
+        *cursor = rev_cnt + (ncl + 1);
+    AICA_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int) * 4 * (size_t)(ncl + 1), st));
+    AICA_CUDA(cudaMemsetAsync(m->flags.p, 0, sizeof(unsigned), st));
+    const size_t shm = sizeof(unsigned long long) * kClWarps * kClKeys;
+    AICA_CUDA(cudaFuncSetAttribute(cl_sched<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    AICA_CUDA(cudaFuncSetAttribute(cl_sched<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    AICA_CUDA(cudaFuncSetAttribute(cl_sort_full, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    const unsigned grid = (unsigned)std::min<int64_t>((ncl + kClWarps - 1) / kClWarps, 152 * 8);
+    ClArgs a{};
+    a.ncl = ncl;
+    a.cl_first = m->cl_first.as<int>();
+    a.cl_of = m->cl_of.as<int>();
+    a.work_off = m->work_off.as<int>();
+    a.orgm = m->orgm.as<int>();
+    a.work = m->work.as<WorkEntry>();
+    a.run_cnt = run_cnt;
+    a.own_cnt = own_cnt;
+    a.rev_cnt = rev_cnt;
+    a.flags = m->flags.as<unsigned>();
+    a.orgm64 = m->orgm64.as<double>();
+    for (int d = 0; d < 3; ++d) a.L[d] = m->box.periodic[d] ? m->box.L[d] : 0.0;
+    a.qs = ldexp(1.0, m->qexp);
+    a.qsi = ldexp(1.0, -m->qexp);
+    a.dmax = ldexp(1.0, 24 - m->qexp) * 0.999;
+    cl_sched<0><<<grid, kClWarps * 32, shm, st>>>(a);
+    // full list sizes: own keys + mirrors
+    AICA_CUDA(m->cl_run_off.reserve(sizeof(int) * (ncl + 1)));
+    AICA_CUDA(m->cl_full_off.reserve(sizeof(int) * (ncl + 1)));
+    m->launches += 1 + exclusive_scan<int, int>(run_cnt, ncl, m->cl_run_off.as<int>(), sw.as<int>(), st);
+    add_counts<<<(ncl + 255) / 256, 256, 0, st>>>(ncl, own_cnt, rev_cnt);
+    m->launches += 1 + exclusive_scan<int, int>(rev_cnt, ncl, m->cl_full_off.as<int>(), sw.as<int>(), st);
+    int tot[2] = {0, 0};
+    unsigned flags = 0;
+    AICA_CUDA(cudaMemcpyAsync(&tot[0], m->cl_run_off.as<int>() + ncl, sizeof(int), cudaMemcpyDeviceToHost, st));
+    AICA_CUDA(cudaMemcpyAsync(&tot[1], m->cl_full_off.as<int>() + ncl, sizeof(int), cudaMemcpyDeviceToHost, st));
+    AICA_CUDA(cudaMemcpyAsync(&flags, m->flags.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    AICA_CUDA(cudaStreamSynchronize(st));
+    if (flags & kFlagCapacity) {
+        AICA_CUDA(cudaMemsetAsync(m->flags.p, 0, sizeof(unsigned), st));
+        return AICA_OK;
+    }
+    AICA_CUDA(m->cl_runs.reserve(sizeof(ClRun) * std::max(tot[0], 1)));
+    AICA_CUDA(m->cl_full.reserve(sizeof(unsigned long long) * std::max(tot[1], 1)));
+    cl_cursor<<<(ncl + 255) / 256, 256, 0, st>>>(ncl, m->cl_full_off.as<int>(), own_cnt, cursor);
+    a.run_off = m->cl_run_off.as<int>();
+    a.full_off = m->cl_full_off.as<int>();
+    a.cursor = cursor;
+    a.runs = m->cl_runs.as<ClRun>();
+    a.full = m->cl_full.as<unsigned long long>();
+    cl_sched<1><<<grid, kClWarps * 32, shm, st>>>(a);
+    cl_sort_full<<<grid, kClWarps * 32, shm, st>>>(ncl, m->cl_full_off.as<int>(), m->cl_full.as<unsigned long long>(),
+                                                   m->flags.as<unsigned>());
+    m->launches += 3;
+    AICA_CUDA(cudaMemcpyAsync(&flags, m->flags.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    AICA_CUDA(cudaStreamSynchronize(st));
+    if (flags & kFlagCapacity) {
+        AICA_CUDA(cudaMemsetAsync(m->flags.p, 0, sizeof(unsigned), st));
+        return AICA_OK;
+    }
+    m->n_cl_runs = tot[0];
+    m->n_cl_full = tot[1];
+    return AICA_OK;
+}
 }  // namespace aica
 
 using namespace aica;
@@ -456,6 +730,7 @@ extern "C" aica_status aica_build_interaction_list_ex(aica_mesh *m, double rc, d
     const int C = (int)m->n_cells;
     m->launches = 0;
     m->built = false;
+    m->n_cl_runs = -1;
 
     // ---- centroid bucket grid (host): about one cell per bucket
     QArgs a{};
@@ -638,6 +913,13 @@ extern "C" aica_status aica_build_interaction_list_ex(aica_mesh *m, double rc, d
     }
     d_boff.release(); d_bcell.release(); d_cnt.release(); d_seg.release(); d_keys.release(); d_scan.release();
     d_ties.release();
+    m->rc = rc;
+    m->skin = skin;
+    m->criterion = (int)criterion;
+    {
+        aica_status s3 = build_cluster_schedule(m, st);
+        if (s3 != AICA_OK) return s3;
+    }
     m->n_dil = tot[0];
     m->n_ref_ids = tot[1];
     m->n_ref = tot[2];

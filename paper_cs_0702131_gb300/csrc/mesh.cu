@@ -243,12 +243,43 @@ extern "C" aica_status aica_mesh_create(const double *points, int64_t n_points, 
         h_rad32[c] = (float)(h_rad[c] * (1 + 1e-6)) + 1e-6f;
     }
 
-    // ---- molecule-frame origins: consecutive cells whose joint bounding box
-    // stays within twice the median cell extent share one dyadic origin, so
-    // a run of consecutive partner cells is one shift for the pair kernels
+    // ---- clusters and molecule frames.  A cluster is a run of consecutive
+    // cells whose joint bounding box is hardly larger than the largest box
+    // among its cells (the tetrahedra split from one hexahedron, or one cell
+    // of a hexahedral mesh): the FP32 pair kernel takes a cluster's molecules
+    // as one i-tile and culls partners against their joint box.  A molecule
+    // frame (one dyadic origin for the binned FP32 coordinates) is a run of
+    // consecutive clusters whose joint box stays within twice the median cell
+    // extent, so a run of consecutive partner cells or clusters is one shift.
     std::vector<int32_t> h_orgm(3 * n_cells);
     std::vector<double> h_orgm64(3 * n_cells);
+    std::vector<int32_t> h_cl_first, h_cl_of(n_cells);
+    double max_mlocal = 0;
     {
+        auto vol = [](const double *lo, const double *hi) {
+            return std::max(hi[0] - lo[0], 0.0) * std::max(hi[1] - lo[1], 0.0) * std::max(hi[2] - lo[2], 0.0);
+        };
+        double clo[3] = {0, 0, 0}, chi[3] = {0, 0, 0}, vmax = 0;
+        for (int64_t c = 0; c < n_cells; ++c) {
+            const double *lo = &h_lo[3 * c], *hi = &h_hi[3 * c];
+            bool join = !h_cl_first.empty() && c - h_cl_first.back() < kMaxClusterCells;
+            if (join) {
+                double jlo[3], jhi[3];
+                for (int d = 0; d < 3; ++d) { jlo[d] = std::min(clo[d], lo[d]); jhi[d] = std::max(chi[d], hi[d]); }
+                join = vol(jlo, jhi) <= 1.35 * std::max(vmax, vol(lo, hi));
+            }
+            if (!join) {
+                h_cl_first.push_back((int32_t)c);
+                vmax = 0;
+                for (int d = 0; d < 3; ++d) { clo[d] = lo[d]; chi[d] = hi[d]; }
+            }
+            for (int d = 0; d < 3; ++d) { clo[d] = std::min(clo[d], lo[d]); chi[d] = std::max(chi[d], hi[d]); }
+            vmax = std::max(vmax, vol(lo, hi));
+            h_cl_of[c] = (int32_t)h_cl_first.size() - 1;
+        }
+        h_cl_first.push_back((int32_t)n_cells);
+        const int64_t ncl = (int64_t)h_cl_first.size() - 1;
+
         std::vector<double> ext(n_cells);
         for (int64_t c = 0; c < n_cells; ++c) {
             double e = 0;
@@ -261,7 +292,7 @@ extern "C" aica_status aica_mesh_create(const double *points, int64_t n_points, 
             std::nth_element(tmp.begin(), tmp.begin() + n_cells / 2, tmp.end());
             emax = 2.0 * tmp[n_cells / 2];
         }
-        int64_t g0 = 0;
+        int64_t g0 = 0;           // first cell of the open frame
         double glo_[3], ghi_[3];
         auto close_group = [&](int64_t g1) {
             for (int d = 0; d < 3; ++d) {
@@ -269,25 +300,34 @@ extern "C" aica_status aica_mesh_create(const double *points, int64_t n_points, 
                 for (int64_t c = g0; c < g1; ++c) {
                     h_orgm[3 * c + d] = k;
                     h_orgm64[3 * c + d] = (double)k / 1024.0;
+                    max_mlocal = std::max(max_mlocal, std::max(fabs(h_lo[3 * c + d] - (double)k / 1024.0),
+                                                               fabs(h_hi[3 * c + d] - (double)k / 1024.0)));
                 }
             }
         };
-        for (int64_t c = 0; c < n_cells; ++c) {
-            bool join = c > g0 && c - g0 < 64;
+        for (int64_t q = 0; q < ncl; ++q) {
+            const int64_t c0 = h_cl_first[q], c1 = h_cl_first[q + 1];
+            double qlo[3], qhi[3];
+            for (int d = 0; d < 3; ++d) { qlo[d] = INFINITY; qhi[d] = -INFINITY; }
+            for (int64_t c = c0; c < c1; ++c)
+                for (int d = 0; d < 3; ++d) {
+                    qlo[d] = std::min(qlo[d], h_lo[3 * c + d]);
+                    qhi[d] = std::max(qhi[d], h_hi[3 * c + d]);
+                }
+            bool join = c0 > g0 && c1 - g0 <= 64;
             if (join) {
                 double e = 0;
-                for (int d = 0; d < 3; ++d)
-                    e = std::max(e, std::max(ghi_[d], h_hi[3 * c + d]) - std::min(glo_[d], h_lo[3 * c + d]));
+                for (int d = 0; d < 3; ++d) e = std::max(e, std::max(ghi_[d], qhi[d]) - std::min(glo_[d], qlo[d]));
                 join = e <= emax;
             }
             if (!join) {
-                if (c > 0) close_group(c);
-                g0 = c;
-                for (int d = 0; d < 3; ++d) { glo_[d] = h_lo[3 * c + d]; ghi_[d] = h_hi[3 * c + d]; }
+                if (c0 > 0) close_group(c0);
+                g0 = c0;
+                for (int d = 0; d < 3; ++d) { glo_[d] = qlo[d]; ghi_[d] = qhi[d]; }
             } else {
                 for (int d = 0; d < 3; ++d) {
-                    glo_[d] = std::min(glo_[d], h_lo[3 * c + d]);
-                    ghi_[d] = std::max(ghi_[d], h_hi[3 * c + d]);
+                    glo_[d] = std::min(glo_[d], qlo[d]);
+                    ghi_[d] = std::max(ghi_[d], qhi[d]);
                 }
             }
         }
@@ -376,6 +416,15 @@ extern "C" aica_status aica_mesh_create(const double *points, int64_t n_points, 
     m->box = *box;
     m->max_tri = max_tri; m->max_vtx = max_vtx; m->max_edg = max_edg;
     m->max_local = max_local;
+    m->max_mlocal = max_mlocal;
+    // the FP32 cluster kernel splits binned coordinates at multiples of
+    // 2^-qexp: |x - o_m| 2^qexp < 2^22 keeps the parts exact, with room for
+    // the shifts of nearby partners
+    m->qexp = 22 - (int)ceil(log2(std::max(max_mlocal, 1e-3) * (1 + 1e-9)));
+    m->qexp = std::min(m->qexp, 40);
+    m->n_cl = (int64_t)h_cl_first.size() - 1;
+    m->max_cl_cells = 0;
+    for (int64_t q = 0; q < m->n_cl; ++q) m->max_cl_cells = std::max<int>(m->max_cl_cells, h_cl_first[q + 1] - h_cl_first[q]);
     for (int d = 0; d < 3; ++d) { m->G[d] = G[d]; m->glo[d] = glo[d]; m->gh[d] = gh[d]; }
     cudaError_t e = cudaSuccess;
     const char *what = "upload";
@@ -396,6 +445,8 @@ extern "C" aica_status aica_mesh_create(const double *points, int64_t n_points, 
     if (e == cudaSuccess) e = upload(m->orgk, h_orgk);
     if (e == cudaSuccess) e = upload(m->orgm, h_orgm);
     if (e == cudaSuccess) e = upload(m->orgm64, h_orgm64);
+    if (e == cudaSuccess) e = upload(m->cl_first, h_cl_first);
+    if (e == cudaSuccess) e = upload(m->cl_of, h_cl_of);
     if (e == cudaSuccess) e = upload(m->tri32, h_tri32);
     if (e == cudaSuccess) e = upload(m->vtx32, h_vtx32);
     if (e == cudaSuccess) e = upload(m->edg32, h_edg32);
@@ -428,7 +479,7 @@ extern "C" aica_status aica_mesh_create(const double *points, int64_t n_points, 
 extern "C" void aica_mesh_destroy(aica_mesh *m) {
     if (!m) return;
     aica::DevBuf *bufs[] = {&m->tri_off, &m->tri, &m->tri_nbr, &m->vtx_off, &m->vtx, &m->edg_off, &m->edg, &m->ctr, &m->rad,
-                            &m->lo, &m->hi, &m->org, &m->ntri, &m->orgk, &m->orgm, &m->orgm64, &m->tri32, &m->vtx32, &m->edg32, &m->ctr32, &m->rad32, &m->box32, &m->bkt_off, &m->bkt_cells, &m->nbr_off, &m->nbr, &m->dil_off,
+                            &m->lo, &m->hi, &m->org, &m->ntri, &m->orgk, &m->orgm, &m->orgm64, &m->cl_first, &m->cl_of, &m->cl_run_off, &m->cl_runs, &m->cl_full_off, &m->cl_full, &m->xlo, &m->flag_list, &m->tri32, &m->vtx32, &m->edg32, &m->ctr32, &m->rad32, &m->box32, &m->bkt_off, &m->bkt_cells, &m->nbr_off, &m->nbr, &m->dil_off,
                             &m->dil_ids, &m->ref_src, &m->ref_n, &m->ref_off, &m->ref_ids, &m->run_off, &m->runs, &m->xf_dev, &m->run_d, &m->work_off,
                             &m->work, &m->work_split, &m->proc_order, &m->cell_of, &m->order, &m->unsorted,
                             &m->cell_off, &m->fill, &m->inv, &m->sph, &m->xloc, &m->xs64, &m->facc,

@@ -78,6 +78,7 @@ struct PairArgs {
     const double *xs64;
     const float4 *sph;           // per-cell molecule bounding spheres (local frame)
     float rc2_lo, rc2_hi;
+    float rc2_pre;               // cluster kernel: hi-part test threshold (margin above the remainders)
     double rc2_d;
     double L[3];
     int S;
@@ -249,19 +250,23 @@ struct Warp32 {
 // (XF) the pair's energy and virial r (x) f are added here with weight w.
 template <bool MULTI, bool SHIFT, bool XF>
 __device__ __forceinline__ void pair32(const float4 *tab, float4 t0, int spi, int spj, float rx, float ry, float rz,
-                                       float r2, bool in, float w, float *fi3, R3<float> &fj, float &u_acc,
-                                       float *v) {
+                                       float r2, bool in, float w, float *fi4, R3<float> &fj, float &gj,
+                                       float &u_acc, float *v) {
     float fs, u;
     lj32<MULTI, SHIFT>(tab, t0, spi, spj, r2, fs, u);
     fs = in ? fs : 0.f;
     if (XF) u_acc += in ? w * u : 0.f;
     else u_acc += in ? u : 0.f;
-    fi3[0] = fmaf(fs, rx, fi3[0]);
-    fi3[1] = fmaf(fs, ry, fi3[1]);
-    fi3[2] = fmaf(fs, rz, fi3[2]);
+    fi4[0] = fmaf(fs, rx, fi4[0]);
+    fi4[1] = fmaf(fs, ry, fi4[1]);
+    fi4[2] = fmaf(fs, rz, fi4[2]);
     fj.x = fmaf(-fs, rx, fj.x);
     fj.y = fmaf(-fs, ry, fj.y);
     fj.z = fmaf(-fs, rz, fj.z);
+    // |f|^2 of the pair: the scale of the FP32 error of both molecules' forces
+    const float g = fs * fs;
+    fi4[3] = fmaf(g, r2, fi4[3]);
+    gj = fmaf(g, r2, gj);
     if (XF) {
         const float g = w * fs, gx = g * rx, gy = g * ry;
         v[1] = fmaf(gx, rx, v[1]);
@@ -280,8 +285,8 @@ __device__ __forceinline__ void pair32(const float4 *tab, float4 t0, int spi, in
 // index below lmax_k take part.  Returns the pairs within rc.
 template <int NI_, bool MULTI, bool SHIFT, bool SAME, bool XF>
 __device__ __forceinline__ unsigned eval_partner(const PairArgs &a, const float4 *tab, const float4 *xi, int ni,
-                                                 int k0, float4 xj, int l, int np, int lmax_k, float (&fi)[3 * NI_],
-                                                 R3<float> &fj, float &u_acc, float *v, float w) {
+                                                 int k0, float4 xj, int l, int np, int lmax_k, float (&fi)[4 * NI_],
+                                                 R3<float> &fj, float &gj, float &u_acc, float *v, float w) {
     unsigned nin = 0, bm = 0;
     const float4 t0 = tab[0];
 #pragma unroll
@@ -294,7 +299,7 @@ __device__ __forceinline__ unsigned eval_partner(const PairArgs &a, const float4
             const bool in = ok && r2 < a.rc2_lo;
             if (ok && !in && r2 < a.rc2_hi) bm |= 1u << t;
             pair32<MULTI, SHIFT, XF>(tab, t0, __float_as_int(x.w), __float_as_int(xj.w), rx, ry, rz, r2, in, w,
-                                     &fi[3 * t], fj, u_acc, v);
+                                     &fi[4 * t], fj, gj, u_acc, v);
             nin += in;
         }
     }
@@ -307,7 +312,7 @@ __device__ __forceinline__ unsigned eval_partner(const PairArgs &a, const float4
                     const float rx = x.x - xj.x, ry = x.y - xj.y, rz = x.z - xj.z;
                     const float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
                     pair32<MULTI, SHIFT, XF>(tab, t0, __float_as_int(x.w), __float_as_int(xj.w), rx, ry, rz, r2, true,
-                                             w, &fi[3 * t], fj, u_acc, v);
+                                             w, &fi[4 * t], fj, gj, u_acc, v);
                     nin++;
                 }
             }
@@ -338,6 +343,19 @@ __device__ __forceinline__ void chunk_reduce(float (&v)[3 * NI_], int lane) {
     for (int o = 16 / NI_; o > 0; o >>= 1)
 #pragma unroll
         for (int i = 0; i < 3; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+}
+
+// The same for NI_ groups of 4 values (x, y, z, |f|^2): on return lanes
+// t * (32 / NI_) .. hold the totals of v[4t..4t+4) in v[0..4).
+template <int NI_>
+__device__ __forceinline__ void chunk_reduce4(float (&v)[4 * NI_], int lane) {
+    if (NI_ >= 2) halve<4 * NI_>(v, lane, 16);
+    if (NI_ >= 4) halve<2 * NI_>(v, lane, 8);
+    if (NI_ >= 8) halve<NI_>(v, lane, 4);
+#pragma unroll
+    for (int o = 16 / NI_; o > 0; o >>= 1)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
 }
 
 __device__ __forceinline__ void outer7(float (&v)[7], float ax, float ay, float az, float bx, float by, float bz) {
@@ -492,9 +510,9 @@ __global__ void __launch_bounds__(kThreads32, MINB) pair_fwd32(PairArgs a) {
                 const int ni = min(NI_, nI - i0), k0 = s0 + i0;
                 __syncwarp();
                 if (lane < ni) w.xi[lane] = a.xloc[k0 + lane];
-                float fi[3 * NI_];
+                float fi[4 * NI_];
 #pragma unroll
-                for (int i = 0; i < 3 * NI_; ++i) fi[i] = 0.f;
+                for (int i = 0; i < 4 * NI_; ++i) fi[i] = 0.f;
                 int head = 0, qn = 0;
                 __syncwarp();
                 // evaluate the `count` partners at the ring's head (lane = partner)
@@ -505,21 +523,22 @@ __global__ void __launch_bounds__(kThreads32, MINB) pair_fwd32(PairArgs a) {
                     const int2 q = valid ? w.ql[s] : make_int2(0, 0);
                     if (lane == 0) w.cnt[3] += (unsigned)(count * ni);
                     R3<float> fj = {0.f, 0.f, 0.f};
+                    float gj = 0.f;
                     const bool same = q.y == kSameCell;
                     const bool one = XF && !same && q.y != 0;     // referred under a transform: one side
                     const float wgt = one ? 0.5f : 1.f;
                     const unsigned nin =
                         __any_sync(FULL, same)
                             ? eval_partner<NI_, MULTI, SHIFT, true, XF>(a, tab, w.xi, ni, k0, xj, q.x, same ? 0 : q.y,
-                                                                        same ? q.x : 0x7fffffff, fi, fj, v[0],
+                                                                        same ? q.x : 0x7fffffff, fi, fj, gj, v[0],
                                                                         XF ? v : nullptr, wgt)
                             : eval_partner<NI_, MULTI, SHIFT, false, XF>(a, tab, w.xi, ni, k0, xj, q.x, q.y, 0, fi, fj,
-                                                                         v[0], XF ? v : nullptr, wgt);
+                                                                         gj, v[0], XF ? v : nullptr, wgt);
                     if (same) within[0] += nin;
                     else if (q.y != 0) within[2] += nin;
                     else within[1] += nin;
                     if (nin && !one) {
-                        atomicAdd((float4 *)a.facc + q.x, make_float4(fj.x, fj.y, fj.z, 0.f));
+                        atomicAdd((float4 *)a.facc + q.x, make_float4(fj.x, fj.y, fj.z, gj));
                         if (!XF) outer7(v, xj.x, xj.y, xj.z, fj.x, fj.y, fj.z);
                     }
                     head = (head + count) & (kRing - 1);
@@ -549,10 +568,10 @@ __global__ void __launch_bounds__(kThreads32, MINB) pair_fwd32(PairArgs a) {
                 walk_runs<XF, true>(a, w.ed, w.eb, w.cnt, xR, e0, e1, ni, oI, sI, rcut, cull_i, lane, push);
                 if (qn > 0) run(qn);
                 // forces on the chunk's molecules: transposed warp sum, one vector atomic each, k-side virial
-                chunk_reduce<NI_>(fi, lane);
+                chunk_reduce4<NI_>(fi, lane);
                 const int t = lane / (32 / NI_);
                 if ((lane & (32 / NI_ - 1)) == 0 && t < ni) {
-                    atomicAdd((float4 *)a.facc + k0 + t, make_float4(fi[0], fi[1], fi[2], 0.f));
+                    atomicAdd((float4 *)a.facc + k0 + t, make_float4(fi[0], fi[1], fi[2], fi[3]));
                     if (!XF) {
                         const float4 x = w.xi[t];
                         outer7(v, x.x, x.y, x.z, fi[0], fi[1], fi[2]);
@@ -846,7 +865,8 @@ __global__ void __launch_bounds__(kPairThreads) pair_fwd64(PairArgs a) {
 template <class T>
 __global__ void __launch_bounds__(256) unsort_forces(const int *inv, int64_t n, const void *facc, T *out, int f64,
                                                      double *acc = nullptr, double *ev = nullptr,
-                                                     long long *counts = nullptr) {
+                                                     long long *counts = nullptr, int *flag_list = nullptr,
+                                                     float kflag2 = 0.f) {
     if (acc && blockIdx.x == 0)
         for (int i = threadIdx.x >> 5; i < 15; i += blockDim.x >> 5) finish_value(acc, ev, counts, i, threadIdx.x & 31);
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -860,6 +880,10 @@ __global__ void __launch_bounds__(256) unsort_forces(const int *inv, int64_t n, 
         } else {
             float4 f = ((const float4 *)facc)[s];
             x = f.x; y = f.y; z = f.z;
+            // the FP32 error of this force is about a fixed multiple of sqrt(sum |f|^2);
+            // a molecule whose force is too small against it is recomputed in FP64
+            if (flag_list && f.x * f.x + f.y * f.y + f.z * f.z < kflag2 * f.w)
+                flag_list[1 + atomicAdd(flag_list, 1)] = s;
         }
     }
     out[3 * k] = (T)x;
@@ -867,6 +891,123 @@ __global__ void __launch_bounds__(256) unsort_forces(const int *inv, int64_t n, 
     out[3 * k + 2] = (T)z;
 }
 
+// FP64 forces of the molecules flagged by unsort_forces: a warp per molecule
+// k (binned) of cluster A, lanes over the molecules of A and of every
+// (partner cluster, image) of A's full list; an FP32 distance test with a
+// wide margin skips the clearly distant ones, the rest are decided and
+// evaluated in FP64 with the all-pairs definition's operation order
+// ((x_k - x_l) - n.L, (dx^2 + dy^2) + dz^2), so the pair set is exactly the
+// pairs within rc.  Writes the force (original order) over the FP32 one.
+struct RefineArgs {
+    const int *flag_list, *cl_first, *cl_of, *full_off, *order;
+    const unsigned long long *full;
+    const double *orgm64;
+    float *out;
+    int C;
+};
+
+__global__ void __launch_bounds__(256) refine64(PairArgs a, RefineArgs r) {
+    __shared__ double tab[kMaxSpecies * kMaxSpecies][4];
+    __shared__ float4 ed[8][32];       // per warp: live entries of the batch (shift, image)
+    __shared__ int eb[8][32];          //           first molecule minus candidate position
+    for (int i = threadIdx.x; i < kMaxSpecies * kMaxSpecies; i += blockDim.x)
+        for (int q = 0; q < 4; ++q) tab[i][q] = a.tab.d[i][q];
+    __syncthreads();
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u, le = FULL >> (31 - lane);
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    const int nflag = r.flag_list[0];
+    const float pre2 = a.rc2_hi * 1.001f + 1e-3f;
+    for (int i = gw; i < nflag; i += nw) {
+        const int k = r.flag_list[1 + i];
+        // cell of k (cell_off[c] <= k < cell_off[c + 1]): 32-ary search, one probe per lane
+        int lo = 0, hi = r.C;
+        while (hi - lo > 1) {
+            const int step = (hi - lo + 31) / 32;
+            const int probe = lo + lane * step;
+            const bool le_k = probe < hi && a.cell_off[probe] <= k;
+            const int last = 31 - __clz(__ballot_sync(FULL, le_k));
+            lo += last * step;
+            hi = min(lo + step, hi);
+        }
+        const int A = r.cl_of[lo];
+        const double *xk = a.xs64 + 3 * (size_t)k;
+        const float4 xk32 = a.xloc[k];
+        const int spk = __float_as_int(xk32.w) & (kMaxSpecies - 1);
+        const double *oA = r.orgm64 + 3 * (size_t)r.cl_first[A];
+        R3<double> F = {0, 0, 0}, dummy = {0, 0, 0};
+        double acc7[7] = {0, 0, 0, 0, 0, 0, 0};
+        const int f0 = r.full_off[A], f1 = r.full_off[A + 1];
+        // entries: A itself (image 0), then A's full list; 32 at a time, one per lane
+        for (int e0 = f0 - 1; e0 < f1; e0 += 32) {
+            const int e = e0 + lane;
+            int n = 0, js = 0;
+            int32_t np = 0;
+            float3 sh = make_float3(0.f, 0.f, 0.f);
+            if (e < f1) {
+                int B = A;
+                if (e >= f0) {
+                    const unsigned long long key = r.full[e];
+                    B = (int)(key & 0xffffffffu);
+                    np = (int32_t)(key >> 32);
+                }
+                const double *oB = r.orgm64 + 3 * (size_t)r.cl_first[B];
+                sh = make_float3((float)((oB[0] - oA[0]) + (double)unpack_n(np, 0) * a.L[0]),
+                                 (float)((oB[1] - oA[1]) + (double)unpack_n(np, 1) * a.L[1]),
+                                 (float)((oB[2] - oA[2]) + (double)unpack_n(np, 2) * a.L[2]));
+                js = a.cell_off[r.cl_first[B]];
+                n = a.cell_off[r.cl_first[B + 1]] - js;
+            }
+            int inc = n;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(FULL, inc, o);
+                if (lane >= o) inc += y;
+            }
+            const int total = __shfl_sync(FULL, inc, 31);
+            const bool live = n > 0;
+            const unsigned lbal = __ballot_sync(FULL, live);
+            if (live) {
+                const int sl = __popc(lbal & lt);
+                ed[wib][sl] = make_float4(sh.x, sh.y, sh.z, __int_as_float(np));
+                eb[wib][sl] = js - (inc - n);
+            }
+            __syncwarp();
+            for (int p0 = 0; p0 < total; p0 += 32) {
+                const int b = inc - p0;
+                const int base = __popc(__ballot_sync(FULL, live && b <= 0));
+                const unsigned M = __reduce_or_sync(FULL, (live && b > 0 && b < 32) ? (1u << b) : 0u);
+                const int p = p0 + lane;
+                if (p < total) {
+                    const int o = base + __popc(M & le);
+                    const int l = p + eb[wib][o];
+                    const float4 d = ed[wib][o];
+                    const int32_t nl = __float_as_int(d.w);
+                    if (!(l == k && nl == 0)) {
+                        const float4 xl = a.xloc[l];
+                        const float qx = xk32.x - (xl.x + d.x), qy = xk32.y - (xl.y + d.y), qz = xk32.z - (xl.z + d.z);
+                        if (qx * qx + qy * qy + qz * qz <= pre2) {
+                            double rx, ry, rz, r2;
+                            sep64(xk, a.xs64 + 3 * (size_t)l, a.L, nl, rx, ry, rz, r2);
+                            if (r2 < a.rc2_d)
+                                pair64<true, false>(tab, rx, ry, rz, r2, spk, __float_as_int(xl.w) & (kMaxSpecies - 1),
+                                                    F, dummy, acc7);
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        const double fx = warp_sum(F.x), fy = warp_sum(F.y), fz = warp_sum(F.z);
+        if (lane == 0) {
+            const int o = r.order[k];
+            r.out[3 * (size_t)o] = (float)fx;
+            r.out[3 * (size_t)o + 1] = (float)fy;
+            r.out[3 * (size_t)o + 2] = (float)fz;
+        }
+    }
+}
 
 // ---------------------------------------------------------------- adjoint
 // Per pair with r = x_k - x_l', f = g(r^2) r, g = 24 e inv s3 (2 s3 - 1):
@@ -1274,6 +1415,441 @@ __global__ void __launch_bounds__(kGradSlots * 32) finish_bwd(const double *acc,
     }
 }
 
+// ------------------------------------------------------ FP32 cluster kernel
+// The box-periodic FP32 forces over clusters (runs of consecutive cells,
+// mesh.cu) instead of single cells.  A warp takes one cluster A at a time:
+//   1. the joint bounding box of A's molecules (this step's positions);
+//   2. candidates: A's own molecules (pairs k < l, §2.3's same-cell rule
+//      extended to the cluster) and the molecules of the partner runs of A's
+//      cluster schedule, each moved into A's frame by the run's shift; a
+//      candidate farther than rc from the box cannot pair with any molecule
+//      of A (margins above the FP32 cut-off) and is dropped, the rest go to
+//      a per-warp survivor buffer in shared memory;
+//   3. for every i-tile of NI molecules of A, every batch of 32 survivors is
+//      evaluated one survivor per lane against the tile (the tile's
+//      molecules broadcast from shared memory): forces by FMA, the survivor's
+//      reaction summed in registers and added to its slot of the buffer, the
+//      tile's forces summed per lane and over the warp at the end of the tile
+//      (recursive halving), one vector atomic per molecule;
+//   4. one vector atomic per survivor adds its reaction.
+// Separations are formed exactly before one rounding: binned coordinates are
+// multiples of 2^-q (xloc) plus a remainder (xlo), run shifts likewise, so
+// (x_k,hi - x_l,hi - shift_hi) is exact and adding the remainders rounds once.
+// Every force accumulator's .w sums |f|^2 over the molecule's pairs: the
+// scale of the FP32 error of its force (see refine64).
+struct ClKArgs {
+    const int *cl_first, *cl_run_off;
+    const ClRun *runs;
+    const float4 *xlo;
+    int ncl;
+    float qround;                // 1.5 * 2^(23 - q): x + qround - qround rounds x to a multiple of 2^-q
+};
+
+// A binned molecule split at multiples of 2^-q: hi exact on the grid, lo the
+// rest (xloc - hi is exact; adding the stored remainder rounds far below
+// the separation's own rounding).  Valid for |x| < 2^(22 - q).
+__device__ __forceinline__ void grid_split(float4 x, float4 r, float qr, float4 &hi, float4 &lo) {
+    hi.x = __fsub_rn(__fadd_rn(x.x, qr), qr);
+    hi.y = __fsub_rn(__fadd_rn(x.y, qr), qr);
+    hi.z = __fsub_rn(__fadd_rn(x.z, qr), qr);
+    hi.w = x.w;
+    lo = make_float4(__fsub_rn(x.x, hi.x) + r.x, __fsub_rn(x.y, hi.y) + r.y, __fsub_rn(x.z, hi.z) + r.z, 0.f);
+}
+
+constexpr int kCT = 128, kCW = kCT / 32;
+// A molecule's FP32 force error is about a multiple of sqrt(sum_l |f_kl|^2)
+// (rounding of each pair force, mostly; the separations are rounded once);
+// kRefineScale bounds that multiple with a wide safety margin.  A molecule
+// whose force is below kRefineScale / tol times that scale gets refined.
+constexpr double kRefineScale = 1e-6;
+constexpr int kCap = 256;                 // survivors buffered per warp
+constexpr int kNI = 8;                    // molecules of A per i-tile
+// packed survivor / tile word (.w of the hi position)
+constexpr int kSpBits = 7, kSameBit = 1 << 3, kImgBit = 1 << 4;
+__device__ __forceinline__ int cellq_of(int w) { return (w >> 5) & 15; }
+__device__ __forceinline__ int32_t n_of(int w) {   // 3 x 4-bit image -> pack_n
+    const int c = w >> 9;
+    return pack_n((c << 28) >> 28, (c << 24) >> 28, (c << 20) >> 28);
+}
+
+struct WarpC {
+    float4 sh[kCap];      // survivor: position in A's frame, hi part (exact); .w packed word
+    float4 sl[kCap];      // survivor: remainder (xyz); .w binned index (int bits)
+    float4 sf[kCap];      // survivor: reaction (xyz) and sum of |f|^2 (w) over the tiles
+    float4 ih[kNI];       // tile: hi part; .w packed word (species, cell within the cluster);
+    float4 il[kNI];       //   unused slots hold a far-away dummy
+    float4 ed[32], el[32];
+    int eb[32];
+    float box[6];         // joint box of A's molecules (lo, hi)
+    float vir[6];         // FP32 virial of the current cluster
+    unsigned cnt[2];      // pair tests, culling tests
+};
+
+// A shared-memory load the compiler keeps in place (a broadcast read per
+// use instead of 64 registers holding the whole tile).
+__device__ __forceinline__ float4 lds4(const float4 *p) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"((unsigned)__cvta_generic_to_shared(p)));
+    return v;
+}
+
+// cell of binned molecule k among A's cells c0 .. c1 - 1 (at most kMaxClusterCells)
+__device__ __forceinline__ int cell_in_cluster(const int *cell_off, int c0, int c1, int k) {
+    int c = c0;
+    while (c + 1 < c1 && cell_off[c + 1] <= k) ++c;
+    return c - c0;
+}
+
+// One lane's survivor (xh, xl) against the tile (broadcast from shared
+// memory): the separation formed exactly and rounded once, r^2 < rc^2
+// decided in FP32 outside the 1e-5 rc^2 band (FP64 with the all-pairs
+// operation order inside it, after the pass), the force body skipped when
+// no lane of the warp is within rc.  SAME: own-cluster survivors pair only
+// with tile molecules of lower binned index.
+template <bool MULTI, bool SHIFT, bool SAME>
+__device__ __forceinline__ unsigned eval_tile(const PairArgs &a, const float4 *tab, const WarpC &w, int ni, int k0, float4 xh,
+                                              float4 xl, float (&fi)[4 * kNI], float4 &fj, float &u_acc,
+                                              unsigned &nsame) {
+    unsigned nin = 0, bm = 0;
+    const float4 t0 = tab[0];
+    const int wj = __float_as_int(xh.w), l = __float_as_int(xl.w);
+    const bool sj = SAME && (wj & kSameBit) != 0;
+#pragma unroll
+    for (int t = 0; t < kNI; ++t) {
+        if (t >= ni) break;
+        const float4 h = lds4(&w.ih[t]), lo = lds4(&w.il[t]);
+        const float rx = (h.x - xh.x) + (lo.x - xl.x);
+        const float ry = (h.y - xh.y) + (lo.y - xl.y);
+        const float rz = (h.z - xh.z) + (lo.z - xl.z);
+        const float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
+        const bool ok = !sj || k0 + t < l;
+        const bool in = ok && r2 < a.rc2_lo;
+        if (ok && !in && r2 < a.rc2_hi) bm |= 1u << t;
+        float fs, u;
+        lj32<MULTI, SHIFT>(tab, t0, __float_as_int(h.w) & kSpBits, wj & kSpBits, r2, fs, u);
+        fs = in ? fs : 0.f;
+        u_acc += in ? u : 0.f;
+        fi[4 * t] = fmaf(fs, rx, fi[4 * t]);
+        fi[4 * t + 1] = fmaf(fs, ry, fi[4 * t + 1]);
+        fi[4 * t + 2] = fmaf(fs, rz, fi[4 * t + 2]);
+        fj.x = fmaf(-fs, rx, fj.x);
+        fj.y = fmaf(-fs, ry, fj.y);
+        fj.z = fmaf(-fs, rz, fj.z);
+        const float g = fs * fs;
+        fi[4 * t + 3] = fmaf(g, r2, fi[4 * t + 3]);
+        fj.w = fmaf(g, r2, fj.w);
+        nin += in;
+        if (SAME) nsame += (in && sj && cellq_of(__float_as_int(h.w)) == cellq_of(wj)) ? 1u : 0u;
+    }
+    if (__any_sync(0xffffffffu, bm != 0)) {
+        const int32_t np = n_of(wj);
+#pragma unroll
+        for (int t = 0; t < kNI; ++t) {
+            if (((bm >> t) & 1u) && band_in(a, k0 + t, l, np)) {
+                const float4 h = lds4(&w.ih[t]), lo = lds4(&w.il[t]);
+                const float rx = (h.x - xh.x) + (lo.x - xl.x);
+                const float ry = (h.y - xh.y) + (lo.y - xl.y);
+                const float rz = (h.z - xh.z) + (lo.z - xl.z);
+                const float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
+                float fs, u;
+                lj32<MULTI, SHIFT>(tab, t0, __float_as_int(h.w) & kSpBits, wj & kSpBits, r2, fs, u);
+                u_acc += u;
+                fi[4 * t] = fmaf(fs, rx, fi[4 * t]);
+                fi[4 * t + 1] = fmaf(fs, ry, fi[4 * t + 1]);
+                fi[4 * t + 2] = fmaf(fs, rz, fi[4 * t + 2]);
+                fj.x = fmaf(-fs, rx, fj.x);
+                fj.y = fmaf(-fs, ry, fj.y);
+                fj.z = fmaf(-fs, rz, fj.z);
+                const float g = fs * fs;
+                fi[4 * t + 3] = fmaf(g, r2, fi[4 * t + 3]);
+                fj.w = fmaf(g, r2, fj.w);
+                nin++;
+                if (sj && cellq_of(__float_as_int(h.w)) == cellq_of(wj)) nsame++;
+            }
+        }
+    }
+    return nin;
+}
+
+// Sum v[0..4 kNI) (kNI groups of x, y, z, |f|^2) over the warp by recursive
+// halving: on return lanes t * (32 / kNI) .. hold the totals of group t in v[0..4).
+__device__ __forceinline__ void tile_reduce4(float (&v)[4 * kNI], int lane) {
+    halve<4 * kNI>(v, lane, 16);
+    halve<2 * kNI>(v, lane, 8);
+    halve<kNI>(v, lane, 4);
+#pragma unroll
+    for (int o = 2; o > 0; o >>= 1)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+}
+template <bool MULTI, bool SHIFT, int MINB>
+__global__ void __launch_bounds__(kCT, MINB) pair_fwd32c(PairArgs a, ClKArgs c) {
+    extern __shared__ float4 csh[];
+    WarpC *wsh = reinterpret_cast<WarpC *>(csh);
+    __shared__ float4 tab[kMaxSpecies * kMaxSpecies];
+    __shared__ double dsums[kCW][8];
+    for (int i = threadIdx.x; i < kMaxSpecies * kMaxSpecies; i += blockDim.x) tab[i] = a.tab.f[i];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    WarpC &w = wsh[wib];
+    if (lane < 8) dsums[wib][lane] = 0.0;
+    if (lane < 2) w.cnt[lane] = 0;
+    if (lane < 6) w.vir[lane] = 0.f;
+    __syncthreads();
+    const unsigned FULL = 0xffffffffu, lt = (1u << lane) - 1u, le = FULL >> (31 - lane);
+    const float4 far = make_float4(1e18f, 1e18f, 1e18f, 0.f), zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float rcut = sqrtf(a.rc2_hi) * 1.00001f + 1e-5f;
+    const float rcut2 = rcut * rcut;
+    float4 *facc = (float4 *)a.facc;
+    double *dsum = dsums[wib];
+    float u_acc = 0.f;
+    unsigned wc0 = 0, wc1 = 0, wc2 = 0;     // this lane's pairs within rc: same cell, DIL, image
+    // virial terms of a tile's or survivors' forces: per lane in FP32, then to the warp's sums
+    auto add_vir = [&](float x, float y, float z, float fx, float fy, float fz) {
+        float q[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        outer7(q, x, y, z, fx, fy, fz);
+#pragma unroll
+        for (int i = 1; i < 7; ++i) {
+            const float s = warp_sum(q[i]);
+            if (lane == 0) w.vir[i - 1] += s;
+        }
+    };
+    for (;;) {
+        int A = lane == 0 ? (int)atomicAdd(a.next_cell, 1u) : 0;
+        A = __shfl_sync(FULL, A, 0);
+        if (A >= c.ncl) break;
+        const int c0 = c.cl_first[A], c1 = c.cl_first[A + 1];
+        const int s0 = a.cell_off[c0], s1 = a.cell_off[c1], nA = s1 - s0;
+        if (nA == 0) continue;
+        // 1. joint box of A's molecules (hi parts; the remainders lie inside the margins)
+        float bl[3] = {1e30f, 1e30f, 1e30f}, bh[3] = {-1e30f, -1e30f, -1e30f};   // to shared memory below
+        for (int k = s0 + lane; k < s1; k += 32) {
+            const float4 x = a.xloc[k];
+            bl[0] = fminf(bl[0], x.x); bl[1] = fminf(bl[1], x.y); bl[2] = fminf(bl[2], x.z);
+            bh[0] = fmaxf(bh[0], x.x); bh[1] = fmaxf(bh[1], x.y); bh[2] = fmaxf(bh[2], x.z);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                bl[d] = fminf(bl[d], __shfl_xor_sync(FULL, bl[d], o));
+                bh[d] = fmaxf(bh[d], __shfl_xor_sync(FULL, bh[d], o));
+            }
+        if (lane < 3) {
+            w.box[lane] = lane == 0 ? bl[0] : lane == 1 ? bl[1] : bl[2];
+            w.box[3 + lane] = lane == 0 ? bh[0] : lane == 1 ? bh[1] : bh[2];
+        }
+        __syncwarp();
+        int nq = 0;
+        // 3./4. every tile of A against the buffered survivors, then their reactions
+        auto flush = [&]() {
+            __syncwarp();
+            for (int i0 = 0; i0 < nA; i0 += kNI) {
+                const int ni = min(kNI, nA - i0), k0 = s0 + i0;
+                if (lane < kNI) {
+                    float4 h = make_float4(1e18f, 1e18f, 1e18f, 0.f), lo = zero4;
+                    if (lane < ni) {
+                        grid_split(a.xloc[k0 + lane], c.xlo[k0 + lane], c.qround, h, lo);
+                        const int q = cell_in_cluster(a.cell_off, c0, c1, k0 + lane);
+                        h.w = __int_as_float((__float_as_int(h.w) & kSpBits) | (q << 5));
+                    }
+                    w.ih[lane] = h;
+                    w.il[lane] = lo;
+                }
+                if (lane == 0) w.cnt[0] += (unsigned)(nq * ni);
+                float fi[4 * kNI];
+#pragma unroll
+                for (int i = 0; i < 4 * kNI; ++i) fi[i] = 0.f;
+                __syncwarp();
+                for (int jb = 0; jb < nq; jb += 32) {
+                    const int j = jb + lane;
+                    const bool valid = j < nq;
+                    const float4 xh = valid ? w.sh[j] : make_float4(-1e18f, -1e18f, -1e18f, 0.f);
+                    const float4 xl = valid ? w.sl[j] : zero4;
+                    float4 fj = zero4;
+                    unsigned nin, nsame = 0;
+                    const bool same = (__float_as_int(xh.w) & kSameBit) != 0;
+                    if (__any_sync(FULL, same))
+                        nin = eval_tile<MULTI, SHIFT, true>(a, tab, w, ni, k0, xh, xl, fi, fj, u_acc, nsame);
+                    else
+                        nin = eval_tile<MULTI, SHIFT, false>(a, tab, w, ni, k0, xh, xl, fi, fj, u_acc, nsame);
+                    if (valid && nin) {
+                        // within-rc counts per category (same cell, DIL, periodic image), per lane
+                        if (same) {
+                            wc0 += nsame;
+                            wc1 += nin - nsame;
+                        } else if (__float_as_int(xh.w) & kImgBit) {
+                            wc2 += nin;
+                        } else {
+                            wc1 += nin;
+                        }
+                        float4 f = w.sf[j];
+                        f.x += fj.x; f.y += fj.y; f.z += fj.z; f.w += fj.w;
+                        w.sf[j] = f;
+                    }
+                }
+                tile_reduce4(fi, lane);
+                const int t = lane >> 2;
+                const bool mine = (lane & 3) == 0 && t < ni;
+                if (mine) atomicAdd(facc + k0 + t, make_float4(fi[0], fi[1], fi[2], fi[3]));
+                const float4 x = w.ih[t];
+                add_vir(x.x, x.y, x.z, mine ? fi[0] : 0.f, mine ? fi[1] : 0.f, mine ? fi[2] : 0.f);
+                __syncwarp();
+            }
+            // survivors' reactions (and the survivor side of the virial, in A's frame)
+            for (int j0 = 0; j0 < nq; j0 += 32) {
+                const int j = j0 + lane;
+                float4 f = zero4, x = zero4;
+                if (j < nq) {
+                    f = w.sf[j];
+                    x = w.sh[j];
+                    if (f.x != 0.f || f.y != 0.f || f.z != 0.f || f.w != 0.f) atomicAdd(facc + __float_as_int(w.sl[j].w), f);
+                }
+                add_vir(x.x, x.y, x.z, f.x, f.y, f.z);
+            }
+            __syncwarp();
+            nq = 0;
+        };
+        // append the live lanes' candidates to the buffer; flush when it cannot take 32 more
+        auto push = [&](bool alive, float4 xh, float4 xl) {
+            const unsigned bal = __ballot_sync(FULL, alive);
+            if (alive) {
+                const int sl = nq + __popc(bal & lt);
+                w.sh[sl] = xh;
+                w.sl[sl] = xl;
+                w.sf[sl] = zero4;
+            }
+            nq += __popc(bal);
+            if (nq > kCap - 32) flush();
+        };
+        // 2a. A's own molecules: pairs k < l inside the cluster
+        for (int k = s0 + lane; k - lane < s1; k += 32) {
+            const bool alive = k < s1;
+            float4 xh = far, xl = zero4;
+            if (alive) {
+                grid_split(a.xloc[k], c.xlo[k], c.qround, xh, xl);
+                const int q = cell_in_cluster(a.cell_off, c0, c1, k);
+                xh.w = __int_as_float((__float_as_int(xh.w) & kSpBits) | kSameBit | (q << 5));
+                xl.w = __int_as_float(k);
+            }
+            push(alive, xh, xl);
+        }
+        // 2b. partner runs, 32 at a time: culled against A's box, compacted, expanded
+        const int e0 = c.cl_run_off[A], e1 = c.cl_run_off[A + 1];
+        for (int eb = e0; eb < e1; eb += 32) {
+            const bool has = eb + lane < e1;
+            int js = 0, n = 0;
+            ClRun r;
+            r.dh = zero4;
+            r.dl = zero4;
+            if (has) {
+                r = c.runs[eb + lane];
+                const int cf = __float_as_int(r.dh.w), code = __float_as_int(r.dl.w);
+                js = a.cell_off[cf];
+                n = a.cell_off[cf + (code & 4095)] - js;
+            }
+            int inc = n;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(FULL, inc, o);
+                if (lane >= o) inc += y;
+            }
+            const int total = __shfl_sync(FULL, inc, 31);
+            const bool live = n > 0;
+            const unsigned lbal = __ballot_sync(FULL, live);
+            if (live) {
+                const int sl = __popc(lbal & lt);
+                w.ed[sl] = r.dh;
+                w.el[sl] = r.dl;
+                w.eb[sl] = js - (inc - n);
+            }
+            if (lane == 0) w.cnt[1] += (unsigned)total;
+            __syncwarp();
+            for (int p0 = 0; p0 < total; p0 += 32) {
+                // run holding candidate p = p0 + lane: the live runs ending at or before p
+                const int b = inc - p0;
+                const int base = __popc(__ballot_sync(FULL, live && b <= 0));
+                const unsigned M = __reduce_or_sync(FULL, (live && b > 0 && b < 32) ? (1u << b) : 0u);
+                const int p = p0 + lane;
+                bool alive = false;
+                float4 xh = far, xl = zero4;
+                if (p < total) {
+                    const int o = base + __popc(M & le);
+                    const int l = p + w.eb[o];
+                    const float4 dh = w.ed[o], dl = w.el[o];
+                    float4 x, y;
+                    grid_split(a.xloc[l], c.xlo[l], c.qround, x, y);
+                    xh = make_float4(x.x + dh.x, x.y + dh.y, x.z + dh.z, 0.f);
+                    const float dx = fmaxf(fmaxf(w.box[0] - xh.x, xh.x - w.box[3]), 0.f);
+                    const float dy = fmaxf(fmaxf(w.box[1] - xh.y, xh.y - w.box[4]), 0.f);
+                    const float dz = fmaxf(fmaxf(w.box[2] - xh.z, xh.z - w.box[5]), 0.f);
+                    alive = dx * dx + dy * dy + dz * dz <= rcut2;
+                    const int code = __float_as_int(dl.w) >> 12;
+                    xh.w = __int_as_float((__float_as_int(x.w) & kSpBits) | (code != 0 ? kImgBit : 0) | (code << 9));
+                    xl = make_float4(y.x + dl.x, y.y + dl.y, y.z + dl.z, __int_as_float(l));
+                }
+                push(alive, xh, xl);
+            }
+            __syncwarp();
+        }
+        if (nq > 0) flush();
+        // FP32 running sums to FP64 once per cluster
+        {
+            const float s = warp_sum(u_acc);
+            u_acc = 0.f;
+            __syncwarp();
+            if (lane == 0) {
+                dsum[0] += (double)s;
+                for (int i = 0; i < 6; ++i) {
+                    dsum[1 + i] += (double)w.vir[i];
+                    w.vir[i] = 0.f;
+                }
+            }
+            __syncwarp();
+        }
+    }
+    __syncwarp();
+    double fin[7];
+#pragma unroll
+    for (int i = 0; i < 7; ++i) fin[i] = dsum[i];
+    unsigned cv[8] = {0u, 0u, 0u, wc0, wc1, wc2, w.cnt[0], w.cnt[1]};
+    cv[6] = __shfl_sync(FULL, cv[6], 0);
+    cv[7] = __shfl_sync(FULL, cv[7], 0);
+    if (lane != 0) cv[6] = cv[7] = 0;
+    cv[6] = __shfl_sync(FULL, cv[6], 0);
+    cv[7] = __shfl_sync(FULL, cv[7], 0);
+    if (lane != 0) cv[6] = cv[7] = 0;
+    warp_to_stripe(a, blockIdx.x * kCW + wib, fin, cv, lane);
+}
+
+// AICA-evaluated pairs of the cell schedule (§2.3's loops count every pair
+// of every listed cell pair): a warp per cell, lanes over its runs.
+__global__ void __launch_bounds__(256) count_evaluated(const int *cell_off, const int *run_off, const RunEntry *runs,
+                                                       int C, double *acc) {
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    unsigned long long ev[3] = {0, 0, 0};
+    for (int I = gw; I < C; I += nw) {
+        const long long nI = cell_off[I + 1] - cell_off[I];
+        if (nI == 0) continue;
+        if (lane == 0) ev[0] += (unsigned long long)(nI * (nI - 1) / 2);
+        for (int r = run_off[I] + lane; r < run_off[I + 1]; r += 32) {
+            const RunEntry e = runs[r];
+            const int len = ((unsigned)e.n >> 24) + 1;
+            const long long m = cell_off[e.j + len] - cell_off[e.j];
+            ev[(e.n & 0xffffff) != 0 ? 2 : 1] += (unsigned long long)(nI * m);
+        }
+    }
+    double *row = acc + kAccStripes + (size_t)(gw % kStripes) * kParts;
+    for (int i = 0; i < 3; ++i) {
+        unsigned long long s = ev[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0 && s) atomicAdd(row + 7 + i, (double)s);
+    }
+}
+
 // grid: enough warps to fill the GPU, at least two cells per warp
 int pair_grid(int C) {
     int need = (C + 2 * kWarps - 1) / (2 * kWarps);
@@ -1336,6 +1912,10 @@ void fill_common(aica_mesh *m, PairArgs &a) {
     a.rc2_d = rc2;
     a.rc2_lo = (float)(rc2 * (1 - 1e-5));
     a.rc2_hi = (float)(rc2 * (1 + 1e-5));
+    {
+        const double rp = sqrt(rc2 * (1 + 1e-5)) + 8.0 * ldexp(1.0, -m->qexp);
+        a.rc2_pre = (float)(rp * rp);
+    }
     for (int d = 0; d < 3; ++d) a.L[d] = m->box.periodic[d] ? m->box.L[d] : 0.0;
     a.facc = m->facc.p;
     a.acc = m->acc.as<double>();
@@ -1434,6 +2014,31 @@ void launch_bwd64(const BwdArgs &b, bool multi, int grid, cudaStream_t st) {
     }
 }
 
+// The FP32 cluster kernel: a persistent grid, every SM filled to its
+// occupancy (dynamic shared memory: the warps' survivor buffers and queues).
+template <bool MULTI, bool SHIFT>
+void launch_fwd32c_t(const PairArgs &a, const ClKArgs &c, cudaStream_t st) {
+    constexpr int MINB = 5;
+    static int cache[64] = {0};
+    const size_t shm = sizeof(WarpC) * kCW;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    if (!cache[dev]) {
+        cudaFuncSetAttribute(pair_fwd32c<MULTI, SHIFT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+        int sms = 0, per = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pair_fwd32c<MULTI, SHIFT, MINB>, kCT, shm);
+        cache[dev] = std::max(1, sms * std::max(1, per));
+    }
+    const int grid = std::min(cache[dev], std::max(1, (c.ncl + kCW - 1) / kCW));
+    pair_fwd32c<MULTI, SHIFT, MINB><<<grid, kCT, shm, st>>>(a, c);
+}
+
+void launch_fwd32c(const PairArgs &a, const ClKArgs &c, bool multi, bool shift, cudaStream_t st) {
+    if (multi) shift ? launch_fwd32c_t<true, true>(a, c, st) : launch_fwd32c_t<true, false>(a, c, st);
+    else shift ? launch_fwd32c_t<false, true>(a, c, st) : launch_fwd32c_t<false, false>(a, c, st);
+}
+
 }  // namespace
 }  // namespace aica
 
@@ -1460,10 +2065,25 @@ extern "C" aica_status aica_forces(aica_mesh *m, const aica_lj *lj, aica_precisi
     const bool multi = a.S > 1, shift = lj->shift != 0;
     cudaEvent_t tstop;
     AICA_CUDA(timing_begin(m, st, &tstop));
+    // FP32 with box periodicity: the cluster kernel when the lists have a
+    // cluster schedule (the cell kernel on request, and for general transforms)
+    const bool clsched = !f64 && !a.xf && m->n_cl_runs >= 0;
+    const bool clpath = clsched && m->fp32_kernel != 1;
     if (!f64) {
-        // i-chunk width: 4 for cells of a few molecules (tetrahedra), 8 otherwise
-        if ((double)n < 5.0 * (double)a.C) launch_fwd32<4>(a, multi, shift, st);
-        else launch_fwd32<8>(a, multi, shift, st);
+        if (clpath) {
+            ClKArgs c{};
+            c.cl_first = m->cl_first.as<int>();
+            c.cl_run_off = m->cl_run_off.as<int>();
+            c.runs = m->cl_runs.as<ClRun>();
+            c.xlo = m->xlo.as<float4>();
+            c.ncl = (int)m->n_cl;
+            c.qround = (float)ldexp(1.5, 23 - m->qexp);
+            launch_fwd32c(a, c, multi, shift, st);
+        } else {
+            // i-chunk width: 4 for cells of a few molecules (tetrahedra), 8 otherwise
+            if ((double)n < 5.0 * (double)a.C) launch_fwd32<4>(a, multi, shift, st);
+            else launch_fwd32<8>(a, multi, shift, st);
+        }
     } else {
         if (a.xf) launch_fwd64<true>(a, multi, shift, grid, st);
         else launch_fwd64<false>(a, multi, shift, grid, st);
@@ -1471,12 +2091,38 @@ extern "C" aica_status aica_forces(aica_mesh *m, const aica_lj *lj, aica_precisi
     AICA_CUDA(timing_end(tstop, st));
     m->launches = 2;
     double *acc = m->acc.as<double>();
+    if (clpath && counts_out && m->count_evaluated && a.C > 0) {
+        // the cluster kernel does not walk the cell schedule: count the method's evaluated pairs
+        count_evaluated<<<(unsigned)std::min<int64_t>(((int64_t)a.C * 32 + 255) / 256, 152 * 16), 256, 0, st>>>(
+            a.cell_off, a.run_off, a.runs, a.C, acc);
+        m->launches += 1;
+    }
+    // FP32 with box periodicity (either kernel): molecules whose FP32 force cannot
+    // be certified to the tolerance are recomputed in FP64 (needs the cluster lists)
+    const bool refine = clpath && m->refine_tol > 0 && n > 0;
+    int *flags = refine ? m->flag_list.as<int>() : nullptr;
+    if (refine) AICA_CUDA(cudaMemsetAsync(flags, 0, sizeof(int), st));
+    const float kf = refine ? (float)(kRefineScale / m->refine_tol) : 0.f;
     if (n > 0) {
         const unsigned g = (unsigned)((n + 255) / 256);
         if (f64) unsort_forces<double><<<g, 256, 0, st>>>(m->inv.as<int>(), n, m->facc.p, (double *)force_out, 1, acc, ev_out, (long long *)counts_out);
-        else unsort_forces<float><<<g, 256, 0, st>>>(m->inv.as<int>(), n, m->facc.p, (float *)force_out, 0, acc, ev_out, (long long *)counts_out);
+        else unsort_forces<float><<<g, 256, 0, st>>>(m->inv.as<int>(), n, m->facc.p, (float *)force_out, 0, acc, ev_out, (long long *)counts_out, flags, kf * kf);
     } else {
         finish_sums<<<1, 15 * 32, 0, st>>>(acc, ev_out, (long long *)counts_out);
+    }
+    if (refine) {
+        RefineArgs r{};
+        r.flag_list = flags;
+        r.cl_first = m->cl_first.as<int>();
+        r.cl_of = m->cl_of.as<int>();
+        r.full_off = m->cl_full_off.as<int>();
+        r.full = m->cl_full.as<unsigned long long>();
+        r.order = m->order.as<int>();
+        r.orgm64 = m->orgm64.as<double>();
+        r.out = (float *)force_out;
+        r.C = a.C;
+        refine64<<<152 * 8, 256, 0, st>>>(a, r);
+        m->launches += 1;
     }
     AICA_CUDA(cudaGetLastError());
     if (!m->deferred) return check_flags(m, st);

@@ -32,13 +32,35 @@ def oracle_all(cfg, lists=True):
     return out
 
 
-def assert_forces(F, ref, tol, idx=None):
-    """|F - F_ref| per component <= tol * sum_l |f_kl| (the scale of the sum)."""
+def force_errors(F, ref, idx=None):
+    """Per-component force errors against the oracle: the stated tolerance's
+    normalisation |dF_ic| / max(|F_ic|, ||F_i||_2), and |dF_ic| / sum_l |f_kl|
+    (the condition scale of the sum), as arrays [n, 3]."""
     Fr = ref["F"]
     F = F if idx is None else F[idx]
-    err = np.abs(F - Fr) / np.maximum(ref["Fabs"], 1e-300)[:, None]
-    assert err.max() <= tol, f"max force error {err.max():.3e} > {tol}"
-    return err.max()
+    d = np.abs(F - Fr)
+    norm = np.maximum(np.abs(Fr), np.linalg.norm(Fr, axis=1)[:, None])
+    return d / np.maximum(norm, 1e-300), d / np.maximum(ref["Fabs"], 1e-300)[:, None]
+
+
+def assert_forces(F, ref, tol, idx=None):
+    """|F - F_ref| per component <= tol * max(|F_ic|, ||F_i||) for every
+    molecule and component (the stated tolerance).  Returns the largest
+    error under both normalisations."""
+    e_norm, e_abs = force_errors(F, ref, idx)
+    bad = np.flatnonzero((e_norm > tol).any(axis=1))
+    assert len(bad) == 0, (f"{len(bad)} molecules beyond tol {tol}: max {e_norm.max():.3e} "
+                           f"(relative to sum |f|: {e_abs.max():.3e})")
+    return e_norm.max(), e_abs.max()
+
+
+def assert_forces_sum_abs(F, ref, tol, idx=None):
+    """|F - F_ref| per component <= tol * sum_l |f_kl|: for paths whose
+    forces the library does not certify to the stated tolerance (the cell
+    kernel under general referring transforms or the vertex criterion)."""
+    e_norm, e_abs = force_errors(F, ref, idx)
+    assert e_abs.max() <= tol, f"max force error {e_abs.max():.3e} of sum |f| > {tol}"
+    return e_abs.max()
 
 
 def compare_lists(g, o, cells=None):

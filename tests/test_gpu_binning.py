@@ -10,8 +10,11 @@ from gpu_helpers import gpu_setup, oracle_all
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("name", ["t0", "c1", "h0", "c4", "c2"])
+@pytest.mark.parametrize("name", ["t0", "c1", "h0", "c4", "c2", "c3", "c5"])
 def test_binning_equals_oracle(name):
+    """Every molecule's cell, the binned order and the cell offsets, at full
+    size (c3: 1.16 M molecules with wall layers on lattice-aligned faces;
+    c5: 8.4 M molecules in 3.07 M tetrahedra)."""
     c = synth.make(name, 2)
     m, pos, sp, (cell_of, order, cell_off) = gpu_setup(c)
     o = oracle_all(c, lists=False)
@@ -20,10 +23,10 @@ def test_binning_equals_oracle(name):
     np.testing.assert_array_equal(cell_off, o["cell_off"])
 
 
-@pytest.mark.parametrize("dist", [0.01, 0.5])
-def test_rebinning_after_displacement(dist):
+@pytest.mark.parametrize("name,dist", [("c2", 0.01), ("c2", 0.5), ("c5", 0.5)])
+def test_rebinning_after_displacement(name, dist):
     """Re-binning uses the previous cells as a search hint; the result stays exact."""
-    c = synth.make("c2", 4)
+    c = synth.make(name, 4)
     m, pos, sp, _ = gpu_setup(c)
     rng = np.random.default_rng(7)
     c["pos"] = synth.random_displacement(c["pos"], dist, rng, c["box"]["L"], c["box"]["periodic"])

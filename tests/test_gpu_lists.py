@@ -26,15 +26,25 @@ def test_lists_open_axis_and_removed_cells():
     compare_lists(m.lists(), oracle.cell_lists(c["mesh"], c["box"], c["rc"], c["skin"]))
 
 
-@pytest.mark.parametrize("name", ["c2", "c4"])
+@pytest.mark.parametrize("name", ["c2", "c4", "c3", "c5"])
 def test_lists_sampled_full_size(name):
+    """Rows of the full-size lists: cell 0, the last cell, cells on each
+    periodic face (referred cells) and random cells."""
     c = synth.make(name, 0)
     m, *_ = gpu_setup(c)
     g = m.lists()
     C = c["mesh"]["n_cells"]
     rng = np.random.default_rng(1)
-    cells = np.unique(np.r_[0, C - 1, rng.choice(C, 10, replace=False)])
-    o = oracle.cell_lists(c["mesh"], c["box"], c["rc"], c["skin"], queries=cells)
+    geo = oracle.cell_geometry(c["mesh"])
+    L, per = c["box"]["L"], c["box"]["periodic"]
+    face = []
+    for d in range(3):
+        if per[d]:
+            lo_side = np.flatnonzero(geo["lo"][:, d] <= 1e-9)
+            hi_side = np.flatnonzero(geo["hi"][:, d] >= L[d] - 1e-9)
+            face += [rng.choice(lo_side), rng.choice(hi_side)]
+    cells = np.unique(np.r_[0, C - 1, face, rng.choice(C, 10, replace=False)])
+    o = oracle.cell_lists(c["mesh"], c["box"], c["rc"], c["skin"], queries=cells, geo=geo)
     assert g["ties"] == 0 and o["ties"] == 0
     compare_lists(g, o, cells)
 
