@@ -168,6 +168,7 @@ struct aica_mesh {
     // partner list of every cluster for the FP64 refinement, one entry per
     // (partner cluster, image).
     aica::DevBuf cl_run_off, cl_runs, cl_full_off, cl_full;
+    aica::DevBuf cl_box;                     // [n_cl][2] float4: molecule box of each cluster (last FP32 call)
     int64_t n_cl_runs = -1, n_cl_full = 0;    // n_cl_runs < 0: no cluster schedule
     int qexp = 20;                           // cluster kernel: hi parts are multiples of 2^-qexp
     // General referring transforms (empty: box periodicity).  With them the

@@ -676,6 +676,7 @@ aica_status build_cluster_schedule(aica_mesh *m, cudaStream_t st) {
     }
     AICA_CUDA(m->cl_runs.reserve(sizeof(ClRun) * std::max(tot[0], 1)));
     AICA_CUDA(m->cl_full.reserve(sizeof(unsigned long long) * std::max(tot[1], 1)));
+    AICA_CUDA(m->cl_box.reserve(sizeof(float4) * 2 * (size_t)ncl));
     cl_cursor<<<(ncl + 255) / 256, 256, 0, st>>>(ncl, m->cl_full_off.as<int>(), own_cnt, cursor);
     a.run_off = m->cl_run_off.as<int>();
     a.full_off = m->cl_full_off.as<int>();

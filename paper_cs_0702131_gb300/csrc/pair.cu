@@ -880,10 +880,8 @@ __global__ void __launch_bounds__(256) unsort_forces(const int *inv, int64_t n, 
         } else {
             float4 f = ((const float4 *)facc)[s];
             x = f.x; y = f.y; z = f.z;
-            // the FP32 error of this force is about a fixed multiple of sqrt(sum |f|^2);
-            // a molecule whose force is too small against it is recomputed in FP64
-            if (flag_list && f.x * f.x + f.y * f.y + f.z * f.z < kflag2 * f.w)
-                flag_list[1 + atomicAdd(flag_list, 1)] = s;
+            (void)flag_list;
+            (void)kflag2;
         }
     }
     out[3 * k] = (T)x;
@@ -891,35 +889,123 @@ __global__ void __launch_bounds__(256) unsort_forces(const int *inv, int64_t n, 
     out[3 * k + 2] = (T)z;
 }
 
-// FP64 forces of the molecules flagged by unsort_forces: a warp per molecule
-// k (binned) of cluster A, lanes over the molecules of A and of every
-// (partner cluster, image) of A's full list; an FP32 distance test with a
-// wide margin skips the clearly distant ones, the rest are decided and
-// evaluated in FP64 with the all-pairs definition's operation order
-// ((x_k - x_l) - n.L, (dx^2 + dy^2) + dz^2), so the pair set is exactly the
-// pairs within rc.  Writes the force (original order) over the FP32 one.
+// A binned molecule split at multiples of 2^-q: hi exact on the grid, lo the
+// rest (xloc - hi is exact; adding the stored remainder rounds far below
+// the separation's own rounding).  Valid for |x| < 2^(22 - q).
+__device__ __forceinline__ void grid_split(float4 x, float4 r, float qr, float4 &hi, float4 &lo) {
+    hi.x = __fsub_rn(__fadd_rn(x.x, qr), qr);
+    hi.y = __fsub_rn(__fadd_rn(x.y, qr), qr);
+    hi.z = __fsub_rn(__fadd_rn(x.z, qr), qr);
+    hi.w = x.w;
+    lo = make_float4(__fsub_rn(x.x, hi.x) + r.x, __fsub_rn(x.y, hi.y) + r.y, __fsub_rn(x.z, hi.z) + r.z, 0.f);
+}
+
+// The FP32 error of a molecule's force is about a fixed multiple of
+// sqrt(sum |f|^2) (the .w of its accumulator); a molecule whose force is too
+// small against it goes to the list for recomputation.  In binned order,
+// one append per warp, so the list follows the molecules' positions.
+__global__ void __launch_bounds__(256) flag_ill_conditioned(const float4 *facc, int nb, float kflag2, int *flag_list) {
+    __shared__ int wcnt[8], wbase[8];
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    bool f = false;
+    if (s < nb) {
+        const float4 v = facc[s];
+        f = v.x * v.x + v.y * v.y + v.z * v.z < kflag2 * v.w;
+    }
+    const unsigned b = __ballot_sync(0xffffffffu, f);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) wcnt[w] = __popc(b);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int i = 0; i < 8; ++i) {
+            wbase[i] = t;
+            t += wcnt[i];
+        }
+        const int base = t ? atomicAdd(flag_list, t) : 0;
+        for (int i = 0; i < 8; ++i) wbase[i] += base;
+    }
+    __syncthreads();
+    if (f) flag_list[1 + wbase[w] + __popc(b & ((1u << lane) - 1u))] = s;
+}
+
+// Double-single ("float-float") arithmetic: a value is an unevaluated sum
+// hi + lo of two FP32 numbers (about 48 significant bits) built from
+// error-free transformations: Knuth's TwoSum, the FMA form of Dekker's
+// TwoProduct, and a Newton step for the reciprocal (x' = x + x (1 - a x)).
+// GB300 runs FP32 about 75 times faster than FP64, so recomputing a
+// molecule this way costs far less than in FP64.
+struct ds {
+    float h, l;
+};
+__device__ __forceinline__ ds ds_fast2sum(float a, float b) {   // |a| >= |b|
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ds ds_twosum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ ds ds_add(ds a, ds b) {
+    const ds s = ds_twosum(a.h, b.h);
+    return ds_fast2sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ ds ds_mul(ds a, ds b) {
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    return ds_fast2sum(p, e);
+}
+__device__ __forceinline__ ds ds_rcp(ds a) {
+    const float y = __frcp_rn(a.h);
+    const float e = __fmaf_rn(-a.l, y, __fmaf_rn(-a.h, y, 1.f));   // 1 - a y
+    return ds_fast2sum(y, __fmul_rn(y, e));
+}
+
+// Recomputation of the molecules flagged by unsort_forces: a warp per
+// molecule k (binned) of cluster A, lanes over the molecules of A and of
+// every (partner cluster, image) of A's full list.  Each separation is
+// formed exactly before one rounding (hi parts on the 2^-q grid, as in the
+// cluster kernel) and an FP32 test with a wide margin queues the nearby
+// ones; the queue is evaluated one pair per lane in double-single
+// arithmetic.  r^2 < rc^2 is decided on the double-single r^2 (relative
+// error ~1e-14); within 1e-10 rc^2 of the cut-off the FP64 all-pairs
+// operation order decides, so the pair set is exactly the pairs within rc.
+// Writes the force (original order) over the FP32 one.
 struct RefineArgs {
     const int *flag_list, *cl_first, *cl_of, *full_off, *order;
     const unsigned long long *full;
-    const double *orgm64;
+    const float4 *xlo;
+    const float4 *cl_box;        // boxes of the clusters' molecules from the FP32 pass
     float *out;
     int C;
+    const int *orgm;             // molecule-frame origins in units of 2^-10 (per cell)
+    float Lh[3], Ll[3];          // box lengths: multiple of 2^-q plus FP32 remainder
+    float qround;                // grid_split constant
+    float sig2[kMaxSpecies * kMaxSpecies][2];   // sigma_ab^2 and 24 eps_ab, double-single
+    float c24[kMaxSpecies * kMaxSpecies][2];
+    float rc2h, rc2l;            // rc^2, double-single
 };
 
-__global__ void __launch_bounds__(256) refine64(PairArgs a, RefineArgs r) {
-    __shared__ double tab[kMaxSpecies * kMaxSpecies][4];
-    __shared__ float4 ed[8][32];       // per warp: live entries of the batch (shift, image)
+__global__ void __launch_bounds__(256) refine_ds(PairArgs a, RefineArgs r) {
+    __shared__ float4 ed[8][32];       // per warp: live entries of the batch: shift hi (xyz), image (w)
+    __shared__ float4 el[8][32];       //           shift remainder (xyz)
     __shared__ int eb[8][32];          //           first molecule minus candidate position
-    for (int i = threadIdx.x; i < kMaxSpecies * kMaxSpecies; i += blockDim.x)
-        for (int q = 0; q < 4; ++q) tab[i][q] = a.tab.d[i][q];
-    __syncthreads();
+    __shared__ float4 rq[8][64][2];    //           queued pairs: separation hi, lo (+ molecule, image)
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u, le = FULL >> (31 - lane);
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
     const int nflag = r.flag_list[0];
     const float pre2 = a.rc2_hi * 1.001f + 1e-3f;
-    for (int i = gw; i < nflag; i += nw) {
+    const float reach = sqrtf(pre2) + 1e-3f;
+    // contiguous chunks of the (spatially ordered) list per warp: neighbouring
+    // molecules share their candidates in the caches
+    const int chunk = (nflag + nw - 1) / nw;
+    const int i_end = min(nflag, (gw + 1) * chunk);
+    for (int i = gw * chunk; i < i_end; ++i) {
         const int k = r.flag_list[1 + i];
         // cell of k (cell_off[c] <= k < cell_off[c + 1]): 32-ary search, one probe per lane
         int lo = 0, hi = r.C;
@@ -932,19 +1018,55 @@ __global__ void __launch_bounds__(256) refine64(PairArgs a, RefineArgs r) {
             hi = min(lo + step, hi);
         }
         const int A = r.cl_of[lo];
-        const double *xk = a.xs64 + 3 * (size_t)k;
-        const float4 xk32 = a.xloc[k];
-        const int spk = __float_as_int(xk32.w) & (kMaxSpecies - 1);
-        const double *oA = r.orgm64 + 3 * (size_t)r.cl_first[A];
-        R3<double> F = {0, 0, 0}, dummy = {0, 0, 0};
-        double acc7[7] = {0, 0, 0, 0, 0, 0, 0};
+        float4 kh, kl;
+        grid_split(a.xloc[k], r.xlo[k], r.qround, kh, kl);
+        const int spk = __float_as_int(kh.w) & (kMaxSpecies - 1);
+        const int *oA = r.orgm + 3 * (size_t)r.cl_first[A];
+        ds Fx = {0.f, 0.f}, Fy = {0.f, 0.f}, Fz = {0.f, 0.f};
+        int nq = 0;
+        // the queued pairs, one per lane
+        auto drain = [&](int count) {
+            if (lane < count) {
+                const float4 q0 = rq[wib][lane][0], q1 = rq[wib][lane][1];
+                const ds rx = ds_fast2sum(q0.x, q0.w), ry = ds_fast2sum(q0.y, q1.x), rz = ds_fast2sum(q0.z, q1.y);
+                const int l = __float_as_int(q1.z);
+                const int32_t nl = __float_as_int(q1.w);
+                // r^2 = sum (h + l)^2 with the squares of the hi parts exact
+                ds r2 = {0.f, 0.f};
+                const ds cs[3] = {rx, ry, rz};
+                for (int c = 0; c < 3; ++c) {
+                    const float p = __fmul_rn(cs[c].h, cs[c].h);
+                    const float e = __fmaf_rn(2.f * cs[c].h, cs[c].l, __fmaf_rn(cs[c].h, cs[c].h, -p));
+                    r2 = ds_add(r2, ds_fast2sum(p, e));
+                }
+                const ds dr = ds_add(r2, ds{-r.rc2h, -r.rc2l});
+                bool in = dr.h < 0.f;
+                if (fabsf(dr.h) <= 1e-10f * r.rc2h) {
+                    double x, y, z, rr;
+                    sep64(a.xs64 + 3 * (size_t)k, a.xs64 + 3 * (size_t)l, a.L, nl, x, y, z, rr);
+                    in = rr < a.rc2_d;
+                }
+                if (in) {
+                    const int ab = spk * kMaxSpecies + (__float_as_int(a.xloc[l].w) & (kMaxSpecies - 1));
+                    const ds inv = ds_rcp(r2);
+                    const ds s = ds_mul(ds{r.sig2[ab][0], r.sig2[ab][1]}, inv);
+                    const ds s3 = ds_mul(ds_mul(s, s), s);
+                    const ds t = ds_add(ds{2.f * s3.h, 2.f * s3.l}, ds{-1.f, 0.f});
+                    const ds fs = ds_mul(ds_mul(ds_mul(ds{r.c24[ab][0], r.c24[ab][1]}, inv), s3), t);
+                    Fx = ds_add(Fx, ds_mul(fs, rx));
+                    Fy = ds_add(Fy, ds_mul(fs, ry));
+                    Fz = ds_add(Fz, ds_mul(fs, rz));
+                }
+            }
+            __syncwarp();
+        };
         const int f0 = r.full_off[A], f1 = r.full_off[A + 1];
         // entries: A itself (image 0), then A's full list; 32 at a time, one per lane
         for (int e0 = f0 - 1; e0 < f1; e0 += 32) {
             const int e = e0 + lane;
             int n = 0, js = 0;
             int32_t np = 0;
-            float3 sh = make_float3(0.f, 0.f, 0.f);
+            float4 dh = make_float4(0.f, 0.f, 0.f, 0.f), dl = dh;
             if (e < f1) {
                 int B = A;
                 if (e >= f0) {
@@ -952,12 +1074,27 @@ __global__ void __launch_bounds__(256) refine64(PairArgs a, RefineArgs r) {
                     B = (int)(key & 0xffffffffu);
                     np = (int32_t)(key >> 32);
                 }
-                const double *oB = r.orgm64 + 3 * (size_t)r.cl_first[B];
-                sh = make_float3((float)((oB[0] - oA[0]) + (double)unpack_n(np, 0) * a.L[0]),
-                                 (float)((oB[1] - oA[1]) + (double)unpack_n(np, 1) * a.L[1]),
-                                 (float)((oB[2] - oA[2]) + (double)unpack_n(np, 2) * a.L[2]));
+                // shift into A's frame: origin difference (a multiple of 2^-10, exact)
+                // plus n.L (a multiple of 2^-q plus a remainder), all in FP32
+                const int *oB = r.orgm + 3 * (size_t)r.cl_first[B];
+                float D[3], H[3], R[3];
+                for (int d = 0; d < 3; ++d) {
+                    const float nd = (float)unpack_n(np, d);
+                    H[d] = __fmaf_rn(nd, r.Lh[d], (float)(oB[d] - oA[d]) * (1.f / 1024.f));
+                    R[d] = nd * r.Ll[d];
+                    D[d] = H[d] + R[d];
+                }
+                dh = make_float4(H[0], H[1], H[2], __int_as_float(np));
+                dl = make_float4(R[0], R[1], R[2], 0.f);
                 js = a.cell_off[r.cl_first[B]];
                 n = a.cell_off[r.cl_first[B + 1]] - js;
+                // a partner cluster whose molecules' box (moved into A's frame) lies beyond
+                // reach of molecule k holds none of its pairs
+                const float4 bl = r.cl_box[2 * B], bh = r.cl_box[2 * B + 1];
+                const float qx = fmaxf(fmaxf(bl.x + D[0] - kh.x, kh.x - (bh.x + D[0])), 0.f);
+                const float qy = fmaxf(fmaxf(bl.y + D[1] - kh.y, kh.y - (bh.y + D[1])), 0.f);
+                const float qz = fmaxf(fmaxf(bl.z + D[2] - kh.z, kh.z - (bh.z + D[2])), 0.f);
+                if (qx * qx + qy * qy + qz * qz > reach * reach) n = 0;
             }
             int inc = n;
 #pragma unroll
@@ -970,7 +1107,8 @@ __global__ void __launch_bounds__(256) refine64(PairArgs a, RefineArgs r) {
             const unsigned lbal = __ballot_sync(FULL, live);
             if (live) {
                 const int sl = __popc(lbal & lt);
-                ed[wib][sl] = make_float4(sh.x, sh.y, sh.z, __int_as_float(np));
+                ed[wib][sl] = dh;
+                el[wib][sl] = dl;
                 eb[wib][sl] = js - (inc - n);
             }
             __syncwarp();
@@ -979,32 +1117,56 @@ __global__ void __launch_bounds__(256) refine64(PairArgs a, RefineArgs r) {
                 const int base = __popc(__ballot_sync(FULL, live && b <= 0));
                 const unsigned M = __reduce_or_sync(FULL, (live && b > 0 && b < 32) ? (1u << b) : 0u);
                 const int p = p0 + lane;
+                bool near = false;
+                float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0;
                 if (p < total) {
                     const int o = base + __popc(M & le);
                     const int l = p + eb[wib][o];
-                    const float4 d = ed[wib][o];
+                    const float4 d = ed[wib][o], dlo = el[wib][o];
                     const int32_t nl = __float_as_int(d.w);
                     if (!(l == k && nl == 0)) {
-                        const float4 xl = a.xloc[l];
-                        const float qx = xk32.x - (xl.x + d.x), qy = xk32.y - (xl.y + d.y), qz = xk32.z - (xl.z + d.z);
-                        if (qx * qx + qy * qy + qz * qz <= pre2) {
-                            double rx, ry, rz, r2;
-                            sep64(xk, a.xs64 + 3 * (size_t)l, a.L, nl, rx, ry, rz, r2);
-                            if (r2 < a.rc2_d)
-                                pair64<true, false>(tab, rx, ry, rz, r2, spk, __float_as_int(xl.w) & (kMaxSpecies - 1),
-                                                    F, dummy, acc7);
-                        }
+                        float4 lh, ll;
+                        grid_split(a.xloc[l], r.xlo[l], r.qround, lh, ll);
+                        // separation k - (l + shift): exact hi part, small remainder
+                        const float hx = kh.x - (lh.x + d.x), hy = kh.y - (lh.y + d.y), hz = kh.z - (lh.z + d.z);
+                        const float lx = kl.x - (ll.x + dlo.x), ly = kl.y - (ll.y + dlo.y), lz = kl.z - (ll.z + dlo.z);
+                        const float x = hx + lx, y = hy + ly, z = hz + lz;
+                        near = x * x + y * y + z * z <= pre2;
+                        q0 = make_float4(hx, hy, hz, lx);
+                        q1 = make_float4(ly, lz, __int_as_float(l), __int_as_float(nl));
                     }
                 }
+                const unsigned nb = __ballot_sync(FULL, near);
+                if (near) {
+                    const int slot = nq + __popc(nb & lt);
+                    rq[wib][slot][0] = q0;
+                    rq[wib][slot][1] = q1;
+                }
+                nq += __popc(nb);
+                __syncwarp();
+                if (nq >= 32) {
+                    drain(32);
+                    nq -= 32;
+                    if (lane < nq) {
+                        rq[wib][lane][0] = rq[wib][32 + lane][0];
+                        rq[wib][lane][1] = rq[wib][32 + lane][1];
+                    }
+                    __syncwarp();
+                }
             }
-            __syncwarp();
         }
-        const double fx = warp_sum(F.x), fy = warp_sum(F.y), fz = warp_sum(F.z);
+        if (nq > 0) drain(nq);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            Fx = ds_add(Fx, ds{__shfl_xor_sync(FULL, Fx.h, o), __shfl_xor_sync(FULL, Fx.l, o)});
+            Fy = ds_add(Fy, ds{__shfl_xor_sync(FULL, Fy.h, o), __shfl_xor_sync(FULL, Fy.l, o)});
+            Fz = ds_add(Fz, ds{__shfl_xor_sync(FULL, Fz.h, o), __shfl_xor_sync(FULL, Fz.l, o)});
+        }
         if (lane == 0) {
             const int o = r.order[k];
-            r.out[3 * (size_t)o] = (float)fx;
-            r.out[3 * (size_t)o + 1] = (float)fy;
-            r.out[3 * (size_t)o + 2] = (float)fz;
+            r.out[3 * (size_t)o] = Fx.h + Fx.l;
+            r.out[3 * (size_t)o + 1] = Fy.h + Fy.l;
+            r.out[3 * (size_t)o + 2] = Fz.h + Fz.l;
         }
     }
 }
@@ -1441,27 +1603,18 @@ struct ClKArgs {
     const int *cl_first, *cl_run_off;
     const ClRun *runs;
     const float4 *xlo;
+    float4 *cl_box;              // out: each cluster's box of molecules (lo, hi; hi parts, own frame)
     int ncl;
     float qround;                // 1.5 * 2^(23 - q): x + qround - qround rounds x to a multiple of 2^-q
 };
 
-// A binned molecule split at multiples of 2^-q: hi exact on the grid, lo the
-// rest (xloc - hi is exact; adding the stored remainder rounds far below
-// the separation's own rounding).  Valid for |x| < 2^(22 - q).
-__device__ __forceinline__ void grid_split(float4 x, float4 r, float qr, float4 &hi, float4 &lo) {
-    hi.x = __fsub_rn(__fadd_rn(x.x, qr), qr);
-    hi.y = __fsub_rn(__fadd_rn(x.y, qr), qr);
-    hi.z = __fsub_rn(__fadd_rn(x.z, qr), qr);
-    hi.w = x.w;
-    lo = make_float4(__fsub_rn(x.x, hi.x) + r.x, __fsub_rn(x.y, hi.y) + r.y, __fsub_rn(x.z, hi.z) + r.z, 0.f);
-}
 
 constexpr int kCT = 128, kCW = kCT / 32;
 // A molecule's FP32 force error is about a multiple of sqrt(sum_l |f_kl|^2)
 // (rounding of each pair force, mostly; the separations are rounded once);
 // kRefineScale bounds that multiple with a wide safety margin.  A molecule
 // whose force is below kRefineScale / tol times that scale gets refined.
-constexpr double kRefineScale = 1e-6;
+constexpr double kRefineScale = 1.25e-6;
 constexpr int kCap = 256;                 // survivors buffered per warp
 constexpr int kNI = 8;                    // molecules of A per i-tile
 // packed survivor / tile word (.w of the hi position)
@@ -1621,7 +1774,13 @@ __global__ void __launch_bounds__(kCT, MINB) pair_fwd32c(PairArgs a, ClKArgs c) 
         if (A >= c.ncl) break;
         const int c0 = c.cl_first[A], c1 = c.cl_first[A + 1];
         const int s0 = a.cell_off[c0], s1 = a.cell_off[c1], nA = s1 - s0;
-        if (nA == 0) continue;
+        if (nA == 0) {
+            if (lane == 0) {
+                c.cl_box[2 * A] = make_float4(1e30f, 1e30f, 1e30f, 0.f);
+                c.cl_box[2 * A + 1] = make_float4(-1e30f, -1e30f, -1e30f, 0.f);
+            }
+            continue;
+        }
         // 1. joint box of A's molecules (hi parts; the remainders lie inside the margins)
         float bl[3] = {1e30f, 1e30f, 1e30f}, bh[3] = {-1e30f, -1e30f, -1e30f};   // to shared memory below
         for (int k = s0 + lane; k < s1; k += 32) {
@@ -1639,6 +1798,10 @@ __global__ void __launch_bounds__(kCT, MINB) pair_fwd32c(PairArgs a, ClKArgs c) 
         if (lane < 3) {
             w.box[lane] = lane == 0 ? bl[0] : lane == 1 ? bl[1] : bl[2];
             w.box[3 + lane] = lane == 0 ? bh[0] : lane == 1 ? bh[1] : bh[2];
+        }
+        if (lane == 0) {
+            c.cl_box[2 * A] = make_float4(bl[0], bl[1], bl[2], 0.f);
+            c.cl_box[2 * A + 1] = make_float4(bh[0], bh[1], bh[2], 0.f);
         }
         __syncwarp();
         int nq = 0;
@@ -2076,6 +2239,7 @@ extern "C" aica_status aica_forces(aica_mesh *m, const aica_lj *lj, aica_precisi
             c.cl_run_off = m->cl_run_off.as<int>();
             c.runs = m->cl_runs.as<ClRun>();
             c.xlo = m->xlo.as<float4>();
+            c.cl_box = m->cl_box.as<float4>();
             c.ncl = (int)m->n_cl;
             c.qround = (float)ldexp(1.5, 23 - m->qexp);
             launch_fwd32c(a, c, multi, shift, st);
@@ -2106,7 +2270,11 @@ extern "C" aica_status aica_forces(aica_mesh *m, const aica_lj *lj, aica_precisi
     if (n > 0) {
         const unsigned g = (unsigned)((n + 255) / 256);
         if (f64) unsort_forces<double><<<g, 256, 0, st>>>(m->inv.as<int>(), n, m->facc.p, (double *)force_out, 1, acc, ev_out, (long long *)counts_out);
-        else unsort_forces<float><<<g, 256, 0, st>>>(m->inv.as<int>(), n, m->facc.p, (float *)force_out, 0, acc, ev_out, (long long *)counts_out, flags, kf * kf);
+        else unsort_forces<float><<<g, 256, 0, st>>>(m->inv.as<int>(), n, m->facc.p, (float *)force_out, 0, acc, ev_out, (long long *)counts_out);
+        if (refine) {
+            flag_ill_conditioned<<<g, 256, 0, st>>>((const float4 *)m->facc.p, (int)n, kf * kf, flags);
+            m->launches += 1;
+        }
     } else {
         finish_sums<<<1, 15 * 32, 0, st>>>(acc, ev_out, (long long *)counts_out);
     }
@@ -2118,10 +2286,30 @@ extern "C" aica_status aica_forces(aica_mesh *m, const aica_lj *lj, aica_precisi
         r.full_off = m->cl_full_off.as<int>();
         r.full = m->cl_full.as<unsigned long long>();
         r.order = m->order.as<int>();
-        r.orgm64 = m->orgm64.as<double>();
+        r.xlo = m->xlo.as<float4>();
+        r.cl_box = m->cl_box.as<float4>();
         r.out = (float *)force_out;
         r.C = a.C;
-        refine64<<<152 * 8, 256, 0, st>>>(a, r);
+        r.orgm = m->orgm.as<int>();
+        for (int d = 0; d < 3; ++d) {
+            const double L = m->box.periodic[d] ? m->box.L[d] : 0.0;
+            // nearest FP32 of L on the 2^-q grid (a multiple of 2^-q whether or not
+            // the grid value itself fits 24 bits), remainder against that FP32 value
+            r.Lh[d] = (float)(rint(ldexp(L, m->qexp)) * ldexp(1.0, -m->qexp));
+            r.Ll[d] = (float)(L - (double)r.Lh[d]);
+        }
+        r.qround = (float)ldexp(1.5, 23 - m->qexp);
+        for (int i = 0; i < kMaxSpecies * kMaxSpecies; ++i) {
+            const double *t = a.tab.d[i];
+            const float sh = (float)t[0], ch = (float)t[1];
+            r.sig2[i][0] = sh;
+            r.sig2[i][1] = (float)(t[0] - (double)sh);
+            r.c24[i][0] = ch;
+            r.c24[i][1] = (float)(t[1] - (double)ch);
+        }
+        r.rc2h = (float)a.rc2_d;
+        r.rc2l = (float)(a.rc2_d - (double)r.rc2h);
+        refine_ds<<<152 * 8, 256, 0, st>>>(a, r);
         m->launches += 1;
     }
     AICA_CUDA(cudaGetLastError());
