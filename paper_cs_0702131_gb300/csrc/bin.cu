@@ -117,14 +117,17 @@ __device__ __forceinline__ int orient(float3 a, float3 b, float3 c, float3 q, fl
 // then q must lie behind that triangle.
 // exit_t (optional): for a convex cell found outside, the triangle whose
 // plane q lies in front of, else -1.
+// boxcheck = false skips the bounding-box rejection, so that a convex cell
+// the point lies outside of always reports an exit triangle (for walks).
 template <bool EXACT>
-__device__ int cell_test(const BinArgs &a, int c, float3 q, const double *p64, int *exit_t = nullptr) {
+__device__ int cell_test(const BinArgs &a, int c, float3 q, const double *p64, int *exit_t = nullptr,
+                         bool boxcheck = true) {
     if (exit_t) *exit_t = -1;
     const float *B = a.box32 + 6 * c;
     const float scale = fmaxf(a.max_local, fmaxf(fabsf(q.x), fmaxf(fabsf(q.y), fabsf(q.z))));
     const float tol = 1e-5f * scale;
-    if (q.x < B[0] - tol || q.y < B[1] - tol || q.z < B[2] - tol || q.x > B[3] + tol || q.y > B[4] + tol ||
-        q.z > B[5] + tol)
+    if (boxcheck && (q.x < B[0] - tol || q.y < B[1] - tol || q.z < B[2] - tol || q.x > B[3] + tol ||
+                     q.y > B[4] + tol || q.z > B[5] + tol))
         return 0;
     const int t0 = a.tri_off[c], code = a.ntri[c], nt = code & 0xffff;
     bool behind = true;
@@ -169,10 +172,66 @@ __device__ __forceinline__ bool cell_contains(const BinArgs &a, int c, float3 q,
     return cell_test<true>(a, c, q, p64) == 1;
 }
 
+// FP64 -> FP32 without the conversion units (on GB300 those share the
+// narrow FP64 pipe): hi = x with its 53-bit significand rounded (half up)
+// to 24 bits, lo = x - hi rounded to 24 bits, both built from the IEEE bit
+// pattern with integer operations.  |lo| <= ulp(hi) / 2 and hi + lo equals x
+// to about 2^-48 |x|.  For |x| in [2^-100, 2^100] or x = 0 (positions in a
+// molecule or cell frame); smaller values give 0.
+__device__ __forceinline__ void split_f64(double x, float &hi, float &lo) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    int E = (int)((b >> 52) & 0x7ff);
+    if (E < 1023 - 100) {
+        hi = lo = 0.f;
+        return;
+    }
+    const unsigned long long m = (b & 0xfffffffffffffULL) | (1ULL << 52);
+    unsigned long long m24 = (m + (1ULL << 28)) >> 29;
+    const long long rem = (long long)m - (long long)(m24 << 29);     // |rem| <= 2^28
+    if (m24 >> 24) {
+        m24 >>= 1;
+        ++E;
+    }
+    hi = __int_as_float((int)(sign | ((unsigned)(E - 1023 + 127) << 23) | ((unsigned)m24 & 0x7fffffu)));
+    if (rem == 0) {
+        lo = 0.f;
+        return;
+    }
+    // rem * 2^(E0 - 1075) with E0 the exponent before a carry (rem was taken against it)
+    const int E0 = (int)((b >> 52) & 0x7ff);
+    unsigned long long r = (unsigned long long)(rem < 0 ? -rem : rem);
+    const int n = 63 - __clzll((long long)r);                           // bit length - 1, <= 28
+    unsigned rm;
+    int eb = E0 - 1075 + n;                                            // exponent of the leading bit
+    if (n > 23) {
+        const int sh = n - 23;
+        unsigned long long q = (r + (1ULL << (sh - 1))) >> sh;
+        if (q >> 24) {
+            q >>= 1;
+            ++eb;
+        }
+        rm = (unsigned)q;
+    } else {
+        rm = (unsigned)(r << (23 - n));
+    }
+    if (eb + 127 < 1) {          // below the normal FP32 range: negligible against hi
+        lo = 0.f;
+        return;
+    }
+    const unsigned lsign = sign ^ (rem < 0 ? 0x80000000u : 0u);
+    lo = __int_as_float((int)(lsign | ((unsigned)(eb + 127) << 23) | (rm & 0x7fffffu)));
+}
+
 // p relative to the dyadic origin c_k * 2^-10 of cell c, in FP32 (one rounding)
 __device__ __forceinline__ float3 local_to(const BinArgs &a, const double *p, int c) {
     const double *o = a.org + 3 * c;
-    return make_float3((float)(p[0] - o[0]), (float)(p[1] - o[1]), (float)(p[2] - o[2]));
+    float3 q;
+    float l;
+    split_f64(p[0] - o[0], q.x, l);
+    split_f64(p[1] - o[1], q.y, l);
+    split_f64(p[2] - o[2], q.z, l);
+    return q;
 }
 
 __device__ __forceinline__ void wrapped_position(const BinArgs &a, int64_t k, double *p, bool &ok) {
@@ -226,7 +285,13 @@ __global__ void __launch_bounds__(256) bin_locate(BinArgs a) {
     count_located(a, found);
 }
 
-// Previous cell first; molecules that left it go to the miss list.
+// Previous cell first.  A molecule that left a convex cell walks: into the
+// cell across the face whose plane it lies in front of, up to kWalk cells
+// (a visibility walk, as in point location in triangulations); the FP32
+// filter alone decides each step.  Molecules not found so (the walk met a
+// boundary, a non-convex cell, an undecided test, or ran out of steps) go
+// to the miss list.
+constexpr int kWalk = 8;
 __global__ void __launch_bounds__(256) bin_locate_hint(BinArgs a) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool miss = false, undecided = false;
@@ -236,20 +301,23 @@ __global__ void __launch_bounds__(256) bin_locate_hint(BinArgs a) {
         bool ok;
         wrapped_position(a, k, p, ok);
         const int h = a.hint[k];
-        int ex = -1;
-        const int r = (ok && h >= 0) ? cell_test<false>(a, h, local_to(a, p, h), p, &ex) : 0;
-        // a molecule that left a convex cell: first the cell across the face it crossed
-        const int h2 = (ok && r == 0 && ex >= 0) ? a.tri_nbr[ex] : -1;
-        const int r2 = h2 >= 0 ? cell_test<false>(a, h2, local_to(a, p, h2), p) : 0;
-        if (r == 1) {
-            a.cell_of[k] = h;
-            located = h;
-        } else if (r2 == 1) {
-            a.cell_of[k] = h2;
-            located = h2;
+        if (ok && h >= 0) {
+            int c = h, ex = -1;
+            int r = cell_test<false>(a, c, local_to(a, p, c), p, &ex, false);
+            undecided = r < 0;
+            for (int step = 0; step < kWalk && r == 0 && ex >= 0; ++step) {
+                c = a.tri_nbr[ex];
+                if (c < 0) break;
+                r = cell_test<false>(a, c, local_to(a, p, c), p, &ex, false);
+            }
+            if (r == 1) {
+                a.cell_of[k] = c;
+                located = c;
+            } else {
+                miss = true;
+            }
         } else if (ok) {
             miss = true;
-            undecided = r < 0;
         } else {
             a.cell_of[k] = -1;
             a.inv[k] = -1;
@@ -430,11 +498,7 @@ __global__ void __launch_bounds__(256) bin_scatter_down(const int *cell_of, int6
 __device__ __forceinline__ void frame_split(const BinArgs &a, const double *p, const double *o, int sp,
                                             float4 &hi, float4 &lo) {
     float h[3], l[3];
-    for (int d = 0; d < 3; ++d) {
-        const double x = p[d] - o[d];
-        h[d] = (float)x;
-        l[d] = (float)(x - (double)h[d]);
-    }
+    for (int d = 0; d < 3; ++d) split_f64(p[d] - o[d], h[d], l[d]);   // p - o is exact (o dyadic, nearby)
     hi = make_float4(h[0], h[1], h[2], __int_as_float(sp & (kMaxSpecies - 1)));
     lo = make_float4(l[0], l[1], l[2], 0.f);
 }
