@@ -328,6 +328,20 @@ aica_status aica_take_kernel_times(aica_mesh *mesh, float *ms, int64_t cap, int6
  *   AICA_OPT_FP32_KERNEL      (default 0) FP32 box-periodic pair kernel:
  *       0 the cluster kernel when the lists have a cluster schedule, 1 the
  *       cell kernel (for comparison; its forces are not refined).
+ *   AICA_OPT_N_OWNED          (default -1) portion of a spatial
+ *       decomposition (§2.1, App. A.2): molecules [0, n_owned) of the next
+ *       aica_bin_molecules call belong to this processor, the rest are the
+ *       halo it received (the molecules of the remote source cells of its
+ *       processor-referred cells, at their own positions).  aica_forces then
+ *       evaluates a pair of two owned molecules with Newton's third law, a
+ *       pair of an owned molecule and a halo molecule one-sidedly (the
+ *       force on the owned molecule; half the pair's energy and virial, the
+ *       other half being the other processor's), and no pair of two halo
+ *       molecules; force rows of halo molecules are unspecified and the
+ *       pair counts count each evaluated pair once.  Needs box periodicity
+ *       and the minimum-distance lists of the whole mesh on every
+ *       processor; aica_forces_backward and the cell kernel refuse it
+ *       (AICA_ERR_INVALID_ARG).  -1 returns to a single processor.
  *   AICA_OPT_REFINED          (read only) molecules the last FP32
  *       aica_forces call recomputed in FP64 (synchronizes `stream`).
  *   AICA_OPT_CLUSTER_PATH     (read only) 1 when the built lists have a
@@ -338,7 +352,8 @@ typedef enum {
     AICA_OPT_COUNT_EVALUATED = 1,
     AICA_OPT_FP32_KERNEL = 2,
     AICA_OPT_REFINED = 3,
-    AICA_OPT_CLUSTER_PATH = 4
+    AICA_OPT_CLUSTER_PATH = 4,
+    AICA_OPT_N_OWNED = 5
 } aica_option;
 aica_status aica_set_option(aica_mesh *mesh, aica_option option, double value);
 aica_status aica_get_option(aica_mesh *mesh, aica_option option, double *value, void *stream);

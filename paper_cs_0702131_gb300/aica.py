@@ -261,7 +261,8 @@ def aica_sort_by_cell_noalloc(cell_of, n_cells, order, cell_off):
     _check(lib().aica_sort_by_cell_noalloc(_ptr(cell_of), n, int(n_cells), _ptr(order), _ptr(cell_off), _stream()))
 
 
-OPTIONS = {"fp32_refine_tol": 0, "count_evaluated": 1, "fp32_kernel": 2, "refined": 3, "cluster_path": 4}
+OPTIONS = {"fp32_refine_tol": 0, "count_evaluated": 1, "fp32_kernel": 2, "refined": 3, "cluster_path": 4,
+           "n_owned": 5}
 
 
 def aica_set_option(h, name, value):

@@ -20,6 +20,9 @@ constexpr int kMaxVtx = 24;
 constexpr int kMaxEdg = 48;
 constexpr int kMaxSpecies = 8;
 constexpr int kMaxClusterCells = 16;   // cells of one pair-kernel cluster (see mesh.cu)
+// Bit of a binned molecule's species word (xloc.w) marking a molecule this
+// portion does not own (a halo copy received from the processor that does).
+constexpr int kGhostBit = kMaxSpecies;
 
 // Device-side error flags (bitwise OR into mesh->d_flags[0]).
 enum : unsigned {
@@ -190,6 +193,8 @@ struct aica_mesh {
     double refine_tol = 1e-5;                // FP32 forces: refine a molecule whose error bound exceeds this (0: off)
     bool count_evaluated = true;             // aica_forces: count the AICA-evaluated pairs (an extra pass)
     int fp32_kernel = 0;                     // 0: cluster kernel when available, 1: the cell kernel
+    int64_t n_owned = -1;                    // portion mode: molecules [0, n_owned) are owned, the rest halo (-1: all)
+    bool ghosts = false;                     // the last binning marked halo molecules
     int64_t n_refined = 0;                   // molecules the last FP32 call recomputed in FP64 (host copy on demand)
     aica::DevBuf unsorted;                   // [n] binned slots before the in-cell sort (cells of a few molecules)
     int max_species = -1;                    // from the last checked binning, -1 if unknown

@@ -64,6 +64,7 @@ struct BinArgs {
     const double *tri, *ctr;
     float max_local;
     float4 *xlo;              // remainders x - o_m - xloc (binned order)
+    int64_t n_owned;          // molecules >= n_owned are halo copies (n_owned = n: none)
     int *cell_of;
     int *cnt;              // molecules per cell (counted as they are located)
     int *inv;              // original -> binned index; -1 for molecules in no cell
@@ -499,7 +500,7 @@ __device__ __forceinline__ void frame_split(const BinArgs &a, const double *p, c
                                             float4 &hi, float4 &lo) {
     float h[3], l[3];
     for (int d = 0; d < 3; ++d) split_f64(p[d] - o[d], h[d], l[d]);   // p - o is exact (o dyadic, nearby)
-    hi = make_float4(h[0], h[1], h[2], __int_as_float(sp & (kMaxSpecies - 1)));
+    hi = make_float4(h[0], h[1], h[2], __int_as_float(sp));
     lo = make_float4(l[0], l[1], l[2], 0.f);
 }
 
@@ -542,7 +543,7 @@ __global__ void __launch_bounds__(256) bin_cells(BinArgs a, const int *cell_off,
                 xs64[3 * (int64_t)slot + d] = p[d];
             }
             float4 lo;
-            frame_split(a, p, a.orgm64 + 3 * c, sp, x, lo);
+            frame_split(a, p, a.orgm64 + 3 * c, (sp & (kMaxSpecies - 1)) | (k >= a.n_owned ? kGhostBit : 0), x, lo);
             xloc[slot] = x;
             a.xlo[slot] = lo;
         }
@@ -588,7 +589,7 @@ __global__ void __launch_bounds__(256) bin_cells(BinArgs a, const int *cell_off,
                     xs64[3 * (int64_t)slot + d] = p[d];
                 }
                 float4 y, lo;
-                frame_split(a, p, a.orgm64 + 3 * c, sp, y, lo);
+                frame_split(a, p, a.orgm64 + 3 * c, (sp & (kMaxSpecies - 1)) | (kk >= a.n_owned ? kGhostBit : 0), y, lo);
                 xloc[slot] = y;
                 a.xlo[slot] = lo;
                 sx += y.x; sy += y.y; sz += y.z;
@@ -632,7 +633,7 @@ __device__ __forceinline__ float4 local_xloc(const BinArgs &a, int k, int c, int
         xs64[3 * (int64_t)slot + d] = p[d];
     }
     float4 hi, lo;
-    frame_split(a, p, a.orgm64 + 3 * c, sp, hi, lo);
+    frame_split(a, p, a.orgm64 + 3 * c, (sp & (kMaxSpecies - 1)) | (k >= a.n_owned ? kGhostBit : 0), hi, lo);
     a.xlo[slot] = lo;
     return hi;
 }
@@ -821,6 +822,12 @@ extern "C" aica_status aica_bin_molecules(aica_mesh *m, const double *pos, const
     a.ctr = m->ctr.as<double>();
     a.max_local = (float)(m->max_local * (1 + 1e-6));
     a.xlo = m->xlo.as<float4>();
+    if (m->n_owned >= 0 && m->n_owned > n) {
+        set_error("aica_bin_molecules: n_owned %lld exceeds the %lld molecules", (long long)m->n_owned, (long long)n);
+        return AICA_ERR_INVALID_ARG;
+    }
+    a.n_owned = m->n_owned >= 0 ? m->n_owned : n;
+    m->ghosts = m->n_owned >= 0 && m->n_owned < n;
     for (int d = 0; d < 3; ++d) {
         a.glo_f[d] = (float)m->glo[d];
         a.gh_f[d] = (float)m->gh[d];

@@ -81,6 +81,10 @@ extern "C" aica_status aica_set_option(aica_mesh *m, aica_option opt, double v) 
         if (v != 0 && v != 1) break;
         m->fp32_kernel = (int)v;
         return AICA_OK;
+    case AICA_OPT_N_OWNED:
+        if (!(v >= -1) || v != (double)(int64_t)v) break;
+        m->n_owned = (int64_t)v;
+        return AICA_OK;
     default: break;
     }
     aica::set_error("aica_set_option: unknown, read-only or invalid option %d = %g", (int)opt, v);
@@ -94,6 +98,7 @@ extern "C" aica_status aica_get_option(aica_mesh *m, aica_option opt, double *v,
     case AICA_OPT_COUNT_EVALUATED: *v = m->count_evaluated ? 1 : 0; return AICA_OK;
     case AICA_OPT_FP32_KERNEL: *v = m->fp32_kernel; return AICA_OK;
     case AICA_OPT_CLUSTER_PATH: *v = m->built && m->n_cl_runs >= 0 ? 1 : 0; return AICA_OK;
+    case AICA_OPT_N_OWNED: *v = (double)m->n_owned; return AICA_OK;
     case AICA_OPT_REFINED: {
         int n = 0;
         if (m->flag_list.p) {

@@ -95,6 +95,7 @@ extern "C" aica_status aica_verlet_step(aica_mesh *m, const aica_lj *lj, aica_pr
     if (prec != AICA_FP32 && prec != AICA_FP64) { set_error("aica_verlet_step: bad precision"); return AICA_ERR_INVALID_ARG; }
     if (!(dt > 0) || !isfinite(dt)) { set_error("aica_verlet_step: dt must be positive"); return AICA_ERR_INVALID_ARG; }
     if (!m->built) { set_error("aica_verlet_step: build the lists first"); return AICA_ERR_NOT_BUILT; }
+    if (m->n_owned >= 0) { set_error("aica_verlet_step: not available in portion mode (halo molecules)"); return AICA_ERR_INVALID_ARG; }
     MdArgs a{};
     aica_status s = fill_md(lj, mass, species, n, a);
     if (s != AICA_OK) return s;

@@ -86,6 +86,7 @@ struct PairArgs {
     const void *vs;              // backward: grad_force in binned order (float4 / double4)
     double *acc;                 // [0..6] U, W; [8..15] counters (as unsigned long long); [16..] grads
     unsigned *next_cell;         // FP32 kernel: next unclaimed cell (zero at launch)
+    int ghosts;                  // portion mode: xloc.w carries kGhostBit on halo molecules
     int xf;                      // general referring transforms: image field = transform index
     int n_xf;                    // transforms in xft
     const XfDev *xft;            // [n_xf] transforms (identity first)
@@ -701,7 +702,7 @@ __global__ void __launch_bounds__(kPairThreads) pair_fwd64(PairArgs a) {
             for (int t = 0; t < NI; ++t) {
                 int k = sI + i0 + min(t, ni - 1);
                 for (int c = 0; c < 3; ++c) xi[t][c] = a.xs64[3 * (size_t)k + c];
-                spi[t] = __float_as_int(a.xloc[k].w);
+                spi[t] = __float_as_int(a.xloc[k].w);      // species | kGhostBit on halo molecules
                 fi[t] = {0, 0, 0};
             }
             // same-cell pairs k' > k
@@ -718,8 +719,10 @@ __global__ void __launch_bounds__(kPairThreads) pair_fwd64(PairArgs a) {
                         if (t < ni && li > i0 + t) {
                             double rx, ry, rz, r2;
                             sep64(xi[t], xl, a.L, 0, rx, ry, rz, r2);
-                            if (r2 < a.rc2_d) {
-                                pair64<MULTI, SHIFT>(tab, rx, ry, rz, r2, spi[t], spj, fi[t], fj, acc);
+                            const int g = ((spi[t] & kGhostBit) ? 1 : 0) + ((spj & kGhostBit) ? 1 : 0);
+                            if (r2 < a.rc2_d && g < 2) {
+                                pair64<MULTI, SHIFT>(tab, rx, ry, rz, r2, spi[t] & (kMaxSpecies - 1),
+                                                     spj & (kMaxSpecies - 1), fi[t], fj, acc, g ? 0.5 : 1.0);
                                 within[0]++;
                                 any = true;
                             }
@@ -741,16 +744,19 @@ __global__ void __launch_bounds__(kPairThreads) pair_fwd64(PairArgs a) {
                     bool any = false;
                     unsigned nin = 0;
                     // general transforms: a referred pair acts on I's molecule only and is met
-                    // again from the other side, so its energy and virial count half
+                    // again from the other side, so its energy and virial count half (so does
+                    // a pair of an owned and a halo molecule in portion mode)
                     const bool one = XF && npl != 0;
-                    const double w = one ? 0.5 : 1.0;
 #pragma unroll
                     for (int t = 0; t < NI; ++t) {
                         if (t < ni) {
                             double rx, ry, rz, r2;
                             sep64x<XF>(a, xi[t], xl, npl, rx, ry, rz, r2);
-                            if (r2 < a.rc2_d) {
-                                pair64<MULTI, SHIFT>(tab, rx, ry, rz, r2, spi[t], spj, fi[t], fj, acc, w);
+                            const int g = ((spi[t] & kGhostBit) ? 1 : 0) + ((spj & kGhostBit) ? 1 : 0);
+                            const double w = (one || g) ? 0.5 : 1.0;
+                            if (r2 < a.rc2_d && g < 2) {
+                                pair64<MULTI, SHIFT>(tab, rx, ry, rz, r2, spi[t] & (kMaxSpecies - 1),
+                                                     spj & (kMaxSpecies - 1), fi[t], fj, acc, w);
                                 nin++;
                                 any = true;
                             }
@@ -904,13 +910,14 @@ __device__ __forceinline__ void grid_split(float4 x, float4 r, float qr, float4 
 // sqrt(sum |f|^2) (the .w of its accumulator); a molecule whose force is too
 // small against it goes to the list for recomputation.  In binned order,
 // one append per warp, so the list follows the molecules' positions.
-__global__ void __launch_bounds__(256) flag_ill_conditioned(const float4 *facc, int nb, float kflag2, int *flag_list) {
+__global__ void __launch_bounds__(256) flag_ill_conditioned(const float4 *facc, const float4 *xloc, int nb,
+                                                              float kflag2, int *flag_list) {
     __shared__ int wcnt[8], wbase[8];
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     bool f = false;
     if (s < nb) {
         const float4 v = facc[s];
-        f = v.x * v.x + v.y * v.y + v.z * v.z < kflag2 * v.w;
+        f = v.x * v.x + v.y * v.y + v.z * v.z < kflag2 * v.w && !(__float_as_int(xloc[s].w) & kGhostBit);
     }
     const unsigned b = __ballot_sync(0xffffffffu, f);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -1618,7 +1625,7 @@ constexpr double kRefineScale = 1.25e-6;
 constexpr int kCap = 256;                 // survivors buffered per warp
 constexpr int kNI = 8;                    // molecules of A per i-tile
 // packed survivor / tile word (.w of the hi position)
-constexpr int kSpBits = 7, kSameBit = 1 << 3, kImgBit = 1 << 4;
+constexpr int kSpBits = 7, kSameBit = 1 << 3, kImgBit = 1 << 4, kGhostW = 1 << 21;
 __device__ __forceinline__ int cellq_of(int w) { return (w >> 5) & 15; }
 __device__ __forceinline__ int32_t n_of(int w) {   // 3 x 4-bit image -> pack_n
     const int c = w >> 9;
@@ -1661,10 +1668,10 @@ __device__ __forceinline__ int cell_in_cluster(const int *cell_off, int c0, int 
 // operation order inside it, after the pass), the force body skipped when
 // no lane of the warp is within rc.  SAME: own-cluster survivors pair only
 // with tile molecules of lower binned index.
-template <bool MULTI, bool SHIFT, bool SAME>
+template <bool MULTI, bool SHIFT, bool SAME, bool GHOST>
 __device__ __forceinline__ unsigned eval_tile(const PairArgs &a, const float4 *tab, const WarpC &w, int ni, int k0, float4 xh,
                                               float4 xl, float (&fi)[4 * kNI], float4 &fj, float &u_acc,
-                                              unsigned &nsame) {
+                                              unsigned &nsame, float *vg) {
     unsigned nin = 0, bm = 0;
     const float4 t0 = tab[0];
     const int wj = __float_as_int(xh.w), l = __float_as_int(xl.w);
@@ -1677,13 +1684,26 @@ __device__ __forceinline__ unsigned eval_tile(const PairArgs &a, const float4 *t
         const float ry = (h.y - xh.y) + (lo.y - xl.y);
         const float rz = (h.z - xh.z) + (lo.z - xl.z);
         const float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
-        const bool ok = !sj || k0 + t < l;
+        // portion mode: a pair of two halo molecules is not evaluated here,
+        // an owned-halo pair carries half its energy and virial
+        const bool gi = GHOST && (__float_as_int(h.w) & kGhostW), gj = GHOST && (wj & kGhostW);
+        const bool ok = (!sj || k0 + t < l) && !(gi && gj);
         const bool in = ok && r2 < a.rc2_lo;
         if (ok && !in && r2 < a.rc2_hi) bm |= 1u << t;
         float fs, u;
         lj32<MULTI, SHIFT>(tab, t0, __float_as_int(h.w) & kSpBits, wj & kSpBits, r2, fs, u);
         fs = in ? fs : 0.f;
-        u_acc += in ? u : 0.f;
+        const float wt = (gi || gj) ? 0.5f : 1.f;
+        u_acc += in ? (GHOST ? wt * u : u) : 0.f;
+        if (GHOST) {
+            const float g = wt * fs, gx = g * rx, gy = g * ry;
+            vg[0] = fmaf(gx, rx, vg[0]);
+            vg[1] = fmaf(gy, ry, vg[1]);
+            vg[2] = fmaf(g * rz, rz, vg[2]);
+            vg[3] = fmaf(gx, ry, vg[3]);
+            vg[4] = fmaf(gx, rz, vg[4]);
+            vg[5] = fmaf(gy, rz, vg[5]);
+        }
         fi[4 * t] = fmaf(fs, rx, fi[4 * t]);
         fi[4 * t + 1] = fmaf(fs, ry, fi[4 * t + 1]);
         fi[4 * t + 2] = fmaf(fs, rz, fi[4 * t + 2]);
@@ -1708,7 +1728,18 @@ __device__ __forceinline__ unsigned eval_tile(const PairArgs &a, const float4 *t
                 const float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
                 float fs, u;
                 lj32<MULTI, SHIFT>(tab, t0, __float_as_int(h.w) & kSpBits, wj & kSpBits, r2, fs, u);
-                u_acc += u;
+                const bool gi = GHOST && (__float_as_int(h.w) & kGhostW), gj = GHOST && (wj & kGhostW);
+                const float wt = (gi || gj) ? 0.5f : 1.f;
+                u_acc += GHOST ? wt * u : u;
+                if (GHOST) {
+                    const float g = wt * fs, gx = g * rx, gy = g * ry;
+                    vg[0] = fmaf(gx, rx, vg[0]);
+                    vg[1] = fmaf(gy, ry, vg[1]);
+                    vg[2] = fmaf(g * rz, rz, vg[2]);
+                    vg[3] = fmaf(gx, ry, vg[3]);
+                    vg[4] = fmaf(gx, rz, vg[4]);
+                    vg[5] = fmaf(gy, rz, vg[5]);
+                }
                 fi[4 * t] = fmaf(fs, rx, fi[4 * t]);
                 fi[4 * t + 1] = fmaf(fs, ry, fi[4 * t + 1]);
                 fi[4 * t + 2] = fmaf(fs, rz, fi[4 * t + 2]);
@@ -1737,7 +1768,7 @@ __device__ __forceinline__ void tile_reduce4(float (&v)[4 * kNI], int lane) {
 #pragma unroll
         for (int i = 0; i < 4; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
 }
-template <bool MULTI, bool SHIFT, int MINB>
+template <bool MULTI, bool SHIFT, bool GHOST, int MINB>
 __global__ void __launch_bounds__(kCT, MINB) pair_fwd32c(PairArgs a, ClKArgs c) {
     extern __shared__ float4 csh[];
     WarpC *wsh = reinterpret_cast<WarpC *>(csh);
@@ -1757,9 +1788,11 @@ __global__ void __launch_bounds__(kCT, MINB) pair_fwd32c(PairArgs a, ClKArgs c) 
     float4 *facc = (float4 *)a.facc;
     double *dsum = dsums[wib];
     float u_acc = 0.f;
+    float vg[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // portion mode: virial summed per pair
     unsigned wc0 = 0, wc1 = 0, wc2 = 0;     // this lane's pairs within rc: same cell, DIL, image
     // virial terms of a tile's or survivors' forces: per lane in FP32, then to the warp's sums
     auto add_vir = [&](float x, float y, float z, float fx, float fy, float fz) {
+        if (GHOST) return;          // summed per pair instead
         float q[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         outer7(q, x, y, z, fx, fy, fz);
 #pragma unroll
@@ -1815,7 +1848,8 @@ __global__ void __launch_bounds__(kCT, MINB) pair_fwd32c(PairArgs a, ClKArgs c) 
                     if (lane < ni) {
                         grid_split(a.xloc[k0 + lane], c.xlo[k0 + lane], c.qround, h, lo);
                         const int q = cell_in_cluster(a.cell_off, c0, c1, k0 + lane);
-                        h.w = __int_as_float((__float_as_int(h.w) & kSpBits) | (q << 5));
+                        const int w0 = __float_as_int(h.w);
+                        h.w = __int_as_float((w0 & kSpBits) | (q << 5) | ((w0 & kGhostBit) ? kGhostW : 0));
                     }
                     w.ih[lane] = h;
                     w.il[lane] = lo;
@@ -1834,9 +1868,9 @@ __global__ void __launch_bounds__(kCT, MINB) pair_fwd32c(PairArgs a, ClKArgs c) 
                     unsigned nin, nsame = 0;
                     const bool same = (__float_as_int(xh.w) & kSameBit) != 0;
                     if (__any_sync(FULL, same))
-                        nin = eval_tile<MULTI, SHIFT, true>(a, tab, w, ni, k0, xh, xl, fi, fj, u_acc, nsame);
+                        nin = eval_tile<MULTI, SHIFT, true, GHOST>(a, tab, w, ni, k0, xh, xl, fi, fj, u_acc, nsame, vg);
                     else
-                        nin = eval_tile<MULTI, SHIFT, false>(a, tab, w, ni, k0, xh, xl, fi, fj, u_acc, nsame);
+                        nin = eval_tile<MULTI, SHIFT, false, GHOST>(a, tab, w, ni, k0, xh, xl, fi, fj, u_acc, nsame, vg);
                     if (valid && nin) {
                         // within-rc counts per category (same cell, DIL, periodic image), per lane
                         if (same) {
@@ -1893,7 +1927,8 @@ __global__ void __launch_bounds__(kCT, MINB) pair_fwd32c(PairArgs a, ClKArgs c) 
             if (alive) {
                 grid_split(a.xloc[k], c.xlo[k], c.qround, xh, xl);
                 const int q = cell_in_cluster(a.cell_off, c0, c1, k);
-                xh.w = __int_as_float((__float_as_int(xh.w) & kSpBits) | kSameBit | (q << 5));
+                const int w0 = __float_as_int(xh.w);
+                xh.w = __int_as_float((w0 & kSpBits) | kSameBit | (q << 5) | ((w0 & kGhostBit) ? kGhostW : 0));
                 xl.w = __int_as_float(k);
             }
             push(alive, xh, xl);
@@ -1949,7 +1984,9 @@ __global__ void __launch_bounds__(kCT, MINB) pair_fwd32c(PairArgs a, ClKArgs c) 
                     const float dz = fmaxf(fmaxf(w.box[2] - xh.z, xh.z - w.box[5]), 0.f);
                     alive = dx * dx + dy * dy + dz * dz <= rcut2;
                     const int code = __float_as_int(dl.w) >> 12;
-                    xh.w = __int_as_float((__float_as_int(x.w) & kSpBits) | (code != 0 ? kImgBit : 0) | (code << 9));
+                    const int w0 = __float_as_int(x.w);
+                    xh.w = __int_as_float((w0 & kSpBits) | (code != 0 ? kImgBit : 0) | (code << 9) |
+                                          ((w0 & kGhostBit) ? kGhostW : 0));
                     xl = make_float4(y.x + dl.x, y.y + dl.y, y.z + dl.z, __int_as_float(l));
                 }
                 push(alive, xh, xl);
@@ -1958,6 +1995,14 @@ __global__ void __launch_bounds__(kCT, MINB) pair_fwd32c(PairArgs a, ClKArgs c) 
         }
         if (nq > 0) flush();
         // FP32 running sums to FP64 once per cluster
+        if (GHOST) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                const float sv = warp_sum(vg[i]);
+                vg[i] = 0.f;
+                if (lane == 0) w.vir[i] += sv;
+            }
+        }
         {
             const float s = warp_sum(u_acc);
             u_acc = 0.f;
@@ -2082,6 +2127,7 @@ void fill_common(aica_mesh *m, PairArgs &a) {
     for (int d = 0; d < 3; ++d) a.L[d] = m->box.periodic[d] ? m->box.L[d] : 0.0;
     a.facc = m->facc.p;
     a.acc = m->acc.as<double>();
+    a.ghosts = m->ghosts ? 1 : 0;
 }
 
 aica_status check_flags(aica_mesh *m, cudaStream_t st) {
@@ -2179,7 +2225,7 @@ void launch_bwd64(const BwdArgs &b, bool multi, int grid, cudaStream_t st) {
 
 // The FP32 cluster kernel: a persistent grid, every SM filled to its
 // occupancy (dynamic shared memory: the warps' survivor buffers and queues).
-template <bool MULTI, bool SHIFT>
+template <bool MULTI, bool SHIFT, bool GHOST>
 void launch_fwd32c_t(const PairArgs &a, const ClKArgs &c, cudaStream_t st) {
     constexpr int MINB = 5;
     static int cache[64] = {0};
@@ -2187,19 +2233,25 @@ void launch_fwd32c_t(const PairArgs &a, const ClKArgs &c, cudaStream_t st) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
     if (!cache[dev]) {
-        cudaFuncSetAttribute(pair_fwd32c<MULTI, SHIFT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+        cudaFuncSetAttribute(pair_fwd32c<MULTI, SHIFT, GHOST, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
         int sms = 0, per = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pair_fwd32c<MULTI, SHIFT, MINB>, kCT, shm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pair_fwd32c<MULTI, SHIFT, GHOST, MINB>, kCT, shm);
         cache[dev] = std::max(1, sms * std::max(1, per));
     }
     const int grid = std::min(cache[dev], std::max(1, (c.ncl + kCW - 1) / kCW));
-    pair_fwd32c<MULTI, SHIFT, MINB><<<grid, kCT, shm, st>>>(a, c);
+    pair_fwd32c<MULTI, SHIFT, GHOST, MINB><<<grid, kCT, shm, st>>>(a, c);
+}
+
+template <bool GHOST>
+void launch_fwd32c_g(const PairArgs &a, const ClKArgs &c, bool multi, bool shift, cudaStream_t st) {
+    if (multi) shift ? launch_fwd32c_t<true, true, GHOST>(a, c, st) : launch_fwd32c_t<true, false, GHOST>(a, c, st);
+    else shift ? launch_fwd32c_t<false, true, GHOST>(a, c, st) : launch_fwd32c_t<false, false, GHOST>(a, c, st);
 }
 
 void launch_fwd32c(const PairArgs &a, const ClKArgs &c, bool multi, bool shift, cudaStream_t st) {
-    if (multi) shift ? launch_fwd32c_t<true, true>(a, c, st) : launch_fwd32c_t<true, false>(a, c, st);
-    else shift ? launch_fwd32c_t<false, true>(a, c, st) : launch_fwd32c_t<false, false>(a, c, st);
+    if (a.ghosts) launch_fwd32c_g<true>(a, c, multi, shift, st);
+    else launch_fwd32c_g<false>(a, c, multi, shift, st);
 }
 
 }  // namespace
@@ -2232,6 +2284,14 @@ extern "C" aica_status aica_forces(aica_mesh *m, const aica_lj *lj, aica_precisi
     // cluster schedule (the cell kernel on request, and for general transforms)
     const bool clsched = !f64 && !a.xf && m->n_cl_runs >= 0;
     const bool clpath = clsched && m->fp32_kernel != 1;
+    if (m->ghosts && !f64 && !clpath) {
+        set_error("aica_forces: portion mode (halo molecules) needs the FP32 cluster kernel");
+        return AICA_ERR_INVALID_ARG;
+    }
+    if (m->ghosts && a.xf) {
+        set_error("aica_forces: portion mode (halo molecules) needs box periodicity");
+        return AICA_ERR_INVALID_ARG;
+    }
     if (!f64) {
         if (clpath) {
             ClKArgs c{};
@@ -2272,7 +2332,8 @@ extern "C" aica_status aica_forces(aica_mesh *m, const aica_lj *lj, aica_precisi
         if (f64) unsort_forces<double><<<g, 256, 0, st>>>(m->inv.as<int>(), n, m->facc.p, (double *)force_out, 1, acc, ev_out, (long long *)counts_out);
         else unsort_forces<float><<<g, 256, 0, st>>>(m->inv.as<int>(), n, m->facc.p, (float *)force_out, 0, acc, ev_out, (long long *)counts_out);
         if (refine) {
-            flag_ill_conditioned<<<g, 256, 0, st>>>((const float4 *)m->facc.p, (int)n, kf * kf, flags);
+            flag_ill_conditioned<<<g, 256, 0, st>>>((const float4 *)m->facc.p, m->xloc.as<float4>(), (int)n, kf * kf,
+                                                    flags);
             m->launches += 1;
         }
     } else {
@@ -2327,6 +2388,7 @@ extern "C" aica_status aica_forces_backward(aica_mesh *m, const aica_lj *lj, aic
     }
     if (prec != AICA_FP32 && prec != AICA_FP64) { set_error("aica_forces_backward: bad precision"); return AICA_ERR_INVALID_ARG; }
     if (!m->built || !m->binned) { set_error("aica_forces_backward: build the lists and bin the molecules first"); return AICA_ERR_NOT_BUILT; }
+    if (m->ghosts) { set_error("aica_forces_backward: not available in portion mode (halo molecules)"); return AICA_ERR_INVALID_ARG; }
     cudaStream_t st = (cudaStream_t)stream;
     BwdArgs b{};
     aica_status s = fill_params(m, lj, kMaxSpecies, b.p);

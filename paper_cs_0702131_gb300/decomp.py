@@ -16,9 +16,17 @@ The plan is derived here from the interaction lists of the whole mesh (the
 CSR arrays of ``aica_get_lists`` / ``Mesh.lists()``), so the paper's
 iterative referral between processors reduces to set operations: a referred
 cell is keyed by (source cell, n), which makes App. A.2's duplicate check
-hold by construction.  The kernels of this package run one processor per
-GPU; the exchange itself needs more than one GPU and is exercised on CPU
-ranks (gloo) in the tests.
+hold by construction.
+
+On the GPU a portion is evaluated by the library itself: every processor
+holds the whole mesh and its lists, bins its own molecules followed by the
+halo it received (the molecules of ``recv``'s cells, at their own
+positions) with the option ``n_owned`` set to the number of its own, and
+``aica_forces`` evaluates owned-owned pairs with Newton's third law and
+owned-halo pairs one-sidedly with half their energy and virial (the
+referred pairs of this plan).  The exchange between processors needs more
+than one GPU; it is exercised on CPU ranks (gloo) in the tests, and the GPU
+evaluation of every portion in one process.
 """
 from __future__ import annotations
 
@@ -101,6 +109,13 @@ def halo_plan(lists, part, rank):
     return dict(local=np.flatnonzero(part == rank), dil_a=a[both], dil_b=b[both], ref_src=src, ref_n=nvec,
                 ref_owner=owner, ref_off=off, ref_ids=np.concatenate(ids) if ids else np.zeros(0, np.int64),
                 recv=recv)
+
+
+def halo_molecules(plan, cell_of):
+    """Indices of the molecules `rank` receives (those of the cells in
+    plan["recv"]), from every molecule's cell."""
+    cells = np.concatenate(list(plan["recv"].values())) if plan["recv"] else np.zeros(0, np.int64)
+    return np.flatnonzero(np.isin(np.asarray(cell_of), cells))
 
 
 def send_lists(plans, rank):
