@@ -1662,99 +1662,98 @@ __device__ __forceinline__ int cell_in_cluster(const int *cell_off, int c0, int 
     return c - c0;
 }
 
-// One lane's survivor (xh, xl) against the tile (broadcast from shared
-// memory): the separation formed exactly and rounded once, r^2 < rc^2
-// decided in FP32 outside the 1e-5 rc^2 band (FP64 with the all-pairs
-// operation order inside it, after the pass), the force body skipped when
-// no lane of the warp is within rc.  SAME: own-cluster survivors pair only
-// with tile molecules of lower binned index.
+// One pair of the cluster kernel (FP32 body, branch-free): tile molecule t
+// (h, lo) against a lane's survivor (xh, xl); the force goes to fi[4t..] and
+// fj, |f|^2 to both .w/[4t+3], the energy to u_acc; FP32 r^2 within the
+// 1e-5 rc^2 band sets bit t of bm for the FP64 re-decision after the pass.
 template <bool MULTI, bool SHIFT, bool SAME, bool GHOST>
-__device__ __forceinline__ unsigned eval_tile(const PairArgs &a, const float4 *tab, const WarpC &w, int ni, int k0, float4 xh,
-                                              float4 xl, float (&fi)[4 * kNI], float4 &fj, float &u_acc,
-                                              unsigned &nsame, float *vg) {
-    unsigned nin = 0, bm = 0;
-    const float4 t0 = tab[0];
+__device__ __forceinline__ void tile_pair(const PairArgs &a, const float4 *tab, float4 t0, float4 h, float4 lo,
+                                          float4 xh, float4 xl, int t, int k0, bool force_in, float (&fi)[4 * kNI],
+                                          float4 &fj, float &u_acc, unsigned &nin, unsigned &nsame, unsigned &bm,
+                                          float *vg) {
     const int wj = __float_as_int(xh.w), l = __float_as_int(xl.w);
     const bool sj = SAME && (wj & kSameBit) != 0;
+    const float rx = (h.x - xh.x) + (lo.x - xl.x);
+    const float ry = (h.y - xh.y) + (lo.y - xl.y);
+    const float rz = (h.z - xh.z) + (lo.z - xl.z);
+    const float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
+    // portion mode: a pair of two halo molecules is not evaluated here,
+    // an owned-halo pair carries half its energy and virial
+    const bool gi = GHOST && (__float_as_int(h.w) & kGhostW), gj = GHOST && (wj & kGhostW);
+    const bool ok = (!sj || k0 + t < l) && !(gi && gj);
+    bool in;
+    if (force_in) {
+        in = true;
+    } else {
+        in = ok && r2 < a.rc2_lo;
+        if (ok && !in && r2 < a.rc2_hi) bm |= 1u << t;
+    }
+    float fs, u;
+    lj32<MULTI, SHIFT>(tab, t0, __float_as_int(h.w) & kSpBits, wj & kSpBits, r2, fs, u);
+    fs = in ? fs : 0.f;
+    const float wt = (gi || gj) ? 0.5f : 1.f;
+    u_acc += in ? (GHOST ? wt * u : u) : 0.f;
+    if (GHOST) {
+        const float g = wt * fs, gx = g * rx, gy = g * ry;
+        vg[0] = fmaf(gx, rx, vg[0]);
+        vg[1] = fmaf(gy, ry, vg[1]);
+        vg[2] = fmaf(g * rz, rz, vg[2]);
+        vg[3] = fmaf(gx, ry, vg[3]);
+        vg[4] = fmaf(gx, rz, vg[4]);
+        vg[5] = fmaf(gy, rz, vg[5]);
+    }
+    fi[4 * t] = fmaf(fs, rx, fi[4 * t]);
+    fi[4 * t + 1] = fmaf(fs, ry, fi[4 * t + 1]);
+    fi[4 * t + 2] = fmaf(fs, rz, fi[4 * t + 2]);
+    fj.x = fmaf(-fs, rx, fj.x);
+    fj.y = fmaf(-fs, ry, fj.y);
+    fj.z = fmaf(-fs, rz, fj.z);
+    const float g = fs * fs;
+    fi[4 * t + 3] = fmaf(g, r2, fi[4 * t + 3]);
+    fj.w = fmaf(g, r2, fj.w);
+    nin += in;
+    if (SAME) nsame += (in && sj && cellq_of(__float_as_int(h.w)) == cellq_of(wj)) ? 1u : 0u;
+}
+
+// NJ survivors per lane (xh[s], xl[s]) against the tile (broadcast from
+// shared memory, one load serving NJ pairs); after the pass, pairs whose
+// FP32 r^2 fell in the 1e-5 rc^2 band are re-decided in FP64 with the
+// all-pairs operation order.  SAME: own-cluster survivors pair only with
+// tile molecules of lower binned index.
+template <bool MULTI, bool SHIFT, bool SAME, bool GHOST, int NJ>
+__device__ __forceinline__ void eval_tile(const PairArgs &a, const float4 *tab, const WarpC &w, int ni, int k0,
+                                          const float4 (&xh)[NJ], const float4 (&xl)[NJ], float (&fi)[4 * kNI],
+                                          float4 (&fj)[NJ], float &u_acc, unsigned (&nin)[NJ],
+                                          unsigned (&nsame)[NJ], float *vg) {
+    unsigned bm[NJ];
+#pragma unroll
+    for (int q = 0; q < NJ; ++q) bm[q] = 0;
+    const float4 t0 = tab[0];
 #pragma unroll
     for (int t = 0; t < kNI; ++t) {
         if (t >= ni) break;
         const float4 h = lds4(&w.ih[t]), lo = lds4(&w.il[t]);
-        const float rx = (h.x - xh.x) + (lo.x - xl.x);
-        const float ry = (h.y - xh.y) + (lo.y - xl.y);
-        const float rz = (h.z - xh.z) + (lo.z - xl.z);
-        const float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
-        // portion mode: a pair of two halo molecules is not evaluated here,
-        // an owned-halo pair carries half its energy and virial
-        const bool gi = GHOST && (__float_as_int(h.w) & kGhostW), gj = GHOST && (wj & kGhostW);
-        const bool ok = (!sj || k0 + t < l) && !(gi && gj);
-        const bool in = ok && r2 < a.rc2_lo;
-        if (ok && !in && r2 < a.rc2_hi) bm |= 1u << t;
-        float fs, u;
-        lj32<MULTI, SHIFT>(tab, t0, __float_as_int(h.w) & kSpBits, wj & kSpBits, r2, fs, u);
-        fs = in ? fs : 0.f;
-        const float wt = (gi || gj) ? 0.5f : 1.f;
-        u_acc += in ? (GHOST ? wt * u : u) : 0.f;
-        if (GHOST) {
-            const float g = wt * fs, gx = g * rx, gy = g * ry;
-            vg[0] = fmaf(gx, rx, vg[0]);
-            vg[1] = fmaf(gy, ry, vg[1]);
-            vg[2] = fmaf(g * rz, rz, vg[2]);
-            vg[3] = fmaf(gx, ry, vg[3]);
-            vg[4] = fmaf(gx, rz, vg[4]);
-            vg[5] = fmaf(gy, rz, vg[5]);
-        }
-        fi[4 * t] = fmaf(fs, rx, fi[4 * t]);
-        fi[4 * t + 1] = fmaf(fs, ry, fi[4 * t + 1]);
-        fi[4 * t + 2] = fmaf(fs, rz, fi[4 * t + 2]);
-        fj.x = fmaf(-fs, rx, fj.x);
-        fj.y = fmaf(-fs, ry, fj.y);
-        fj.z = fmaf(-fs, rz, fj.z);
-        const float g = fs * fs;
-        fi[4 * t + 3] = fmaf(g, r2, fi[4 * t + 3]);
-        fj.w = fmaf(g, r2, fj.w);
-        nin += in;
-        if (SAME) nsame += (in && sj && cellq_of(__float_as_int(h.w)) == cellq_of(wj)) ? 1u : 0u;
-    }
-    if (__any_sync(0xffffffffu, bm != 0)) {
-        const int32_t np = n_of(wj);
 #pragma unroll
-        for (int t = 0; t < kNI; ++t) {
-            if (((bm >> t) & 1u) && band_in(a, k0 + t, l, np)) {
-                const float4 h = lds4(&w.ih[t]), lo = lds4(&w.il[t]);
-                const float rx = (h.x - xh.x) + (lo.x - xl.x);
-                const float ry = (h.y - xh.y) + (lo.y - xl.y);
-                const float rz = (h.z - xh.z) + (lo.z - xl.z);
-                const float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
-                float fs, u;
-                lj32<MULTI, SHIFT>(tab, t0, __float_as_int(h.w) & kSpBits, wj & kSpBits, r2, fs, u);
-                const bool gi = GHOST && (__float_as_int(h.w) & kGhostW), gj = GHOST && (wj & kGhostW);
-                const float wt = (gi || gj) ? 0.5f : 1.f;
-                u_acc += GHOST ? wt * u : u;
-                if (GHOST) {
-                    const float g = wt * fs, gx = g * rx, gy = g * ry;
-                    vg[0] = fmaf(gx, rx, vg[0]);
-                    vg[1] = fmaf(gy, ry, vg[1]);
-                    vg[2] = fmaf(g * rz, rz, vg[2]);
-                    vg[3] = fmaf(gx, ry, vg[3]);
-                    vg[4] = fmaf(gx, rz, vg[4]);
-                    vg[5] = fmaf(gy, rz, vg[5]);
+        for (int q = 0; q < NJ; ++q)
+            tile_pair<MULTI, SHIFT, SAME, GHOST>(a, tab, t0, h, lo, xh[q], xl[q], t, k0, false, fi, fj[q], u_acc,
+                                                 nin[q], nsame[q], bm[q], vg);
+    }
+#pragma unroll
+    for (int q = 0; q < NJ; ++q) {
+        if (__any_sync(0xffffffffu, bm[q] != 0)) {
+            const int wj = __float_as_int(xh[q].w), l = __float_as_int(xl[q].w);
+            const int32_t np = n_of(wj);
+            unsigned dummy = 0;
+#pragma unroll
+            for (int t = 0; t < kNI; ++t) {
+                if (((bm[q] >> t) & 1u) && band_in(a, k0 + t, l, np)) {
+                    const float4 h = w.ih[t], lo = w.il[t];
+                    tile_pair<MULTI, SHIFT, SAME, GHOST>(a, tab, t0, h, lo, xh[q], xl[q], t, k0, true, fi, fj[q], u_acc,
+                                                         nin[q], nsame[q], dummy, vg);
                 }
-                fi[4 * t] = fmaf(fs, rx, fi[4 * t]);
-                fi[4 * t + 1] = fmaf(fs, ry, fi[4 * t + 1]);
-                fi[4 * t + 2] = fmaf(fs, rz, fi[4 * t + 2]);
-                fj.x = fmaf(-fs, rx, fj.x);
-                fj.y = fmaf(-fs, ry, fj.y);
-                fj.z = fmaf(-fs, rz, fj.z);
-                const float g = fs * fs;
-                fi[4 * t + 3] = fmaf(g, r2, fi[4 * t + 3]);
-                fj.w = fmaf(g, r2, fj.w);
-                nin++;
-                if (sj && cellq_of(__float_as_int(h.w)) == cellq_of(wj)) nsame++;
             }
         }
     }
-    return nin;
 }
 
 // Sum v[0..4 kNI) (kNI groups of x, y, z, |f|^2) over the warp by recursive
@@ -1859,31 +1858,43 @@ __global__ void __launch_bounds__(kCT, MINB) pair_fwd32c(PairArgs a, ClKArgs c) 
 #pragma unroll
                 for (int i = 0; i < 4 * kNI; ++i) fi[i] = 0.f;
                 __syncwarp();
-                for (int jb = 0; jb < nq; jb += 32) {
-                    const int j = jb + lane;
-                    const bool valid = j < nq;
-                    const float4 xh = valid ? w.sh[j] : make_float4(-1e18f, -1e18f, -1e18f, 0.f);
-                    const float4 xl = valid ? w.sl[j] : zero4;
-                    float4 fj = zero4;
-                    unsigned nin, nsame = 0;
-                    const bool same = (__float_as_int(xh.w) & kSameBit) != 0;
-                    if (__any_sync(FULL, same))
-                        nin = eval_tile<MULTI, SHIFT, true, GHOST>(a, tab, w, ni, k0, xh, xl, fi, fj, u_acc, nsame, vg);
+                constexpr int NJ = 1;
+                for (int jb = 0; jb < nq; jb += 32 * NJ) {
+                    float4 xh[NJ], xl[NJ], fj[NJ];
+                    unsigned nin[NJ], nsame[NJ];
+                    bool any_same = false;
+#pragma unroll
+                    for (int q = 0; q < NJ; ++q) {
+                        const int j = jb + 32 * q + lane;
+                        const bool valid = j < nq;
+                        xh[q] = valid ? w.sh[j] : make_float4(-1e18f, -1e18f, -1e18f, 0.f);
+                        xl[q] = valid ? w.sl[j] : zero4;
+                        fj[q] = zero4;
+                        nin[q] = nsame[q] = 0;
+                        any_same |= (__float_as_int(xh[q].w) & kSameBit) != 0;
+                    }
+                    if (__any_sync(FULL, any_same))
+                        eval_tile<MULTI, SHIFT, true, GHOST, NJ>(a, tab, w, ni, k0, xh, xl, fi, fj, u_acc, nin, nsame, vg);
                     else
-                        nin = eval_tile<MULTI, SHIFT, false, GHOST>(a, tab, w, ni, k0, xh, xl, fi, fj, u_acc, nsame, vg);
-                    if (valid && nin) {
-                        // within-rc counts per category (same cell, DIL, periodic image), per lane
-                        if (same) {
-                            wc0 += nsame;
-                            wc1 += nin - nsame;
-                        } else if (__float_as_int(xh.w) & kImgBit) {
-                            wc2 += nin;
-                        } else {
-                            wc1 += nin;
+                        eval_tile<MULTI, SHIFT, false, GHOST, NJ>(a, tab, w, ni, k0, xh, xl, fi, fj, u_acc, nin, nsame, vg);
+#pragma unroll
+                    for (int q = 0; q < NJ; ++q) {
+                        const int j = jb + 32 * q + lane;
+                        if (j < nq && nin[q]) {
+                            // within-rc counts per category (same cell, DIL, periodic image), per lane
+                            const int wq = __float_as_int(xh[q].w);
+                            if (wq & kSameBit) {
+                                wc0 += nsame[q];
+                                wc1 += nin[q] - nsame[q];
+                            } else if (wq & kImgBit) {
+                                wc2 += nin[q];
+                            } else {
+                                wc1 += nin[q];
+                            }
+                            float4 f = w.sf[j];
+                            f.x += fj[q].x; f.y += fj[q].y; f.z += fj[q].z; f.w += fj[q].w;
+                            w.sf[j] = f;
                         }
-                        float4 f = w.sf[j];
-                        f.x += fj.x; f.y += fj.y; f.z += fj.z; f.w += fj.w;
-                        w.sf[j] = f;
                     }
                 }
                 tile_reduce4(fi, lane);
