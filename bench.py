@@ -329,7 +329,8 @@ def run_ours(args):
         kmean = statistics.mean(kms)
         achieved = flops / (kmean * 1e-3) / 1e12
         peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
-        roof = {"kernel": "pair_fwd32", "bound": "alu", "achieved": round(achieved, 3),
+        kname = "pair_fwd32c" if mesh.get_option("cluster_path") else "pair_fwd32"
+        roof = {"kernel": kname, "bound": "alu", "achieved": round(achieved, 3),
                 "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
                 "traffic": None, "kernel_ms": round(kmean, 5), "launches_timed": len(kms),
                 "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz",
@@ -356,7 +357,7 @@ def run_ours(args):
                            "spheres), CUDA graph, L2 flushed, position sets alternating"}
         # DRAM bytes per launch of this kernel from the committed ncu summary
         # (dram__bytes_read.sum + dram__bytes_write.sum), if one exists for it
-        prof = os.path.join(ROOT, "profiles", f"pair_fwd32_{args.config}.md")
+        prof = os.path.join(ROOT, "profiles", f"{kname}_{args.config}.md")
         if os.path.exists(prof):
             for line in open(prof):
                 if line.startswith("| traffic_bytes_per_launch |"):
@@ -378,6 +379,10 @@ def run_ours(args):
                                                   "within_dil", "within_ref"]},
                "energy_per_molecule": ev_main[0] / n,
                "fp32_refined_molecules": refined,
+               "precision": ("pair arithmetic FP32 (separations rounded once); energy and virial sums and the "
+                             "cut-off decisions within 1e-5 rc^2 of rc in FP64; molecules whose FP32 force the "
+                             "error bound cannot certify to 1e-5 of max(|F_ic|, ||F_i||) recomputed in "
+                             f"double-single arithmetic ({refined} of {n} here), inside the timed step"),
                "gpu_launches": int(launches["fp32"]) * args.steps,
                "launches_per_step": int(launches["fp32"]),
                "roofline": roof, "binning": binning, "clocks": clk,
