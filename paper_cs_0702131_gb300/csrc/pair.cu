@@ -1622,7 +1622,7 @@ constexpr int kCT = 128, kCW = kCT / 32;
 // kRefineScale bounds that multiple with a wide safety margin.  A molecule
 // whose force is below kRefineScale / tol times that scale gets refined.
 constexpr double kRefineScale = 1.25e-6;
-constexpr int kCap = 256;                 // survivors buffered per warp
+constexpr int kCap = 240;                 // survivors buffered per warp
 constexpr int kNI = 8;                    // molecules of A per i-tile
 // packed survivor / tile word (.w of the hi position)
 constexpr int kSpBits = 7, kSameBit = 1 << 3, kImgBit = 1 << 4, kGhostW = 1 << 21;
@@ -1641,7 +1641,7 @@ struct WarpC {
     float4 ed[32], el[32];
     int eb[32];
     float box[6];         // joint box of A's molecules (lo, hi)
-    float vir[6];         // FP32 virial of the current cluster
+    float vl[6][32];      // per-lane virial sums (xx, yy, zz, xy, xz, yz) of the current cluster
     unsigned cnt[2];      // pair tests, culling tests
 };
 
@@ -1664,14 +1664,16 @@ __device__ __forceinline__ int cell_in_cluster(const int *cell_off, int c0, int 
 
 // One pair of the cluster kernel (FP32 body, branch-free): tile molecule t
 // (h, lo) against a lane's survivor (xh, xl); the force goes to fi[4t..] and
-// fj, |f|^2 to both .w/[4t+3], the energy to u_acc; FP32 r^2 within the
-// 1e-5 rc^2 band sets bit t of bm for the FP64 re-decision after the pass.
+// fj, |f|^2 to both .w/[4t+3], the energy to u_acc; a pair whose FP32 r^2
+// falls within the 1e-5 rc^2 band sets bit t of bm for the FP64 re-decision
+// after the tile (band_pair).  Pairs outside rc get 1/r^2 = 0, which zeroes
+// their force and energy without further selects: u = 4 eps (s^6 - s^3).
 template <bool MULTI, bool SHIFT, bool SAME, bool GHOST>
 __device__ __forceinline__ void tile_pair(const PairArgs &a, const float4 *tab, float4 t0, float4 h, float4 lo,
-                                          float4 xh, float4 xl, int t, int k0, bool force_in, float (&fi)[4 * kNI],
+                                          float4 xh, float4 xl, int t, int k0, float (&fi)[4 * kNI],
                                           float4 &fj, float &u_acc, unsigned &nin, unsigned &nsame, unsigned &bm,
-                                          float *vg) {
-    const int wj = __float_as_int(xh.w), l = __float_as_int(xl.w);
+                                          float (&vg)[6]) {
+    const int wi = __float_as_int(h.w), wj = __float_as_int(xh.w), l = __float_as_int(xl.w);
     const bool sj = SAME && (wj & kSameBit) != 0;
     const float rx = (h.x - xh.x) + (lo.x - xl.x);
     const float ry = (h.y - xh.y) + (lo.y - xl.y);
@@ -1679,20 +1681,19 @@ __device__ __forceinline__ void tile_pair(const PairArgs &a, const float4 *tab, 
     const float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
     // portion mode: a pair of two halo molecules is not evaluated here,
     // an owned-halo pair carries half its energy and virial
-    const bool gi = GHOST && (__float_as_int(h.w) & kGhostW), gj = GHOST && (wj & kGhostW);
+    const bool gi = GHOST && (wi & kGhostW), gj = GHOST && (wj & kGhostW);
     const bool ok = (!sj || k0 + t < l) && !(gi && gj);
-    bool in;
-    if (force_in) {
-        in = true;
-    } else {
-        in = ok && r2 < a.rc2_lo;
-        if (ok && !in && r2 < a.rc2_hi) bm |= 1u << t;
-    }
-    float fs, u;
-    lj32<MULTI, SHIFT>(tab, t0, __float_as_int(h.w) & kSpBits, wj & kSpBits, r2, fs, u);
-    fs = in ? fs : 0.f;
-    const float wt = (gi || gj) ? 0.5f : 1.f;
-    u_acc += in ? (GHOST ? wt * u : u) : 0.f;
+    const bool in = ok && r2 < a.rc2_lo;
+    if (ok && !in && r2 < a.rc2_hi) bm |= 1u << t;
+    const float4 p = MULTI ? tab[(wi & kSpBits) * kMaxSpecies + (wj & kSpBits)] : t0;
+    const float inv = in ? rcp_approx(r2) : 0.f;      // (r^2 = 0 for a molecule against itself)
+    const float s = p.x * inv;
+    const float s3 = s * s * s;
+    const float fs = (p.y * inv) * s3 * fmaf(2.f, s3, -1.f);
+    const float v = fmaf(s3, s3, -s3);
+    const float wt = (GHOST && (gi || gj)) ? 0.5f : 1.f;
+    u_acc = fmaf(GHOST ? wt * p.z : p.z, v, u_acc);
+    if (SHIFT) u_acc -= in ? (GHOST ? wt * p.w : p.w) : 0.f;
     if (GHOST) {
         const float g = wt * fs, gx = g * rx, gy = g * ry;
         vg[0] = fmaf(gx, rx, vg[0]);
@@ -1712,47 +1713,88 @@ __device__ __forceinline__ void tile_pair(const PairArgs &a, const float4 *tab, 
     fi[4 * t + 3] = fmaf(g, r2, fi[4 * t + 3]);
     fj.w = fmaf(g, r2, fj.w);
     nin += in;
-    if (SAME) nsame += (in && sj && cellq_of(__float_as_int(h.w)) == cellq_of(wj)) ? 1u : 0u;
+    if (SAME) nsame += (in && sj && cellq_of(wi) == cellq_of(wj)) ? 1u : 0u;
 }
 
-// NJ survivors per lane (xh[s], xl[s]) against the tile (broadcast from
-// shared memory, one load serving NJ pairs); after the pass, pairs whose
-// FP32 r^2 fell in the 1e-5 rc^2 band are re-decided in FP64 with the
-// all-pairs operation order.  SAME: own-cluster survivors pair only with
-// tile molecules of lower binned index.
-template <bool MULTI, bool SHIFT, bool SAME, bool GHOST, int NJ>
+// x (x) f added to the virial sums v[0], v[S], .. v[5 S] (xx, yy, zz, xy, xz, yz)
+template <int S = 1>
+__device__ __forceinline__ void vir_add(float *v, float x, float y, float z, float fx, float fy, float fz) {
+    v[0] = fmaf(x, fx, v[0]);
+    v[S] = fmaf(y, fy, v[S]);
+    v[2 * S] = fmaf(z, fz, v[2 * S]);
+    v[3 * S] = fmaf(x, fy, v[3 * S]);
+    v[4 * S] = fmaf(x, fz, v[4 * S]);
+    v[5 * S] = fmaf(y, fz, v[5 * S]);
+}
+
+// A pair of the 1e-5 rc^2 band that the FP64 decision puts within rc: the
+// body of tile_pair with the pair inside, the tile molecule's force added
+// to its accumulator at once (rare; one copy of the body in the code).
+template <bool MULTI, bool SHIFT, bool SAME, bool GHOST>
+__device__ __forceinline__ void band_pair(const PairArgs &a, const float4 *tab, float4 t0, float4 h, float4 lo,
+                                       float4 xh, float4 xl, float4 &fj, float &u_acc, unsigned &nin,
+                                       unsigned &nsame, float (&vg)[6], float *vl, float4 *fdst) {
+    const int wi = __float_as_int(h.w), wj = __float_as_int(xh.w);
+    const bool sj = SAME && (wj & kSameBit) != 0;
+    const float rx = (h.x - xh.x) + (lo.x - xl.x);
+    const float ry = (h.y - xh.y) + (lo.y - xl.y);
+    const float rz = (h.z - xh.z) + (lo.z - xl.z);
+    const float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
+    const bool gi = GHOST && (wi & kGhostW), gj = GHOST && (wj & kGhostW);
+    const float4 p = MULTI ? tab[(wi & kSpBits) * kMaxSpecies + (wj & kSpBits)] : t0;
+    const float inv = rcp_approx(r2);
+    const float s = p.x * inv;
+    const float s3 = s * s * s;
+    const float fs = (p.y * inv) * s3 * fmaf(2.f, s3, -1.f);
+    const float wt = (GHOST && (gi || gj)) ? 0.5f : 1.f;
+    u_acc = fmaf(GHOST ? wt * p.z : p.z, fmaf(s3, s3, -s3), u_acc);
+    if (SHIFT) u_acc -= GHOST ? wt * p.w : p.w;
+    const float fx = fs * rx, fy = fs * ry, fz = fs * rz, g = fs * fs * r2;
+    fj.x -= fx;
+    fj.y -= fy;
+    fj.z -= fz;
+    fj.w += g;
+    atomicAdd(fdst, make_float4(fx, fy, fz, g));
+    if (GHOST) {
+        const float q = wt * fs, gx = q * rx, gy = q * ry;
+        vg[0] = fmaf(gx, rx, vg[0]);
+        vg[1] = fmaf(gy, ry, vg[1]);
+        vg[2] = fmaf(q * rz, rz, vg[2]);
+        vg[3] = fmaf(gx, ry, vg[3]);
+        vg[4] = fmaf(gx, rz, vg[4]);
+        vg[5] = fmaf(gy, rz, vg[5]);
+    } else {
+        vir_add<32>(vl, h.x, h.y, h.z, fx, fy, fz);     // the force issued on the tile molecule
+    }
+    nin += 1u;
+    if (SAME) nsame += (sj && cellq_of(wi) == cellq_of(wj)) ? 1u : 0u;
+}
+
+// A lane's survivor (xh, xl) against the tile (broadcast from shared
+// memory); afterwards the pairs whose FP32 r^2 fell in the 1e-5 rc^2 band
+// are re-decided in FP64 with the all-pairs operation order.  SAME:
+// own-cluster survivors pair only with tile molecules of lower binned index.
+template <bool MULTI, bool SHIFT, bool SAME, bool GHOST>
 __device__ __forceinline__ void eval_tile(const PairArgs &a, const float4 *tab, const WarpC &w, int ni, int k0,
-                                          const float4 (&xh)[NJ], const float4 (&xl)[NJ], float (&fi)[4 * kNI],
-                                          float4 (&fj)[NJ], float &u_acc, unsigned (&nin)[NJ],
-                                          unsigned (&nsame)[NJ], float *vg) {
-    unsigned bm[NJ];
-#pragma unroll
-    for (int q = 0; q < NJ; ++q) bm[q] = 0;
+                                          float4 xh, float4 xl, float (&fi)[4 * kNI], float4 &fj, float &u_acc,
+                                          unsigned &nin, unsigned &nsame, float (&vg)[6], float *vl,
+                                          float4 *facc) {
+    unsigned bm = 0;
     const float4 t0 = tab[0];
 #pragma unroll
     for (int t = 0; t < kNI; ++t) {
         if (t >= ni) break;
         const float4 h = lds4(&w.ih[t]), lo = lds4(&w.il[t]);
-#pragma unroll
-        for (int q = 0; q < NJ; ++q)
-            tile_pair<MULTI, SHIFT, SAME, GHOST>(a, tab, t0, h, lo, xh[q], xl[q], t, k0, false, fi, fj[q], u_acc,
-                                                 nin[q], nsame[q], bm[q], vg);
+        tile_pair<MULTI, SHIFT, SAME, GHOST>(a, tab, t0, h, lo, xh, xl, t, k0, fi, fj, u_acc, nin, nsame, bm, vg);
     }
-#pragma unroll
-    for (int q = 0; q < NJ; ++q) {
-        if (__any_sync(0xffffffffu, bm[q] != 0)) {
-            const int wj = __float_as_int(xh[q].w), l = __float_as_int(xl[q].w);
-            const int32_t np = n_of(wj);
-            unsigned dummy = 0;
-#pragma unroll
-            for (int t = 0; t < kNI; ++t) {
-                if (((bm[q] >> t) & 1u) && band_in(a, k0 + t, l, np)) {
-                    const float4 h = w.ih[t], lo = w.il[t];
-                    tile_pair<MULTI, SHIFT, SAME, GHOST>(a, tab, t0, h, lo, xh[q], xl[q], t, k0, true, fi, fj[q], u_acc,
-                                                         nin[q], nsame[q], dummy, vg);
-                }
-            }
-        }
+    if (__any_sync(0xffffffffu, bm != 0)) {
+        const int l = __float_as_int(xl.w);
+        const int32_t np = n_of(__float_as_int(xh.w));
+#pragma unroll 1
+        for (int t = 0; t < ni; ++t)
+            if (((bm >> t) & 1u) && band_in(a, k0 + t, l, np))
+                band_pair<MULTI, SHIFT, SAME, GHOST>(a, tab, t0, w.ih[t], w.il[t], xh, xl, fj, u_acc, nin, nsame, vg,
+                                                     vl, facc + k0 + t);
     }
 }
 
@@ -1767,6 +1809,7 @@ __device__ __forceinline__ void tile_reduce4(float (&v)[4 * kNI], int lane) {
 #pragma unroll
         for (int i = 0; i < 4; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
 }
+
 template <bool MULTI, bool SHIFT, bool GHOST, int MINB>
 __global__ void __launch_bounds__(kCT, MINB) pair_fwd32c(PairArgs a, ClKArgs c) {
     extern __shared__ float4 csh[];
@@ -1778,7 +1821,6 @@ __global__ void __launch_bounds__(kCT, MINB) pair_fwd32c(PairArgs a, ClKArgs c) 
     WarpC &w = wsh[wib];
     if (lane < 8) dsums[wib][lane] = 0.0;
     if (lane < 2) w.cnt[lane] = 0;
-    if (lane < 6) w.vir[lane] = 0.f;
     __syncthreads();
     const unsigned FULL = 0xffffffffu, lt = (1u << lane) - 1u, le = FULL >> (31 - lane);
     const float4 far = make_float4(1e18f, 1e18f, 1e18f, 0.f), zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1787,19 +1829,15 @@ __global__ void __launch_bounds__(kCT, MINB) pair_fwd32c(PairArgs a, ClKArgs c) 
     float4 *facc = (float4 *)a.facc;
     double *dsum = dsums[wib];
     float u_acc = 0.f;
-    float vg[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // portion mode: virial summed per pair
-    unsigned wc0 = 0, wc1 = 0, wc2 = 0;     // this lane's pairs within rc: same cell, DIL, image
-    // virial terms of a tile's or survivors' forces: per lane in FP32, then to the warp's sums
-    auto add_vir = [&](float x, float y, float z, float fx, float fy, float fz) {
-        if (GHOST) return;          // summed per pair instead
-        float q[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        outer7(q, x, y, z, fx, fy, fz);
+    // virial: sum of x (x) F over the forces this lane issues (positions in
+    // the cluster's frame; the forces of a cluster sum to zero, so this is
+    // the sum of r (x) f over its pairs), in the lane's column vl of shared
+    // memory; portion mode sums r (x) f per pair in registers (vg)
+    float vg[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float *vl = &w.vl[0][lane];
 #pragma unroll
-        for (int i = 1; i < 7; ++i) {
-            const float s = warp_sum(q[i]);
-            if (lane == 0) w.vir[i - 1] += s;
-        }
-    };
+    for (int i = 0; i < 6; ++i) vl[32 * i] = 0.f;
+    unsigned wc0 = 0, wc1 = 0, wc2 = 0;     // this lane's pairs within rc: same cell, DIL, image
     for (;;) {
         int A = lane == 0 ? (int)atomicAdd(a.next_cell, 1u) : 0;
         A = __shfl_sync(FULL, A, 0);
@@ -1814,7 +1852,7 @@ __global__ void __launch_bounds__(kCT, MINB) pair_fwd32c(PairArgs a, ClKArgs c) 
             continue;
         }
         // 1. joint box of A's molecules (hi parts; the remainders lie inside the margins)
-        float bl[3] = {1e30f, 1e30f, 1e30f}, bh[3] = {-1e30f, -1e30f, -1e30f};   // to shared memory below
+        float bl[3] = {1e30f, 1e30f, 1e30f}, bh[3] = {-1e30f, -1e30f, -1e30f};
         for (int k = s0 + lane; k < s1; k += 32) {
             const float4 x = a.xloc[k];
             bl[0] = fminf(bl[0], x.x); bl[1] = fminf(bl[1], x.y); bl[2] = fminf(bl[2], x.z);
@@ -1837,89 +1875,7 @@ __global__ void __launch_bounds__(kCT, MINB) pair_fwd32c(PairArgs a, ClKArgs c) 
         }
         __syncwarp();
         int nq = 0;
-        // 3./4. every tile of A against the buffered survivors, then their reactions
-        auto flush = [&]() {
-            __syncwarp();
-            for (int i0 = 0; i0 < nA; i0 += kNI) {
-                const int ni = min(kNI, nA - i0), k0 = s0 + i0;
-                if (lane < kNI) {
-                    float4 h = make_float4(1e18f, 1e18f, 1e18f, 0.f), lo = zero4;
-                    if (lane < ni) {
-                        grid_split(a.xloc[k0 + lane], c.xlo[k0 + lane], c.qround, h, lo);
-                        const int q = cell_in_cluster(a.cell_off, c0, c1, k0 + lane);
-                        const int w0 = __float_as_int(h.w);
-                        h.w = __int_as_float((w0 & kSpBits) | (q << 5) | ((w0 & kGhostBit) ? kGhostW : 0));
-                    }
-                    w.ih[lane] = h;
-                    w.il[lane] = lo;
-                }
-                if (lane == 0) w.cnt[0] += (unsigned)(nq * ni);
-                float fi[4 * kNI];
-#pragma unroll
-                for (int i = 0; i < 4 * kNI; ++i) fi[i] = 0.f;
-                __syncwarp();
-                constexpr int NJ = 1;
-                for (int jb = 0; jb < nq; jb += 32 * NJ) {
-                    float4 xh[NJ], xl[NJ], fj[NJ];
-                    unsigned nin[NJ], nsame[NJ];
-                    bool any_same = false;
-#pragma unroll
-                    for (int q = 0; q < NJ; ++q) {
-                        const int j = jb + 32 * q + lane;
-                        const bool valid = j < nq;
-                        xh[q] = valid ? w.sh[j] : make_float4(-1e18f, -1e18f, -1e18f, 0.f);
-                        xl[q] = valid ? w.sl[j] : zero4;
-                        fj[q] = zero4;
-                        nin[q] = nsame[q] = 0;
-                        any_same |= (__float_as_int(xh[q].w) & kSameBit) != 0;
-                    }
-                    if (__any_sync(FULL, any_same))
-                        eval_tile<MULTI, SHIFT, true, GHOST, NJ>(a, tab, w, ni, k0, xh, xl, fi, fj, u_acc, nin, nsame, vg);
-                    else
-                        eval_tile<MULTI, SHIFT, false, GHOST, NJ>(a, tab, w, ni, k0, xh, xl, fi, fj, u_acc, nin, nsame, vg);
-#pragma unroll
-                    for (int q = 0; q < NJ; ++q) {
-                        const int j = jb + 32 * q + lane;
-                        if (j < nq && nin[q]) {
-                            // within-rc counts per category (same cell, DIL, periodic image), per lane
-                            const int wq = __float_as_int(xh[q].w);
-                            if (wq & kSameBit) {
-                                wc0 += nsame[q];
-                                wc1 += nin[q] - nsame[q];
-                            } else if (wq & kImgBit) {
-                                wc2 += nin[q];
-                            } else {
-                                wc1 += nin[q];
-                            }
-                            float4 f = w.sf[j];
-                            f.x += fj[q].x; f.y += fj[q].y; f.z += fj[q].z; f.w += fj[q].w;
-                            w.sf[j] = f;
-                        }
-                    }
-                }
-                tile_reduce4(fi, lane);
-                const int t = lane >> 2;
-                const bool mine = (lane & 3) == 0 && t < ni;
-                if (mine) atomicAdd(facc + k0 + t, make_float4(fi[0], fi[1], fi[2], fi[3]));
-                const float4 x = w.ih[t];
-                add_vir(x.x, x.y, x.z, mine ? fi[0] : 0.f, mine ? fi[1] : 0.f, mine ? fi[2] : 0.f);
-                __syncwarp();
-            }
-            // survivors' reactions (and the survivor side of the virial, in A's frame)
-            for (int j0 = 0; j0 < nq; j0 += 32) {
-                const int j = j0 + lane;
-                float4 f = zero4, x = zero4;
-                if (j < nq) {
-                    f = w.sf[j];
-                    x = w.sh[j];
-                    if (f.x != 0.f || f.y != 0.f || f.z != 0.f || f.w != 0.f) atomicAdd(facc + __float_as_int(w.sl[j].w), f);
-                }
-                add_vir(x.x, x.y, x.z, f.x, f.y, f.z);
-            }
-            __syncwarp();
-            nq = 0;
-        };
-        // append the live lanes' candidates to the buffer; flush when it cannot take 32 more
+        // append the live lanes' candidates to the buffer
         auto push = [&](bool alive, float4 xh, float4 xl) {
             const unsigned bal = __ballot_sync(FULL, alive);
             if (alive) {
@@ -1929,101 +1885,189 @@ __global__ void __launch_bounds__(kCT, MINB) pair_fwd32c(PairArgs a, ClKArgs c) 
                 w.sf[sl] = zero4;
             }
             nq += __popc(bal);
-            if (nq > kCap - 32) flush();
         };
-        // 2a. A's own molecules: pairs k < l inside the cluster
-        for (int k = s0 + lane; k - lane < s1; k += 32) {
-            const bool alive = k < s1;
-            float4 xh = far, xl = zero4;
-            if (alive) {
-                grid_split(a.xloc[k], c.xlo[k], c.qround, xh, xl);
-                const int q = cell_in_cluster(a.cell_off, c0, c1, k);
-                const int w0 = __float_as_int(xh.w);
-                xh.w = __int_as_float((w0 & kSpBits) | kSameBit | (q << 5) | ((w0 & kGhostBit) ? kGhostW : 0));
-                xl.w = __int_as_float(k);
-            }
-            push(alive, xh, xl);
-        }
-        // 2b. partner runs, 32 at a time: culled against A's box, compacted, expanded
-        const int e0 = c.cl_run_off[A], e1 = c.cl_run_off[A + 1];
-        for (int eb = e0; eb < e1; eb += 32) {
-            const bool has = eb + lane < e1;
-            int js = 0, n = 0;
-            ClRun r;
-            r.dh = zero4;
-            r.dl = zero4;
-            if (has) {
-                r = c.runs[eb + lane];
-                const int cf = __float_as_int(r.dh.w), code = __float_as_int(r.dl.w);
-                js = a.cell_off[cf];
-                n = a.cell_off[cf + (code & 4095)] - js;
-            }
-            int inc = n;
+        // 2. fill the buffer (A's own molecules, then the partner runs 32 at
+        // a time) until it cannot take 32 more; 3./4. evaluate it; repeat
+        int own = s0;                               // next own molecule to push
+        const int e1 = c.cl_run_off[A + 1];
+        int eb = c.cl_run_off[A];                   // next batch of 32 runs
+        int p0 = 0, total = 0, inc = 0;             // candidate cursor of the loaded batch
+        bool live = false;
+        for (;;) {
+            bool more = true;
+            while (nq <= kCap - 32) {
+                if (own < s1) {
+                    // 2a. A's own molecules: pairs k < l inside the cluster
+                    const int k = own + lane;
+                    const bool alive = k < s1;
+                    float4 xh = far, xl = zero4;
+                    if (alive) {
+                        grid_split(a.xloc[k], c.xlo[k], c.qround, xh, xl);
+                        const int q = cell_in_cluster(a.cell_off, c0, c1, k);
+                        const int w0 = __float_as_int(xh.w);
+                        xh.w = __int_as_float((w0 & kSpBits) | kSameBit | (q << 5) | ((w0 & kGhostBit) ? kGhostW : 0));
+                        xl.w = __int_as_float(k);
+                    }
+                    push(alive, xh, xl);
+                    own += 32;
+                } else if (p0 < total) {
+                    // 2b. candidates p0 .. p0 + 31 of the loaded runs: moved into
+                    // A's frame, culled against A's box, compacted
+                    const int b = inc - p0;
+                    const int base = __popc(__ballot_sync(FULL, live && b <= 0));
+                    const unsigned M = __reduce_or_sync(FULL, (live && b > 0 && b < 32) ? (1u << b) : 0u);
+                    const int p = p0 + lane;
+                    bool alive = false;
+                    float4 xh = far, xl = zero4;
+                    if (p < total) {
+                        const int o = base + __popc(M & le);
+                        const int l = p + w.eb[o];
+                        const float4 dh = w.ed[o], dl = w.el[o];
+                        float4 x, y;
+                        grid_split(a.xloc[l], c.xlo[l], c.qround, x, y);
+                        xh = make_float4(x.x + dh.x, x.y + dh.y, x.z + dh.z, 0.f);
+                        const float dx = fmaxf(fmaxf(w.box[0] - xh.x, xh.x - w.box[3]), 0.f);
+                        const float dy = fmaxf(fmaxf(w.box[1] - xh.y, xh.y - w.box[4]), 0.f);
+                        const float dz = fmaxf(fmaxf(w.box[2] - xh.z, xh.z - w.box[5]), 0.f);
+                        alive = dx * dx + dy * dy + dz * dz <= rcut2;
+                        const int code = __float_as_int(dl.w) >> 12;
+                        const int w0 = __float_as_int(x.w);
+                        xh.w = __int_as_float((w0 & kSpBits) | (code != 0 ? kImgBit : 0) | (code << 9) |
+                                              ((w0 & kGhostBit) ? kGhostW : 0));
+                        xl = make_float4(y.x + dl.x, y.y + dl.y, y.z + dl.z, __int_as_float(l));
+                    }
+                    push(alive, xh, xl);
+                    p0 += 32;
+                } else if (eb < e1) {
+                    // the next 32 partner runs: candidate counts prefix-summed,
+                    // live runs compacted into ed / el / eb
+                    const bool has = eb + lane < e1;
+                    int js = 0, n = 0;
+                    ClRun r;
+                    r.dh = zero4;
+                    r.dl = zero4;
+                    if (has) {
+                        r = c.runs[eb + lane];
+                        const int cf = __float_as_int(r.dh.w), code = __float_as_int(r.dl.w);
+                        js = a.cell_off[cf];
+                        n = a.cell_off[cf + (code & 4095)] - js;
+                    }
+                    inc = n;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(FULL, inc, o);
-                if (lane >= o) inc += y;
-            }
-            const int total = __shfl_sync(FULL, inc, 31);
-            const bool live = n > 0;
-            const unsigned lbal = __ballot_sync(FULL, live);
-            if (live) {
-                const int sl = __popc(lbal & lt);
-                w.ed[sl] = r.dh;
-                w.el[sl] = r.dl;
-                w.eb[sl] = js - (inc - n);
-            }
-            if (lane == 0) w.cnt[1] += (unsigned)total;
-            __syncwarp();
-            for (int p0 = 0; p0 < total; p0 += 32) {
-                // run holding candidate p = p0 + lane: the live runs ending at or before p
-                const int b = inc - p0;
-                const int base = __popc(__ballot_sync(FULL, live && b <= 0));
-                const unsigned M = __reduce_or_sync(FULL, (live && b > 0 && b < 32) ? (1u << b) : 0u);
-                const int p = p0 + lane;
-                bool alive = false;
-                float4 xh = far, xl = zero4;
-                if (p < total) {
-                    const int o = base + __popc(M & le);
-                    const int l = p + w.eb[o];
-                    const float4 dh = w.ed[o], dl = w.el[o];
-                    float4 x, y;
-                    grid_split(a.xloc[l], c.xlo[l], c.qround, x, y);
-                    xh = make_float4(x.x + dh.x, x.y + dh.y, x.z + dh.z, 0.f);
-                    const float dx = fmaxf(fmaxf(w.box[0] - xh.x, xh.x - w.box[3]), 0.f);
-                    const float dy = fmaxf(fmaxf(w.box[1] - xh.y, xh.y - w.box[4]), 0.f);
-                    const float dz = fmaxf(fmaxf(w.box[2] - xh.z, xh.z - w.box[5]), 0.f);
-                    alive = dx * dx + dy * dy + dz * dz <= rcut2;
-                    const int code = __float_as_int(dl.w) >> 12;
-                    const int w0 = __float_as_int(x.w);
-                    xh.w = __int_as_float((w0 & kSpBits) | (code != 0 ? kImgBit : 0) | (code << 9) |
-                                          ((w0 & kGhostBit) ? kGhostW : 0));
-                    xl = make_float4(y.x + dl.x, y.y + dl.y, y.z + dl.z, __int_as_float(l));
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int y = __shfl_up_sync(FULL, inc, o);
+                        if (lane >= o) inc += y;
+                    }
+                    total = __shfl_sync(FULL, inc, 31);
+                    live = n > 0;
+                    const unsigned lbal = __ballot_sync(FULL, live);
+                    __syncwarp();                       // the previous runs' readers are done
+                    if (live) {
+                        const int sl = __popc(lbal & lt);
+                        w.ed[sl] = r.dh;
+                        w.el[sl] = r.dl;
+                        w.eb[sl] = js - (inc - n);
+                    }
+                    if (lane == 0) w.cnt[1] += (unsigned)total;
+                    __syncwarp();
+                    eb += 32;
+                    p0 = 0;
+                } else {
+                    more = false;
+                    break;
                 }
-                push(alive, xh, xl);
             }
-            __syncwarp();
+            if (nq > 0) {
+                // 3. every tile of A against the buffered survivors
+                __syncwarp();
+                for (int i0 = 0; i0 < nA; i0 += kNI) {
+                    const int ni = min(kNI, nA - i0), k0 = s0 + i0;
+                    if (lane < kNI) {
+                        float4 h = make_float4(1e18f, 1e18f, 1e18f, 0.f), lo = zero4;
+                        if (lane < ni) {
+                            grid_split(a.xloc[k0 + lane], c.xlo[k0 + lane], c.qround, h, lo);
+                            const int q = cell_in_cluster(a.cell_off, c0, c1, k0 + lane);
+                            const int w0 = __float_as_int(h.w);
+                            h.w = __int_as_float((w0 & kSpBits) | (q << 5) | ((w0 & kGhostBit) ? kGhostW : 0));
+                        }
+                        w.ih[lane] = h;
+                        w.il[lane] = lo;
+                    }
+                    if (lane == 0) w.cnt[0] += (unsigned)(nq * ni);
+                    float fi[4 * kNI];
+#pragma unroll
+                    for (int i = 0; i < 4 * kNI; ++i) fi[i] = 0.f;
+                    __syncwarp();
+                    for (int jb = 0; jb < nq; jb += 32) {
+                        const int j = jb + lane;
+                        const bool valid = j < nq;
+                        const float4 xh = valid ? w.sh[j] : make_float4(-1e18f, -1e18f, -1e18f, 0.f);
+                        const float4 xl = valid ? w.sl[j] : zero4;
+                        float4 fj = zero4;
+                        unsigned nin = 0, nsame = 0;
+                        if (__any_sync(FULL, (__float_as_int(xh.w) & kSameBit) != 0))
+                            eval_tile<MULTI, SHIFT, true, GHOST>(a, tab, w, ni, k0, xh, xl, fi, fj, u_acc, nin, nsame,
+                                                                 vg, vl, facc);
+                        else
+                            eval_tile<MULTI, SHIFT, false, GHOST>(a, tab, w, ni, k0, xh, xl, fi, fj, u_acc, nin, nsame,
+                                                                  vg, vl, facc);
+                        if (valid && nin) {
+                            // within-rc counts per category (same cell, DIL, periodic image)
+                            const int wq = __float_as_int(xh.w);
+                            if (wq & kSameBit) {
+                                wc0 += nsame;
+                                wc1 += nin - nsame;
+                            } else if (wq & kImgBit) {
+                                wc2 += nin;
+                            } else {
+                                wc1 += nin;
+                            }
+                            float4 f = w.sf[j];
+                            f.x += fj.x; f.y += fj.y; f.z += fj.z; f.w += fj.w;
+                            w.sf[j] = f;
+                        }
+                    }
+                    tile_reduce4(fi, lane);
+                    const int t = lane >> 2;
+                    if ((lane & 3) == 0 && t < ni) {
+                        atomicAdd(facc + k0 + t, make_float4(fi[0], fi[1], fi[2], fi[3]));
+                        if (!GHOST) {
+                            const float4 x = w.ih[t];
+                            vir_add<32>(vl, x.x, x.y, x.z, fi[0], fi[1], fi[2]);
+                        }
+                    }
+                    __syncwarp();
+                }
+                // 4. survivors' reactions (and the survivor side of the virial, in A's frame)
+                for (int j = lane; j < nq; j += 32) {
+                    const float4 f = w.sf[j];
+                    if (f.x != 0.f || f.y != 0.f || f.z != 0.f || f.w != 0.f) {
+                        atomicAdd(facc + __float_as_int(w.sl[j].w), f);
+                        if (!GHOST) {
+                            const float4 x = w.sh[j];
+                            vir_add<32>(vl, x.x, x.y, x.z, f.x, f.y, f.z);
+                        }
+                    }
+                }
+                __syncwarp();
+                nq = 0;
+            }
+            if (!more) break;
         }
-        if (nq > 0) flush();
         // FP32 running sums to FP64 once per cluster
-        if (GHOST) {
+        {
+            const float su = warp_sum(u_acc);
+            u_acc = 0.f;
+            float sv[6];
 #pragma unroll
             for (int i = 0; i < 6; ++i) {
-                const float sv = warp_sum(vg[i]);
+                sv[i] = warp_sum(GHOST ? vg[i] : vl[32 * i]);
                 vg[i] = 0.f;
-                if (lane == 0) w.vir[i] += sv;
+                if (!GHOST) vl[32 * i] = 0.f;
             }
-        }
-        {
-            const float s = warp_sum(u_acc);
-            u_acc = 0.f;
-            __syncwarp();
             if (lane == 0) {
-                dsum[0] += (double)s;
-                for (int i = 0; i < 6; ++i) {
-                    dsum[1 + i] += (double)w.vir[i];
-                    w.vir[i] = 0.f;
-                }
+                dsum[0] += (double)su;
+                for (int i = 0; i < 6; ++i) dsum[1 + i] += (double)sv[i];
             }
             __syncwarp();
         }
@@ -2033,11 +2077,6 @@ __global__ void __launch_bounds__(kCT, MINB) pair_fwd32c(PairArgs a, ClKArgs c) 
 #pragma unroll
     for (int i = 0; i < 7; ++i) fin[i] = dsum[i];
     unsigned cv[8] = {0u, 0u, 0u, wc0, wc1, wc2, w.cnt[0], w.cnt[1]};
-    cv[6] = __shfl_sync(FULL, cv[6], 0);
-    cv[7] = __shfl_sync(FULL, cv[7], 0);
-    if (lane != 0) cv[6] = cv[7] = 0;
-    cv[6] = __shfl_sync(FULL, cv[6], 0);
-    cv[7] = __shfl_sync(FULL, cv[7], 0);
     if (lane != 0) cv[6] = cv[7] = 0;
     warp_to_stripe(a, blockIdx.x * kCW + wib, fin, cv, lane);
 }
