@@ -1012,10 +1012,26 @@ __global__ void __launch_bounds__(256) refine_ds(PairArgs a, RefineArgs r) {
     // molecules share their candidates in the caches
     const int chunk = (nflag + nw - 1) / nw;
     const int i_end = min(nflag, (gw + 1) * chunk);
+    int prev = 0;                      // cell of the warp's previous molecule (the list ascends)
     for (int i = gw * chunk; i < i_end; ++i) {
         const int k = r.flag_list[1 + i];
-        // cell of k (cell_off[c] <= k < cell_off[c + 1]): 32-ary search, one probe per lane
+        // cell of k (cell_off[c] <= k < cell_off[c + 1]): first the 32 cells
+        // from the previous molecule's, then a 32-ary search, one probe per lane
         int lo = 0, hi = r.C;
+        {
+            const int probe = prev + lane;
+            const bool le_k = probe < r.C && a.cell_off[probe] <= k;
+            const unsigned bl = __ballot_sync(FULL, le_k);
+            // cells prev .. prev + 31 start at or before k; the last of them holds k
+            // when a later probe starts beyond k (or the mesh ends)
+            if ((bl & 1u) && bl != FULL) {
+                lo = prev + 31 - __clz(bl);
+                hi = lo + 1;
+            } else if ((bl & 1u) && prev + 32 >= r.C) {
+                lo = r.C - 1;
+                hi = r.C;
+            }
+        }
         while (hi - lo > 1) {
             const int step = (hi - lo + 31) / 32;
             const int probe = lo + lane * step;
@@ -1024,6 +1040,7 @@ __global__ void __launch_bounds__(256) refine_ds(PairArgs a, RefineArgs r) {
             lo += last * step;
             hi = min(lo + step, hi);
         }
+        prev = lo;
         const int A = r.cl_of[lo];
         float4 kh, kl;
         grid_split(a.xloc[k], r.xlo[k], r.qround, kh, kl);
@@ -1622,7 +1639,7 @@ constexpr int kCT = 128, kCW = kCT / 32;
 // kRefineScale bounds that multiple with a wide safety margin.  A molecule
 // whose force is below kRefineScale / tol times that scale gets refined.
 constexpr double kRefineScale = 1.25e-6;
-constexpr int kCap = 240;                 // survivors buffered per warp
+constexpr int kCap = 176;                 // survivors buffered per warp (5 blocks of 4 warps per SM)
 constexpr int kNI = 8;                    // molecules of A per i-tile
 // packed survivor / tile word (.w of the hi position)
 constexpr int kSpBits = 7, kSameBit = 1 << 3, kImgBit = 1 << 4, kGhostW = 1 << 21;
