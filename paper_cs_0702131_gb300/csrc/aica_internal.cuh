@@ -148,6 +148,8 @@ struct aica_mesh {
     int max_cl_cells = 0;
     aica::DevBuf cl_first, cl_of;
     aica::DevBuf tri32, vtx32, edg32, ctr32;                 // float, minus org_c
+    aica::DevBuf pl32;                  // float4 per triangle: plane n / |n|_1, offset (local to org_c)
+    aica::DevBuf tric;                  // int2 per cell: first triangle, count | convex bit
     aica::DevBuf rad32;                                      // [C] float, rad rounded up
     double max_local = 0;                                    // largest |local coordinate|
     // Point-location grid: cells whose bounding box meets a bucket.

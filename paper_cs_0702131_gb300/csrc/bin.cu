@@ -61,6 +61,8 @@ struct BinArgs {
     const double *orgm64;     // molecule-frame origins (FP64, exact): frame of the binned coordinates
     long long Lkey[3], glo_key[3], ghi_key[3];
     const float *tri32, *ctr32, *box32;
+    const float4 *pl32;       // triangle planes n / |n|_1, offset (cell frame)
+    const int2 *tric;         // per cell: first triangle, count | convex bit
     const double *tri, *ctr;
     float max_local;
     float4 *xlo;              // remainders x - o_m - xloc (binned order)
@@ -130,12 +132,21 @@ __device__ int cell_test(const BinArgs &a, int c, float3 q, const double *p64, i
     if (boxcheck && (q.x < B[0] - tol || q.y < B[1] - tol || q.z < B[2] - tol || q.x > B[3] + tol ||
                      q.y > B[4] + tol || q.z > B[5] + tol))
         return 0;
-    const int t0 = a.tri_off[c], code = a.ntri[c], nt = code & 0xffff;
+    const int2 tc = a.tric[c];
+    const int t0 = tc.x, code = tc.y, nt = code & 0xffff;
+    // the face planes: e = n.q - d with |n|_1 = 1 carries at most about
+    // 9 * 2^-24 * scale of rounding (plane, point, three FMAs), far below
+    // the filter's bound; undecided faces go to the exact orientation
+    const float pb = 1e-5f * scale;
     bool behind = true;
     for (int t = t0; t < t0 + nt; ++t) {
-        const float *T = a.tri32 + 9 * t;
-        const double *D = a.tri + 9 * t;
-        const int s = orient<EXACT>(ld3f(T), ld3f(T + 3), ld3f(T + 6), q, scale, D, D + 3, D + 6, p64);
+        const float4 P = a.pl32[t];
+        const float e = fmaf(P.z, q.z, fmaf(P.y, q.y, fmaf(P.x, q.x, -P.w)));
+        int s = e > pb ? 1 : (e < -pb ? -1 : 0);
+        if (EXACT && s == 0) {
+            const double *D = a.tri + 9 * t;
+            s = orient_sos_slow(D, D + 3, D + 6, p64);
+        }
         if (!EXACT && s == 0) return -1;
         if (s > 0) {
             behind = false;
@@ -816,6 +827,8 @@ extern "C" aica_status aica_bin_molecules(aica_mesh *m, const double *pos, const
         a.ghi_key[d] = dkey(a.ghi[d]);
     }
     a.tri32 = m->tri32.as<float>();
+    a.pl32 = m->pl32.as<float4>();
+    a.tric = m->tric.as<int2>();
     a.ctr32 = m->ctr32.as<float>();
     a.box32 = m->box32.as<float>();
     a.tri = m->tri.as<double>();

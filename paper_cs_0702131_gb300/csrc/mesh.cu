@@ -223,6 +223,11 @@ extern "C" aica_status aica_mesh_create(const double *points, int64_t n_points, 
     if (T > INT32_MAX / 2) { set_error("too many triangles"); return AICA_ERR_CAPACITY; }
     std::vector<float> h_tri32(9 * T), h_vtx32(h_vtx.size()), h_edg32(h_edg.size()), h_ctr32(3 * n_cells),
         h_rad32(n_cells), h_box32(6 * n_cells);
+    // per triangle, its plane in the cell's frame for the FP32 point-location
+    // filter: N = (b - a) x (c - a) and N.a in FP64, both divided by |N|_1 and
+    // rounded (16 B per triangle instead of 36 B of vertices)
+    std::vector<float> h_pl32(4 * T);
+    std::vector<int32_t> h_tric(2 * n_cells);
     double max_local = 0;
     for (int64_t c = 0; c < n_cells; ++c) {
         for (int64_t i = 3 * (int64_t)h_tri_off[c]; i < 3 * (int64_t)h_tri_off[c + 1]; ++i)
@@ -231,6 +236,24 @@ extern "C" aica_status aica_mesh_create(const double *points, int64_t n_points, 
                 max_local = std::max(max_local, fabs(x));
                 h_tri32[3 * i + d] = (float)x;
             }
+        for (int64_t t = h_tri_off[c]; t < h_tri_off[c + 1]; ++t) {
+            double v[3][3];
+            for (int j = 0; j < 3; ++j)
+                for (int d = 0; d < 3; ++d) v[j][d] = h_tri[9 * t + 3 * j + d] - h_org[3 * c + d];
+            const double e1[3] = {v[1][0] - v[0][0], v[1][1] - v[0][1], v[1][2] - v[0][2]};
+            const double e2[3] = {v[2][0] - v[0][0], v[2][1] - v[0][1], v[2][2] - v[0][2]};
+            const double N[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
+                                 e1[0] * e2[1] - e1[1] * e2[0]};
+            const double s1 = fabs(N[0]) + fabs(N[1]) + fabs(N[2]);
+            const double g = (fabs(e1[0]) + fabs(e1[1]) + fabs(e1[2])) * (fabs(e2[0]) + fabs(e2[1]) + fabs(e2[2]));
+            // a sliver (|N| tiny against its edges, so N's direction carries FP64
+            // cancellation) or degenerate triangle gets plane 0: never decided
+            const double w = s1 > 1e-6 * g ? 1.0 / s1 : 0.0;
+            for (int d = 0; d < 3; ++d) h_pl32[4 * t + d] = (float)(N[d] * w);
+            h_pl32[4 * t + 3] = (float)((N[0] * v[0][0] + N[1] * v[0][1] + N[2] * v[0][2]) * w);
+        }
+        h_tric[2 * c] = h_tri_off[c];
+        h_tric[2 * c + 1] = h_ntri[c];
         for (int64_t i = h_vtx_off[c]; i < h_vtx_off[c + 1]; ++i)
             for (int d = 0; d < 3; ++d) h_vtx32[3 * i + d] = (float)(h_vtx[3 * i + d] - h_org[3 * c + d]);
         for (int64_t i = 2 * (int64_t)h_edg_off[c]; i < 2 * (int64_t)h_edg_off[c + 1]; ++i)
@@ -448,6 +471,8 @@ extern "C" aica_status aica_mesh_create(const double *points, int64_t n_points, 
     if (e == cudaSuccess) e = upload(m->cl_first, h_cl_first);
     if (e == cudaSuccess) e = upload(m->cl_of, h_cl_of);
     if (e == cudaSuccess) e = upload(m->tri32, h_tri32);
+    if (e == cudaSuccess) e = upload(m->pl32, h_pl32);
+    if (e == cudaSuccess) e = upload(m->tric, h_tric);
     if (e == cudaSuccess) e = upload(m->vtx32, h_vtx32);
     if (e == cudaSuccess) e = upload(m->edg32, h_edg32);
     if (e == cudaSuccess) e = upload(m->ctr32, h_ctr32);
@@ -479,7 +504,7 @@ extern "C" aica_status aica_mesh_create(const double *points, int64_t n_points, 
 extern "C" void aica_mesh_destroy(aica_mesh *m) {
     if (!m) return;
     aica::DevBuf *bufs[] = {&m->tri_off, &m->tri, &m->tri_nbr, &m->vtx_off, &m->vtx, &m->edg_off, &m->edg, &m->ctr, &m->rad,
-                            &m->lo, &m->hi, &m->org, &m->ntri, &m->orgk, &m->orgm, &m->orgm64, &m->cl_first, &m->cl_of, &m->cl_run_off, &m->cl_runs, &m->cl_full_off, &m->cl_full, &m->cl_box, &m->xlo, &m->flag_list, &m->tri32, &m->vtx32, &m->edg32, &m->ctr32, &m->rad32, &m->box32, &m->bkt_off, &m->bkt_cells, &m->nbr_off, &m->nbr, &m->dil_off,
+                            &m->lo, &m->hi, &m->org, &m->ntri, &m->orgk, &m->orgm, &m->orgm64, &m->cl_first, &m->cl_of, &m->cl_run_off, &m->cl_runs, &m->cl_full_off, &m->cl_full, &m->cl_box, &m->xlo, &m->flag_list, &m->tri32, &m->pl32, &m->tric, &m->vtx32, &m->edg32, &m->ctr32, &m->rad32, &m->box32, &m->bkt_off, &m->bkt_cells, &m->nbr_off, &m->nbr, &m->dil_off,
                             &m->dil_ids, &m->ref_src, &m->ref_n, &m->ref_off, &m->ref_ids, &m->run_off, &m->runs, &m->xf_dev, &m->run_d, &m->work_off,
                             &m->work, &m->work_split, &m->proc_order, &m->cell_of, &m->order, &m->unsorted,
                             &m->cell_off, &m->fill, &m->inv, &m->sph, &m->xloc, &m->xs64, &m->facc,
