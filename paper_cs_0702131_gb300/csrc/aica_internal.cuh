@@ -152,6 +152,7 @@ struct aica_mesh {
     aica::DevBuf tric;                  // int2 per cell: first triangle, count | convex bit
     aica::DevBuf rad32;                                      // [C] float, rad rounded up
     double max_local = 0;                                    // largest |local coordinate|
+    bool org32 = false;                 // every cell origin (orgk * 2^-10) exact in FP32 (|orgk| < 2^24)
     // Point-location grid: cells whose bounding box meets a bucket.
     int G[3] = {1, 1, 1};
     double glo[3] = {0, 0, 0}, gh[3] = {1, 1, 1};

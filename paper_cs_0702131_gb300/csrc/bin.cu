@@ -65,6 +65,7 @@ struct BinArgs {
     const int2 *tric;         // per cell: first triangle, count | convex bit
     const double *tri, *ctr;
     float max_local;
+    int org32;                // cell origins exact in FP32 (the hint kernel's FP32 frame change)
     float4 *xlo;              // remainders x - o_m - xloc (binned order)
     int64_t n_owned;          // molecules >= n_owned are halo copies (n_owned = n: none)
     int *cell_of;
@@ -314,13 +315,26 @@ __global__ void __launch_bounds__(256) bin_locate_hint(BinArgs a) {
         wrapped_position(a, k, p, ok);
         const int h = a.hint[k];
         if (ok && h >= 0) {
+            // p in a cell's frame without the FP64 pipe: p = ph + pl (split on
+            // the integer units), the cell origin exact in FP32, q = (ph - o) + pl
+            // (at most about 2.2 * 2^-24 of the frame scale off the exact local
+            // point, inside the filter's bound)
+            float ph[3], pl[3];
+            for (int d = 0; d < 3; ++d) split_f64(p[d], ph[d], pl[d]);
+            auto loc = [&](int cc) {
+                if (!a.org32) return local_to(a, p, cc);
+                const int *o = a.orgk + 3 * cc;
+                return make_float3((ph[0] - (float)o[0] * (1.f / 1024.f)) + pl[0],
+                                   (ph[1] - (float)o[1] * (1.f / 1024.f)) + pl[1],
+                                   (ph[2] - (float)o[2] * (1.f / 1024.f)) + pl[2]);
+            };
             int c = h, ex = -1;
-            int r = cell_test<false>(a, c, local_to(a, p, c), p, &ex, false);
+            int r = cell_test<false>(a, c, loc(c), p, &ex, false);
             undecided = r < 0;
             for (int step = 0; step < kWalk && r == 0 && ex >= 0; ++step) {
                 c = a.tri_nbr[ex];
                 if (c < 0) break;
-                r = cell_test<false>(a, c, local_to(a, p, c), p, &ex, false);
+                r = cell_test<false>(a, c, loc(c), p, &ex, false);
             }
             if (r == 1) {
                 a.cell_of[k] = c;
@@ -834,6 +848,7 @@ extern "C" aica_status aica_bin_molecules(aica_mesh *m, const double *pos, const
     a.tri = m->tri.as<double>();
     a.ctr = m->ctr.as<double>();
     a.max_local = (float)(m->max_local * (1 + 1e-6));
+    a.org32 = m->org32 ? 1 : 0;
     a.xlo = m->xlo.as<float4>();
     if (m->n_owned >= 0 && m->n_owned > n) {
         set_error("aica_bin_molecules: n_owned %lld exceeds the %lld molecules", (long long)m->n_owned, (long long)n);

@@ -440,6 +440,8 @@ extern "C" aica_status aica_mesh_create(const double *points, int64_t n_points, 
     m->max_tri = max_tri; m->max_vtx = max_vtx; m->max_edg = max_edg;
     m->max_local = max_local;
     m->max_mlocal = max_mlocal;
+    m->org32 = true;
+    for (int32_t k : h_orgk) m->org32 = m->org32 && k > -(1 << 24) && k < (1 << 24);
     // the FP32 cluster kernel splits binned coordinates at multiples of
     // 2^-qexp: |x - o_m| 2^qexp < 2^22 keeps the parts exact, with room for
     // the shifts of nearby partners
