@@ -150,6 +150,7 @@ struct aica_mesh {
     aica::DevBuf tri32, vtx32, edg32, ctr32;                 // float, minus org_c
     aica::DevBuf pl32;                  // float4 per triangle: plane n / |n|_1, offset (local to org_c)
     aica::DevBuf tric;                  // int2 per cell: first triangle, count | convex bit
+    aica::DevBuf orgf;                  // float x3 per cell: orgk * 2^-10 (exact when org32)
     aica::DevBuf rad32;                                      // [C] float, rad rounded up
     double max_local = 0;                                    // largest |local coordinate|
     bool org32 = false;                 // every cell origin (orgk * 2^-10) exact in FP32 (|orgk| < 2^24)

@@ -63,6 +63,7 @@ struct BinArgs {
     const float *tri32, *ctr32, *box32;
     const float4 *pl32;       // triangle planes n / |n|_1, offset (cell frame)
     const int2 *tric;         // per cell: first triangle, count | convex bit
+    const float *orgf;        // cell origins in FP32 (exact when org32)
     const double *tri, *ctr;
     float max_local;
     int org32;                // cell origins exact in FP32 (the hint kernel's FP32 frame change)
@@ -323,10 +324,8 @@ __global__ void __launch_bounds__(256) bin_locate_hint(BinArgs a) {
             for (int d = 0; d < 3; ++d) split_f64(p[d], ph[d], pl[d]);
             auto loc = [&](int cc) {
                 if (!a.org32) return local_to(a, p, cc);
-                const int *o = a.orgk + 3 * cc;
-                return make_float3((ph[0] - (float)o[0] * (1.f / 1024.f)) + pl[0],
-                                   (ph[1] - (float)o[1] * (1.f / 1024.f)) + pl[1],
-                                   (ph[2] - (float)o[2] * (1.f / 1024.f)) + pl[2]);
+                const float *o = a.orgf + 3 * cc;
+                return make_float3((ph[0] - o[0]) + pl[0], (ph[1] - o[1]) + pl[1], (ph[2] - o[2]) + pl[2]);
             };
             int c = h, ex = -1;
             int r = cell_test<false>(a, c, loc(c), p, &ex, false);
@@ -520,13 +519,15 @@ __global__ void __launch_bounds__(256) bin_scatter_down(const int *cell_of, int6
 
 // Coordinates of p in the molecule frame o: the nearest FP32 values and the
 // FP32 remainders (hi + lo equals p - o to about 2^-48 |p - o|).  The FP32
-// cluster pair kernel rebuilds exactly rounded separations from both.
-__device__ __forceinline__ void frame_split(const BinArgs &a, const double *p, const double *o, int sp,
+// cluster pair kernel rebuilds exactly rounded separations from both.  The
+// remainder's .w carries the molecule's cell (int bits): the cluster kernel
+// tells cells of a cluster (at most 16 consecutive ones) apart by it.
+__device__ __forceinline__ void frame_split(const BinArgs &a, const double *p, const double *o, int sp, int cell,
                                             float4 &hi, float4 &lo) {
     float h[3], l[3];
     for (int d = 0; d < 3; ++d) split_f64(p[d] - o[d], h[d], l[d]);   // p - o is exact (o dyadic, nearby)
     hi = make_float4(h[0], h[1], h[2], __int_as_float(sp));
-    lo = make_float4(l[0], l[1], l[2], 0.f);
+    lo = make_float4(l[0], l[1], l[2], __int_as_float(cell));
 }
 
 // Per cell, by groups of G lanes: order the cell's molecules by original
@@ -568,7 +569,7 @@ __global__ void __launch_bounds__(256) bin_cells(BinArgs a, const int *cell_off,
                 xs64[3 * (int64_t)slot + d] = p[d];
             }
             float4 lo;
-            frame_split(a, p, a.orgm64 + 3 * c, (sp & (kMaxSpecies - 1)) | (k >= a.n_owned ? kGhostBit : 0), x, lo);
+            frame_split(a, p, a.orgm64 + 3 * c, (sp & (kMaxSpecies - 1)) | (k >= a.n_owned ? kGhostBit : 0), c, x, lo);
             xloc[slot] = x;
             a.xlo[slot] = lo;
         }
@@ -614,7 +615,7 @@ __global__ void __launch_bounds__(256) bin_cells(BinArgs a, const int *cell_off,
                     xs64[3 * (int64_t)slot + d] = p[d];
                 }
                 float4 y, lo;
-                frame_split(a, p, a.orgm64 + 3 * c, (sp & (kMaxSpecies - 1)) | (kk >= a.n_owned ? kGhostBit : 0), y, lo);
+                frame_split(a, p, a.orgm64 + 3 * c, (sp & (kMaxSpecies - 1)) | (kk >= a.n_owned ? kGhostBit : 0), c, y, lo);
                 xloc[slot] = y;
                 a.xlo[slot] = lo;
                 sx += y.x; sy += y.y; sz += y.z;
@@ -658,7 +659,7 @@ __device__ __forceinline__ float4 local_xloc(const BinArgs &a, int k, int c, int
         xs64[3 * (int64_t)slot + d] = p[d];
     }
     float4 hi, lo;
-    frame_split(a, p, a.orgm64 + 3 * c, (sp & (kMaxSpecies - 1)) | (k >= a.n_owned ? kGhostBit : 0), hi, lo);
+    frame_split(a, p, a.orgm64 + 3 * c, (sp & (kMaxSpecies - 1)) | (k >= a.n_owned ? kGhostBit : 0), c, hi, lo);
     a.xlo[slot] = lo;
     return hi;
 }
@@ -843,6 +844,7 @@ extern "C" aica_status aica_bin_molecules(aica_mesh *m, const double *pos, const
     a.tri32 = m->tri32.as<float>();
     a.pl32 = m->pl32.as<float4>();
     a.tric = m->tric.as<int2>();
+    a.orgf = m->orgf.as<float>();
     a.ctr32 = m->ctr32.as<float>();
     a.box32 = m->box32.as<float>();
     a.tri = m->tri.as<double>();

@@ -442,6 +442,8 @@ extern "C" aica_status aica_mesh_create(const double *points, int64_t n_points, 
     m->max_mlocal = max_mlocal;
     m->org32 = true;
     for (int32_t k : h_orgk) m->org32 = m->org32 && k > -(1 << 24) && k < (1 << 24);
+    std::vector<float> h_orgf(h_orgk.size());
+    for (size_t i = 0; i < h_orgk.size(); ++i) h_orgf[i] = (float)h_orgk[i] * (1.0f / 1024.0f);
     // the FP32 cluster kernel splits binned coordinates at multiples of
     // 2^-qexp: |x - o_m| 2^qexp < 2^22 keeps the parts exact, with room for
     // the shifts of nearby partners
@@ -475,6 +477,7 @@ extern "C" aica_status aica_mesh_create(const double *points, int64_t n_points, 
     if (e == cudaSuccess) e = upload(m->tri32, h_tri32);
     if (e == cudaSuccess) e = upload(m->pl32, h_pl32);
     if (e == cudaSuccess) e = upload(m->tric, h_tric);
+    if (e == cudaSuccess) e = upload(m->orgf, h_orgf);
     if (e == cudaSuccess) e = upload(m->vtx32, h_vtx32);
     if (e == cudaSuccess) e = upload(m->edg32, h_edg32);
     if (e == cudaSuccess) e = upload(m->ctr32, h_ctr32);
@@ -506,7 +509,7 @@ extern "C" aica_status aica_mesh_create(const double *points, int64_t n_points, 
 extern "C" void aica_mesh_destroy(aica_mesh *m) {
     if (!m) return;
     aica::DevBuf *bufs[] = {&m->tri_off, &m->tri, &m->tri_nbr, &m->vtx_off, &m->vtx, &m->edg_off, &m->edg, &m->ctr, &m->rad,
-                            &m->lo, &m->hi, &m->org, &m->ntri, &m->orgk, &m->orgm, &m->orgm64, &m->cl_first, &m->cl_of, &m->cl_run_off, &m->cl_runs, &m->cl_full_off, &m->cl_full, &m->cl_box, &m->xlo, &m->flag_list, &m->tri32, &m->pl32, &m->tric, &m->vtx32, &m->edg32, &m->ctr32, &m->rad32, &m->box32, &m->bkt_off, &m->bkt_cells, &m->nbr_off, &m->nbr, &m->dil_off,
+                            &m->lo, &m->hi, &m->org, &m->ntri, &m->orgk, &m->orgm, &m->orgm64, &m->cl_first, &m->cl_of, &m->cl_run_off, &m->cl_runs, &m->cl_full_off, &m->cl_full, &m->cl_box, &m->xlo, &m->flag_list, &m->tri32, &m->pl32, &m->tric, &m->orgf, &m->vtx32, &m->edg32, &m->ctr32, &m->rad32, &m->box32, &m->bkt_off, &m->bkt_cells, &m->nbr_off, &m->nbr, &m->dil_off,
                             &m->dil_ids, &m->ref_src, &m->ref_n, &m->ref_off, &m->ref_ids, &m->run_off, &m->runs, &m->xf_dev, &m->run_d, &m->work_off,
                             &m->work, &m->work_split, &m->proc_order, &m->cell_of, &m->order, &m->unsorted,
                             &m->cell_off, &m->fill, &m->inv, &m->sph, &m->xloc, &m->xs64, &m->facc,

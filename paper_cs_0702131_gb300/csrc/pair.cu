@@ -1071,7 +1071,7 @@ __global__ void __launch_bounds__(256) refine_ds(PairArgs a, RefineArgs r) {
                     in = rr < a.rc2_d;
                 }
                 if (in) {
-                    const int ab = spk * kMaxSpecies + (__float_as_int(a.xloc[l].w) & (kMaxSpecies - 1));
+                    const int ab = a.S > 1 ? spk * kMaxSpecies + (__float_as_int(a.xloc[l].w) & (kMaxSpecies - 1)) : 0;
                     const ds inv = ds_rcp(r2);
                     const ds s = ds_mul(ds{r.sig2[ab][0], r.sig2[ab][1]}, inv);
                     const ds s3 = ds_mul(ds_mul(s, s), s);
@@ -1662,23 +1662,6 @@ struct WarpC {
     unsigned cnt[2];      // pair tests, culling tests
 };
 
-// A shared-memory load the compiler keeps in place (a broadcast read per
-// use instead of 64 registers holding the whole tile).
-__device__ __forceinline__ float4 lds4(const float4 *p) {
-    float4 v;
-    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                 : "r"((unsigned)__cvta_generic_to_shared(p)));
-    return v;
-}
-
-// cell of binned molecule k among A's cells c0 .. c1 - 1 (at most kMaxClusterCells)
-__device__ __forceinline__ int cell_in_cluster(const int *cell_off, int c0, int c1, int k) {
-    int c = c0;
-    while (c + 1 < c1 && cell_off[c + 1] <= k) ++c;
-    return c - c0;
-}
-
 // One pair of the cluster kernel (FP32 body, branch-free): tile molecule t
 // (h, lo) against a lane's survivor (xh, xl); the force goes to fi[4t..] and
 // fj, |f|^2 to both .w/[4t+3], the energy to u_acc; a pair whose FP32 r^2
@@ -1801,7 +1784,7 @@ __device__ __forceinline__ void eval_tile(const PairArgs &a, const float4 *tab, 
 #pragma unroll
     for (int t = 0; t < kNI; ++t) {
         if (t >= ni) break;
-        const float4 h = lds4(&w.ih[t]), lo = lds4(&w.il[t]);
+        const float4 h = w.ih[t], lo = w.il[t];
         tile_pair<MULTI, SHIFT, SAME, GHOST>(a, tab, t0, h, lo, xh, xl, t, k0, fi, fj, u_acc, nin, nsame, bm, vg);
     }
     if (__any_sync(0xffffffffu, bm != 0)) {
@@ -1919,8 +1902,9 @@ __global__ void __launch_bounds__(kCT, MINB) pair_fwd32c(PairArgs a, ClKArgs c) 
                     const bool alive = k < s1;
                     float4 xh = far, xl = zero4;
                     if (alive) {
-                        grid_split(a.xloc[k], c.xlo[k], c.qround, xh, xl);
-                        const int q = cell_in_cluster(a.cell_off, c0, c1, k);
+                        const float4 r = c.xlo[k];
+                        grid_split(a.xloc[k], r, c.qround, xh, xl);
+                        const int q = __float_as_int(r.w) & 15;     // cell label within the cluster
                         const int w0 = __float_as_int(xh.w);
                         xh.w = __int_as_float((w0 & kSpBits) | kSameBit | (q << 5) | ((w0 & kGhostBit) ? kGhostW : 0));
                         xl.w = __int_as_float(k);
@@ -2002,8 +1986,9 @@ __global__ void __launch_bounds__(kCT, MINB) pair_fwd32c(PairArgs a, ClKArgs c) 
                     if (lane < kNI) {
                         float4 h = make_float4(1e18f, 1e18f, 1e18f, 0.f), lo = zero4;
                         if (lane < ni) {
-                            grid_split(a.xloc[k0 + lane], c.xlo[k0 + lane], c.qround, h, lo);
-                            const int q = cell_in_cluster(a.cell_off, c0, c1, k0 + lane);
+                            const float4 r = c.xlo[k0 + lane];
+                            grid_split(a.xloc[k0 + lane], r, c.qround, h, lo);
+                            const int q = __float_as_int(r.w) & 15;
                             const int w0 = __float_as_int(h.w);
                             h.w = __int_as_float((w0 & kSpBits) | (q << 5) | ((w0 & kGhostBit) ? kGhostW : 0));
                         }
