@@ -67,6 +67,10 @@ def lib():
         L.oracle_cell_pairs.argtypes = [_i64, _f64, _i64, _f64, _i64, _f64, _f64, _f64, ctypes.c_int64, _i64,
                                         ctypes.c_int64, ctypes.c_double, _i32, _f64, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_int64, _i64, _i32, _i32, _f64, _i64]
+        L.oracle_cell_pairs_grid.argtypes = [_i64, _f64, _i64, _f64, _i64, _f64, _f64, _f64, ctypes.c_int64,
+                                             _i64, ctypes.c_int64, ctypes.c_double, _i32, _f64, ctypes.c_int, ctypes.c_int, _i64, _i64,
+                                             _i64, _f64, ctypes.c_double, _i64, _i64, _i32,
+                                             np.ctypeslib.ndpointer(np.int8, flags="C_CONTIGUOUS"), _i64]
         L.oracle_locate.argtypes = [_i64, _f64, _f64, _f64, ctypes.c_int64, _f64, ctypes.c_int64, _f64, _i32,
                                     _i32, _f64]
         L.oracle_aica_loop.argtypes = [ctypes.c_int64, _i64, _f64, _i32, _f64, _f64, ctypes.c_double, _f64,
@@ -309,6 +313,67 @@ def cell_lists(mesh, box, rc, skin, queries=None, geo=None, use_bound=True, crit
                 ref_src=np.asarray(ref_src, np.int32),
                 ref_n=np.asarray(ref_n, np.int32).reshape(-1, 3),
                 ref_off=np.asarray(ref_off, np.int64), ref_ids=cat(ref_ids), ties=ties)
+
+
+def cell_lists_full(mesh, box, rc, skin, queries=None, geo=None, criterion="min_distance"):
+    """The lists of cell_lists at full size: the candidate cells of each
+    query come from a bucket grid of the cell centres (oracle_cell_pairs_grid)
+    instead of a loop over all cells; the sphere bound and the distance that
+    decide are the same, so the lists are too (pinned against cell_lists in
+    the tests).  Same arguments and dict as cell_lists."""
+    if criterion not in ("min_distance", "vertex"):
+        raise ValueError(criterion)
+    geo = geo or cell_geometry(mesh)
+    thr = rc + skin
+    C = geo["n_cells"]
+    ctr = geo["ctr"].reshape(-1, 3)
+    rmax = float(geo["rad"].max()) if C else 0.0
+    h = max((thr + 2 * rmax) / 2, 1e-9)
+    glo = ctr.min(axis=0) if C else np.zeros(3)
+    G = (np.floor((ctr.max(axis=0) - glo) / h).astype(np.int64) + 1) if C else np.ones(3, np.int64)
+    ib = np.clip(np.floor((ctr - glo) / h).astype(np.int64), 0, G - 1)
+    bk = (ib[:, 0] * G[1] + ib[:, 1]) * G[2] + ib[:, 2]
+    order = np.argsort(bk, kind="stable").astype(np.int64)
+    bkt_off = np.r_[0, np.cumsum(np.bincount(bk, minlength=int(G.prod())))].astype(np.int64)
+    m = image_range(thr, box)
+    cells = np.arange(C, dtype=np.int64) if queries is None else np.asarray(queries, np.int64)
+    nq = len(cells)
+    cnt = np.zeros(nq, np.int64)
+    ties = np.zeros(nq, np.int64)
+    args = (geo["tri_off"], geo["tri"], geo["vtx_off"], geo["vtx"], geo["edg_off"], geo["edg"], geo["ctr"],
+            geo["rad"], C, cells, nq, float(thr), m, _c(box["L"], np.float64), int(criterion == "vertex"))
+    grid = (bkt_off, order, G, _c(glo, np.float64), float(h))
+    one = np.zeros(1, np.int32)
+    one8 = np.zeros(3, np.int8)
+    lib().oracle_cell_pairs_grid(*args, 0, *grid, cnt, np.zeros(nq + 1, np.int64), one, one8, ties)
+    off = np.r_[0, np.cumsum(cnt)].astype(np.int64)
+    E = int(off[-1])
+    outB = np.zeros(max(E, 1), np.int32)
+    outN = np.zeros(3 * max(E, 1), np.int8)
+    lib().oracle_cell_pairs_grid(*args, 1, *grid, cnt, off, outB, outN, ties)
+    A = np.repeat(cells, cnt)
+    B = outB[:E].astype(np.int64)
+    N = outN[:3 * E].reshape(-1, 3).astype(np.int64)
+    zero = ~N.any(axis=1)
+    dA, dB = A[zero], B[zero]                        # n = 0, B > A
+    o = np.lexsort((dB, dA))
+    rows = np.searchsorted(cells, dA) if queries is not None else dA      # row of each entry's owner
+    if queries is not None and len(cells) and not np.all(np.diff(cells) > 0):
+        raise ValueError("queries must be ascending and unique")
+    dil_off = np.r_[0, np.cumsum(np.bincount(rows, minlength=nq))].astype(np.int64)
+    dil_ids = dB[o].astype(np.int32)
+    rA, rB, rn = A[~zero], B[~zero], -N[~zero]       # referred cell (source A, image -n)
+    o = np.lexsort((rB, rn[:, 2], rn[:, 1], rn[:, 0], rA))
+    rA, rB, rn = rA[o], rB[o], rn[o]
+    if len(rA):
+        new = np.r_[True, (np.diff(rA) != 0) | np.any(np.diff(rn, axis=0) != 0, axis=1)]
+        starts = np.flatnonzero(new)
+    else:
+        starts = np.zeros(0, np.int64)
+    return dict(cells=cells, dil_off=dil_off, dil_ids=dil_ids,
+                ref_src=rA[starts].astype(np.int32), ref_n=rn[starts].astype(np.int32).reshape(-1, 3),
+                ref_off=np.r_[starts, len(rA)].astype(np.int64), ref_ids=rB.astype(np.int32),
+                ties=int(ties.sum()))
 
 
 # ------------------------------------------------------------------- point location

@@ -15,6 +15,8 @@
  *                        triangulated polyhedra, all periodic images (§2.2,
  *                        App. A.1, with the exact-distance criterion), or the
  *                        paper's vertex-vertex distance
+ *   oracle_cell_pairs_grid  the same pairs for all cells, candidates from a
+ *                        bucket grid of cell centres (full-size lists)
  *   oracle_locate        point location by ray parity with a symbolic
  *                        perturbation tie-break, FP64 with an error filter;
  *                        uncertain cases are flagged for exact resolution
@@ -298,6 +300,83 @@ void oracle_cell_pairs(const int64_t *tri_off, const double *tri, const int64_t 
                     }
                 }
         count[q] = c > cap ? -1 : c;
+        ties[q] = nt;
+    }
+}
+
+/* The same pairs for every cell as query, found through a uniform grid of
+ * buckets over the cell centres instead of a loop over all cells: for query
+ * A and image n only the cells whose centre lies within thr + rad_A +
+ * max(rad) of c_A - n.L can pass the sphere bound of oracle_cell_pairs, and
+ * the buckets searched cover that ball, so the set of cells that reach the
+ * bound and the exact distance is unchanged.  The same sphere bound and the
+ * same distance then decide.  Only the entries the lists need are written:
+ * n = 0 with B > A (the DIL) and every n != 0 (referred cells); ties are
+ * counted over all pairs evaluated, as in oracle_cell_pairs.
+ *   pass 0: count[q] = entries of query cell query[q]; pass 1: its entries
+ *   at off[q] .. off[q] + count[q] (in search order; the caller sorts). */
+void oracle_cell_pairs_grid(const int64_t *tri_off, const double *tri, const int64_t *vtx_off,
+                            const double *vtx, const int64_t *edg_off, const double *edg,
+                            const double *ctr, const double *rad, int64_t n_cells,
+                            const int64_t *query, int64_t nq, double thr,
+                            const int32_t *m, const double *L, int vertex_only, int pass,
+                            const int64_t *bkt_off, const int64_t *bkt_cells, const int64_t *G,
+                            const double *glo, double h, int64_t *count, const int64_t *off,
+                            int32_t *outB, int8_t *outN, int64_t *ties)
+{
+    cellgeo g = {tri_off, vtx_off, edg_off, tri, vtx, edg};
+    double thr2 = thr * thr, rmax = 0;
+    for (int64_t B = 0; B < n_cells; ++B) rmax = rad[B] > rmax ? rad[B] : rmax;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t q = 0; q < nq; ++q) {
+        const int64_t A = query[q];
+        int64_t c = 0, nt = 0;
+        /* a cell passing the sphere bound lies within thr (1 + 1e-9) + 1e-9 +
+         * rad_A + rad_B of c_A - n.L; the searched ball is wider by far more
+         * than the rounding of the bucket arithmetic */
+        double R = (thr + rad[A] + rmax) * (1 + 1e-6) + 1e-6;
+        for (int nx = -m[0]; nx <= m[0]; ++nx)
+            for (int ny = -m[1]; ny <= m[1]; ++ny)
+                for (int nz = -m[2]; nz <= m[2]; ++nz) {
+                    v3 s = {nx * L[0], ny * L[1], nz * L[2]};
+                    double p[3] = {ctr[3 * A] - s.x, ctr[3 * A + 1] - s.y, ctr[3 * A + 2] - s.z};
+                    int64_t b0[3], b1[3];
+                    int empty = 0;
+                    for (int d = 0; d < 3; ++d) {
+                        double lo = floor((p[d] - R - glo[d]) / h), hi = floor((p[d] + R - glo[d]) / h);
+                        if (hi < 0 || lo > (double)(G[d] - 1)) empty = 1;
+                        b0[d] = lo < 0 ? 0 : (int64_t)lo;
+                        b1[d] = hi > (double)(G[d] - 1) ? G[d] - 1 : (int64_t)hi;
+                    }
+                    if (empty) continue;
+                    for (int64_t i = b0[0]; i <= b1[0]; ++i)
+                        for (int64_t j = b0[1]; j <= b1[1]; ++j)
+                            for (int64_t k = b0[2]; k <= b1[2]; ++k) {
+                                int64_t bk = (i * G[1] + j) * G[2] + k;
+                                for (int64_t t = bkt_off[bk]; t < bkt_off[bk + 1]; ++t) {
+                                    int64_t B = bkt_cells[t];
+                                    if (B == A && nx == 0 && ny == 0 && nz == 0) continue;
+                                    v3 dc = {ctr[3 * A] - ctr[3 * B] - s.x, ctr[3 * A + 1] - ctr[3 * B + 1] - s.y,
+                                             ctr[3 * A + 2] - ctr[3 * B + 2] - s.z};
+                                    double lb = sqrt(dot(dc, dc)) - rad[A] - rad[B];
+                                    if (lb > thr * (1 + 1e-9) + 1e-9) continue;
+                                    double d2 = vertex_only ? cell_vertex_d2(&g, A, B, s) : cell_d2(&g, A, B, s);
+                                    if (fabs(d2 - thr2) <= 1e-9 * thr2) nt++;
+                                    if (!(d2 < thr2)) continue;
+                                    int zero = nx == 0 && ny == 0 && nz == 0;
+                                    if (zero && B < A) continue;
+                                    if (pass == 1) {
+                                        int64_t o = off[q] + c;
+                                        outB[o] = (int32_t)B;
+                                        outN[3 * o] = (int8_t)nx;
+                                        outN[3 * o + 1] = (int8_t)ny;
+                                        outN[3 * o + 2] = (int8_t)nz;
+                                    }
+                                    c++;
+                                }
+                            }
+                }
+        if (pass == 0) count[q] = c;
         ties[q] = nt;
     }
 }

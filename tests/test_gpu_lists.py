@@ -49,6 +49,33 @@ def test_lists_sampled_full_size(name):
     compare_lists(g, o, cells)
 
 
+def test_lists_full_c3():
+    """Every row of the nanochannel's lists (91 680 hexahedra, open y axis,
+    removed post columns, periodic x and z) against the oracle."""
+    c = synth.make("c3", 0)
+    m, *_ = gpu_setup(c)
+    g = m.lists()
+    o = oracle.cell_lists_full(c["mesh"], c["box"], c["rc"], c["skin"])
+    assert g["ties"] == 0 and o["ties"] == 0
+    compare_lists(g, o)
+
+
+def test_lists_slab_c5():
+    """Every row of a slab of c5's lists: the 5 % of its 3 072 000 tetrahedra
+    whose centres lie nearest the periodic face x = 0 (their referred cells
+    included), against the oracle."""
+    c = synth.make("c5", 0)
+    m, *_ = gpu_setup(c)
+    g = m.lists()
+    geo = oracle.cell_geometry(c["mesh"])
+    x = geo["ctr"].reshape(-1, 3)[:, 0]
+    cells = np.flatnonzero(x < np.quantile(x, 0.05))
+    o = oracle.cell_lists_full(c["mesh"], c["box"], c["rc"], c["skin"], queries=cells, geo=geo)
+    assert g["ties"] == 0 and o["ties"] == 0
+    assert len(o["ref_src"]) > 0
+    compare_lists(g, o, cells)
+
+
 def test_uniform_cubes_give_n_c(golden):
     n, w = 6, 2.28
     L = n * w

@@ -220,3 +220,32 @@ def test_sampled_queries_equal_full():
     sel = np.isin(full["ref_src"], q)
     np.testing.assert_array_equal(part["ref_src"], full["ref_src"][sel])
     np.testing.assert_array_equal(part["ref_n"], full["ref_n"][sel])
+
+
+def _same_lists(a, b):
+    for k in ("cells", "dil_off", "dil_ids", "ref_src", "ref_n", "ref_off", "ref_ids"):
+        np.testing.assert_array_equal(np.asarray(a[k]).reshape(-1), np.asarray(b[k]).reshape(-1), err_msg=k)
+    assert a["ties"] == b["ties"]
+
+
+@pytest.mark.parametrize("name,seed", [("t0", 0), ("t0", 5), ("c1", 0), ("h0", 1)])
+def test_full_size_search_equals_brute_force(name, seed):
+    """cell_lists_full (candidates from a bucket grid of cell centres, for the
+    full-size list comparisons) gives exactly the brute-force lists: all
+    cells, a subset of query cells, and the paper's vertex criterion."""
+    c = synth.make(name, seed)
+    geo = oracle.cell_geometry(c["mesh"])
+    _same_lists(oracle.cell_lists(c["mesh"], c["box"], c["rc"], c["skin"], geo=geo),
+                oracle.cell_lists_full(c["mesh"], c["box"], c["rc"], c["skin"], geo=geo))
+    q = np.unique(np.random.default_rng(seed).choice(geo["n_cells"], 40, replace=False))
+    _same_lists(oracle.cell_lists(c["mesh"], c["box"], c["rc"], c["skin"], queries=q, geo=geo),
+                oracle.cell_lists_full(c["mesh"], c["box"], c["rc"], c["skin"], queries=q, geo=geo))
+    _same_lists(oracle.cell_lists(c["mesh"], c["box"], c["rc"], 0.3, geo=geo, criterion="vertex"),
+                oracle.cell_lists_full(c["mesh"], c["box"], c["rc"], 0.3, geo=geo, criterion="vertex"))
+
+
+def test_full_size_search_open_axis_and_removed_cells():
+    c = synth.nanochannel(2, nfcc=(12, 4, 12), hex_shape=(8, 4, 8), post_radius=2.0)
+    geo = oracle.cell_geometry(c["mesh"])
+    _same_lists(oracle.cell_lists(c["mesh"], c["box"], c["rc"], 1e-3, geo=geo),
+                oracle.cell_lists_full(c["mesh"], c["box"], c["rc"], 1e-3, geo=geo))
