@@ -994,8 +994,10 @@ struct RefineArgs {
     float sig2[kMaxSpecies * kMaxSpecies][2];   // sigma_ab^2 and 24 eps_ab, double-single
     float c24[kMaxSpecies * kMaxSpecies][2];
     float rc2h, rc2l;            // rc^2, double-single
+    unsigned *next;              // next unclaimed entry of the flag list (zero at launch)
 };
 
+constexpr int kRefineGrab = 4;        // flagged molecules claimed per warp at a time
 __global__ void __launch_bounds__(256) refine_ds(PairArgs a, RefineArgs r) {
     __shared__ float4 ed[8][32];       // per warp: live entries of the batch: shift hi (xyz), image (w)
     __shared__ float4 el[8][32];       //           shift remainder (xyz)
@@ -1004,16 +1006,22 @@ __global__ void __launch_bounds__(256) refine_ds(PairArgs a, RefineArgs r) {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u, le = FULL >> (31 - lane);
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
     const int nflag = r.flag_list[0];
     const float pre2 = a.rc2_hi * 1.001f + 1e-3f;
     const float reach = sqrtf(pre2) + 1e-3f;
-    // contiguous chunks of the (spatially ordered) list per warp: neighbouring
-    // molecules share their candidates in the caches
-    const int chunk = (nflag + nw - 1) / nw;
-    const int i_end = min(nflag, (gw + 1) * chunk);
+    // warps claim consecutive entries of the (spatially ordered) list, up to
+    // kRefineGrab at a time when the list is long enough to keep every warp
+    // busy: neighbouring molecules share their candidates in the caches, and
+    // the claims balance molecules of unequal cost
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const int grab = max(1, min(kRefineGrab, nflag / (4 * nw)));      // c5: 4, c2 and c4: 1
     int prev = 0;                      // cell of the warp's previous molecule (the list ascends)
-    for (int i = gw * chunk; i < i_end; ++i) {
+    for (;;) {
+    int i0 = lane == 0 ? (int)atomicAdd(r.next, (unsigned)grab) : 0;
+    i0 = __shfl_sync(FULL, i0, 0);
+    if (i0 >= nflag) break;
+    const int i_end = min(nflag, i0 + grab);
+    for (int i = i0; i < i_end; ++i) {
         const int k = r.flag_list[1 + i];
         // cell of k (cell_off[c] <= k < cell_off[c + 1]): first the 32 cells
         // from the previous molecule's, then a 32-ary search, one probe per lane
@@ -1192,6 +1200,7 @@ __global__ void __launch_bounds__(256) refine_ds(PairArgs a, RefineArgs r) {
             r.out[3 * (size_t)o + 1] = Fy.h + Fy.l;
             r.out[3 * (size_t)o + 2] = Fz.h + Fz.l;
         }
+    }
     }
 }
 
@@ -2422,6 +2431,7 @@ extern "C" aica_status aica_forces(aica_mesh *m, const aica_lj *lj, aica_precisi
         }
         r.rc2h = (float)a.rc2_d;
         r.rc2l = (float)(a.rc2_d - (double)r.rc2h);
+        r.next = (unsigned *)(m->acc.as<double>() + 25);      // zeroed with the sums at the call's start
         refine_ds<<<152 * 8, 256, 0, st>>>(a, r);
         m->launches += 1;
     }
