@@ -2022,17 +2022,16 @@ __global__ void __launch_bounds__(kCT, MINB) pair_fwd32c(PairArgs a, ClKArgs c) 
                         else
                             eval_tile<MULTI, SHIFT, false, GHOST>(a, tab, w, ni, k0, xh, xl, fi, fj, u_acc, nin, nsame,
                                                                   vg, vl, facc);
-                        if (valid && nin) {
-                            // within-rc counts per category (same cell, DIL, periodic image)
+                        {
+                            // within-rc counts per category (same cell, DIL, periodic image),
+                            // without branches (nin = nsame = 0 on invalid lanes)
                             const int wq = __float_as_int(xh.w);
-                            if (wq & kSameBit) {
-                                wc0 += nsame;
-                                wc1 += nin - nsame;
-                            } else if (wq & kImgBit) {
-                                wc2 += nin;
-                            } else {
-                                wc1 += nin;
-                            }
+                            const unsigned img = (wq & kImgBit) ? nin : 0u;
+                            wc0 += nsame;
+                            wc1 += nin - nsame - img;
+                            wc2 += img;
+                        }
+                        if (valid && nin) {
                             float4 f = w.sf[j];
                             f.x += fj.x; f.y += fj.y; f.z += fj.z; f.w += fj.w;
                             w.sf[j] = f;
