@@ -81,3 +81,39 @@ def test_pairs_at_and_just_inside_the_cut(prec):
     assert cnt[3] + cnt[4] + cnt[5] == 1
     assert np.all(F[[0, 1, 4, 5]] == 0) and np.all(F[[2, 3], 0] != 0)
     _check(pos, prec, True)
+
+
+@pytest.mark.parametrize("tets", [False, True])
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_clusters_larger_than_the_survivor_buffer(tets, prec):
+    """A liquid at rho* = 0.8 in 2^3 hexahedra of about 6 sigma (about 171
+    molecules per hexahedron, the FP32 kernel's cluster): a cluster's own
+    molecules no longer fit the survivor buffer's fill threshold, so the
+    buffer is evaluated in the middle of pushing them, over many tiles.
+    Every molecule at the stated tolerance, energy, virial and pair counts
+    against the oracle."""
+    from gpu_helpers import assert_forces
+    a = (4 / 0.8) ** (1 / 3)
+    n = 7
+    Lb = n * a
+    box = dict(L=np.array([Lb, Lb, Lb]), periodic=np.array([1, 1, 1], np.int32))
+    rng = np.random.default_rng(21)
+    pos = synth.wrap(synth.fcc_sites(n, n, n, a) + rng.normal(scale=0.05, size=(4 * n ** 3, 3)), box["L"],
+                     box["periodic"])
+    mesh = synth.hex_mesh((2, 2, 2), (0, 0, 0), (Lb, Lb, Lb), 0.1, np.random.default_rng(4), tets=tets)
+    m = Mesh(mesh, box)
+    m.build_lists(2.5, 1e-3)
+    assert m.get_option("cluster_path") == 1
+    p = torch.tensor(pos, dtype=torch.float64, device="cuda")
+    sp = torch.zeros(len(pos), dtype=torch.int32, device="cuda")
+    m.bin(p, sp)
+    F, ev, cnt = m.forces(EPS, SIG, prec)
+    ref = oracle.lj(pos, np.zeros(len(pos), np.int32), EPS, SIG, 2.5, box)
+    assert_forces(F.double().cpu().numpy(), ref, 1e-12 if prec == "fp64" else 1e-5)
+    ev = ev.cpu().numpy()
+    cnt = cnt.cpu().numpy()
+    tol = 1e-12 if prec == "fp64" else 1e-6
+    assert abs(ev[0] - ref["U"]) <= tol * ref["Uabs"]
+    np.testing.assert_allclose(ev[1:7], ref["W"], rtol=0, atol=tol * ref["Wabs"])
+    assert cnt[3] + cnt[4] + cnt[5] == ref["pairs"]
+    m.close()
