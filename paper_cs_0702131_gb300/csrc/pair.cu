@@ -1784,7 +1784,8 @@ __device__ __forceinline__ void band_pair(const PairArgs &a, const float4 *tab, 
 // are re-decided in FP64 with the all-pairs operation order.  SAME:
 // own-cluster survivors pair only with tile molecules of lower binned index.
 template <bool MULTI, bool SHIFT, bool SAME, bool GHOST>
-__device__ __forceinline__ void eval_tile(const PairArgs &a, const float4 *tab, const WarpC &w, int ni, int k0,
+__device__ __forceinline__ void eval_tile(const PairArgs &a, const float4 *tab, const float4 *th, const float4 *tl,
+                                          int ni, int k0,
                                           float4 xh, float4 xl, float (&fi)[4 * kNI], float4 &fj, float &u_acc,
                                           unsigned &nin, unsigned &nsame, float (&vg)[6], float *vl,
                                           float4 *facc) {
@@ -1793,7 +1794,7 @@ __device__ __forceinline__ void eval_tile(const PairArgs &a, const float4 *tab, 
 #pragma unroll
     for (int t = 0; t < kNI; ++t) {
         if (t >= ni) break;
-        const float4 h = w.ih[t], lo = w.il[t];
+        const float4 h = th[t], lo = tl[t];
         tile_pair<MULTI, SHIFT, SAME, GHOST>(a, tab, t0, h, lo, xh, xl, t, k0, fi, fj, u_acc, nin, nsame, bm, vg);
     }
     if (__any_sync(0xffffffffu, bm != 0)) {
@@ -1802,7 +1803,7 @@ __device__ __forceinline__ void eval_tile(const PairArgs &a, const float4 *tab, 
 #pragma unroll 1
         for (int t = 0; t < ni; ++t)
             if (((bm >> t) & 1u) && band_in(a, k0 + t, l, np))
-                band_pair<MULTI, SHIFT, SAME, GHOST>(a, tab, t0, w.ih[t], w.il[t], xh, xl, fj, u_acc, nin, nsame, vg,
+                band_pair<MULTI, SHIFT, SAME, GHOST>(a, tab, t0, th[t], tl[t], xh, xl, fj, u_acc, nin, nsame, vg,
                                                      vl, facc + k0 + t);
     }
 }
@@ -1898,6 +1899,7 @@ __global__ void __launch_bounds__(kCT, MINB) pair_fwd32c(PairArgs a, ClKArgs c) 
         // 2. fill the buffer (A's own molecules, then the partner runs 32 at
         // a time) until it cannot take 32 more; 3./4. evaluate it; repeat
         int own = s0;                               // next own molecule to push
+        bool own_first = true;                      // no flush of this cluster yet
         const int e1 = c.cl_run_off[A + 1];
         int eb = c.cl_run_off[A];                   // next batch of 32 runs
         int p0 = 0, total = 0, inc = 0;             // candidate cursor of the loaded batch
@@ -1988,11 +1990,16 @@ __global__ void __launch_bounds__(kCT, MINB) pair_fwd32c(PairArgs a, ClKArgs c) 
                 }
             }
             if (nq > 0) {
-                // 3. every tile of A against the buffered survivors
+                // 3. every tile of A against the buffered survivors; while A's own
+                // molecules are all in the buffer (slots 0 .. nA - 1, as in the
+                // first flush of a cluster below the fill threshold) the tiles
+                // are read there, in the same representation
                 __syncwarp();
+                const bool own_buf = own_first && own >= s1;
                 for (int i0 = 0; i0 < nA; i0 += kNI) {
                     const int ni = min(kNI, nA - i0), k0 = s0 + i0;
-                    if (lane < kNI) {
+                    const float4 *th = own_buf ? &w.sh[i0] : w.ih, *tl = own_buf ? &w.sl[i0] : w.il;
+                    if (!own_buf && lane < kNI) {
                         float4 h = make_float4(1e18f, 1e18f, 1e18f, 0.f), lo = zero4;
                         if (lane < ni) {
                             const float4 r = c.xlo[k0 + lane];
@@ -2017,11 +2024,11 @@ __global__ void __launch_bounds__(kCT, MINB) pair_fwd32c(PairArgs a, ClKArgs c) 
                         float4 fj = zero4;
                         unsigned nin = 0, nsame = 0;
                         if (__any_sync(FULL, (__float_as_int(xh.w) & kSameBit) != 0))
-                            eval_tile<MULTI, SHIFT, true, GHOST>(a, tab, w, ni, k0, xh, xl, fi, fj, u_acc, nin, nsame,
-                                                                 vg, vl, facc);
+                            eval_tile<MULTI, SHIFT, true, GHOST>(a, tab, th, tl, ni, k0, xh, xl, fi, fj, u_acc, nin,
+                                                                 nsame, vg, vl, facc);
                         else
-                            eval_tile<MULTI, SHIFT, false, GHOST>(a, tab, w, ni, k0, xh, xl, fi, fj, u_acc, nin, nsame,
-                                                                  vg, vl, facc);
+                            eval_tile<MULTI, SHIFT, false, GHOST>(a, tab, th, tl, ni, k0, xh, xl, fi, fj, u_acc, nin,
+                                                                  nsame, vg, vl, facc);
                         {
                             // within-rc counts per category (same cell, DIL, periodic image),
                             // without branches (nin = nsame = 0 on invalid lanes)
@@ -2042,7 +2049,7 @@ __global__ void __launch_bounds__(kCT, MINB) pair_fwd32c(PairArgs a, ClKArgs c) 
                     if ((lane & 3) == 0 && t < ni) {
                         atomicAdd(facc + k0 + t, make_float4(fi[0], fi[1], fi[2], fi[3]));
                         if (!GHOST) {
-                            const float4 x = w.ih[t];
+                            const float4 x = th[t];
                             vir_add<32>(vl, x.x, x.y, x.z, fi[0], fi[1], fi[2]);
                         }
                     }
@@ -2061,6 +2068,7 @@ __global__ void __launch_bounds__(kCT, MINB) pair_fwd32c(PairArgs a, ClKArgs c) 
                 }
                 __syncwarp();
                 nq = 0;
+                own_first = false;
             }
             if (!more) break;
         }
