@@ -201,6 +201,7 @@ struct aica_mesh {
     bool ghosts = false;                     // the last binning marked halo molecules
     int64_t n_refined = 0;                   // molecules the last FP32 call recomputed in FP64 (host copy on demand)
     aica::DevBuf unsorted;                   // [n] binned slots before the in-cell sort (cells of a few molecules)
+    aica::DevBuf ucell;                      // [n] the cell of each slot of `unsorted`
     int max_species = -1;                    // from the last checked binning, -1 if unknown
     aica::DevBuf sph;                        // [C] float4 molecule bounding sphere per cell (local frame)
     aica::DevBuf miss;                       // molecules whose previous cell no longer holds them

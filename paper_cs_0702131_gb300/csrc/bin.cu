@@ -506,7 +506,7 @@ __global__ void __launch_bounds__(kFixWarps * 32) bin_fixup(const int *cell_off,
 // counted down, so the counts are zero again afterwards.  Order within a
 // cell is fixed by bin_cells.
 __global__ void __launch_bounds__(256) bin_scatter_down(const int *cell_of, int64_t n, const int *cell_off, int *cnt,
-                                                        int *order) {
+                                                        int *order, int *slot_cell) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int c = k < n ? cell_of[k] : -1;
     const unsigned same = __match_any_sync(0xffffffffu, c);
@@ -514,7 +514,11 @@ __global__ void __launch_bounds__(256) bin_scatter_down(const int *cell_of, int6
     int top = 0;
     if (c >= 0 && lane == leader) top = atomicSub(cnt + c, m);
     top = __shfl_sync(0xffffffffu, top, leader);
-    if (c >= 0) order[cell_off[c] + top - m + __popc(same & ((1u << lane) - 1u))] = (int)k;
+    if (c >= 0) {
+        const int s = cell_off[c] + top - m + __popc(same & ((1u << lane) - 1u));
+        order[s] = (int)k;
+        if (slot_cell) slot_cell[s] = c;         // read in slot order by the in-cell sort
+    }
 }
 
 // Coordinates of p in the molecule frame o: the nearest FP32 values and the
@@ -647,14 +651,13 @@ __global__ void __launch_bounds__(256) bin_cells(BinArgs a, const int *cell_off,
 // `order` gets them sorted.  nbp points at the binned count (cell_off[C]).
 constexpr int kSlotWarps = 8;
 
-__device__ __forceinline__ float4 local_xloc(const BinArgs &a, int k, int c, int slot, double *xs64, int &spmax,
-                                             bool &bad) {
-    const int sp = a.species[k];
+__device__ __forceinline__ float4 local_xloc_from(const BinArgs &a, int k, int c, int slot, double *xs64, int &spmax,
+                                                  bool &bad, int sp, const double (&raw)[3]) {
     spmax = max(spmax, sp < 0 ? kMaxSpecies : sp);
     bad |= (unsigned)sp >= (unsigned)kMaxSpecies;
     double p[3];
     for (int d = 0; d < 3; ++d) {
-        p[d] = a.pos[3 * (int64_t)k + d];
+        p[d] = raw[d];
         if (a.per[d]) p[d] = wrap_coord(p[d], a.L[d], a.Lkey[d]);
         xs64[3 * (int64_t)slot + d] = p[d];
     }
@@ -662,6 +665,12 @@ __device__ __forceinline__ float4 local_xloc(const BinArgs &a, int k, int c, int
     frame_split(a, p, a.orgm64 + 3 * c, (sp & (kMaxSpecies - 1)) | (k >= a.n_owned ? kGhostBit : 0), c, hi, lo);
     a.xlo[slot] = lo;
     return hi;
+}
+
+__device__ __forceinline__ float4 local_xloc(const BinArgs &a, int k, int c, int slot, double *xs64, int &spmax,
+                                             bool &bad) {
+    const double raw[3] = {a.pos[3 * (int64_t)k], a.pos[3 * (int64_t)k + 1], a.pos[3 * (int64_t)k + 2]};
+    return local_xloc_from(a, k, c, slot, xs64, spmax, bad, a.species[k], raw);
 }
 
 __device__ __forceinline__ float4 sphere_of(const float4 *x, int m) {
@@ -684,8 +693,8 @@ __device__ __forceinline__ float4 sphere_of(const float4 *x, int m) {
 }
 
 __global__ void __launch_bounds__(kSlotWarps * 32) bin_slots(BinArgs a, const int *cell_off, const int *nbp,
-                                                             const int *un, int *order, double *xs64, float4 *xloc,
-                                                             float4 *sph) {
+                                                             const int *un, const int *ucell, int *order,
+                                                             double *xs64, float4 *xloc, float4 *sph) {
     __shared__ int sk[kSlotWarps][64];
     __shared__ float4 sx[kSlotWarps][64];
     const unsigned FULL = 0xffffffffu;
@@ -693,14 +702,18 @@ __global__ void __launch_bounds__(kSlotWarps * 32) bin_slots(BinArgs a, const in
     const int64_t w0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane;   // first slot of the window
     const int nb = *nbp;
     if (w0 >= nb) return;                 // whole warp
-    int k[2], c[2], s0[2], m[2];
+    int k[2], c[2], s0[2], m[2], sp[2] = {0, 0};
+    double raw[2][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
     bool st[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const int64_t S = w0 + 32 * h + lane;
         if (S < nb) {
             k[h] = un[S];
-            c[h] = a.cell_of[k[h]];
+            c[h] = ucell[S];                  // the slot's cell, written with the slot claim
+            // the molecule's data, loaded while the cell offsets arrive
+            sp[h] = a.species[k[h]];
+            for (int d = 0; d < 3; ++d) raw[h][d] = a.pos[3 * (int64_t)k[h] + d];
             s0[h] = cell_off[c[h]];
             m[h] = cell_off[c[h] + 1] - s0[h];
             st[h] = s0[h] == S;
@@ -733,7 +746,7 @@ __global__ void __launch_bounds__(kSlotWarps * 32) bin_slots(BinArgs a, const in
             const int slot = s0[h] + rank;
             order[slot] = k[h];
             a.inv[k[h]] = slot;
-            const float4 x = local_xloc(a, k[h], c[h], slot, xs64, spmax, bad);
+            const float4 x = local_xloc_from(a, k[h], c[h], slot, xs64, spmax, bad, sp[h], raw[h]);
             xloc[slot] = x;
             sx[wib][ls + rank] = x;
         }
@@ -802,6 +815,7 @@ extern "C" aica_status aica_bin_molecules(aica_mesh *m, const double *pos, const
         AICA_CUDA(m->cell_of.reserve(sizeof(int) * cap));
         AICA_CUDA(m->order.reserve(sizeof(int) * cap));
         AICA_CUDA(m->unsorted.reserve(sizeof(int) * cap));
+        AICA_CUDA(m->ucell.reserve(sizeof(int) * cap));
         AICA_CUDA(m->xloc.reserve(sizeof(float4) * cap));
         AICA_CUDA(m->xlo.reserve(sizeof(float4) * cap));
         AICA_CUDA(m->flag_list.reserve(sizeof(int) * (cap + 1)));
@@ -897,7 +911,7 @@ extern "C" aica_status aica_bin_molecules(aica_mesh *m, const double *pos, const
     const bool wide = (double)n > 6.0 * (double)C;
     int *slots_out = wide ? m->order.as<int>() : m->unsorted.as<int>();
     if (n > 0) {
-        bin_scatter_down<<<nb, 256, 0, st>>>(a.cell_of, n, off, cnt, slots_out);
+        bin_scatter_down<<<nb, 256, 0, st>>>(a.cell_of, n, off, cnt, slots_out, wide ? nullptr : m->ucell.as<int>());
         m->launches += 1;
     }
     // order by original index, gather, bounding spheres: per slot for cells of
@@ -907,7 +921,7 @@ extern "C" aica_status aica_bin_molecules(aica_mesh *m, const double *pos, const
             const unsigned gc = (unsigned)std::min<int64_t>(((int64_t)C * 32 + 255) / 256, 152 * 16);
             bin_cells<32><<<gc, 256, 0, st>>>(a, off, C, m->order.as<int>(), m->xs64.as<double>(), m->xloc.as<float4>(), m->sph.as<float4>());
         } else {
-            bin_slots<<<nb, kSlotWarps * 32, 0, st>>>(a, off, off + C, slots_out, m->order.as<int>(), m->xs64.as<double>(), m->xloc.as<float4>(), m->sph.as<float4>());
+            bin_slots<<<nb, kSlotWarps * 32, 0, st>>>(a, off, off + C, slots_out, m->ucell.as<int>(), m->order.as<int>(), m->xs64.as<double>(), m->xloc.as<float4>(), m->sph.as<float4>());
         }
         m->launches += 1;
     }

@@ -511,7 +511,7 @@ extern "C" void aica_mesh_destroy(aica_mesh *m) {
     aica::DevBuf *bufs[] = {&m->tri_off, &m->tri, &m->tri_nbr, &m->vtx_off, &m->vtx, &m->edg_off, &m->edg, &m->ctr, &m->rad,
                             &m->lo, &m->hi, &m->org, &m->ntri, &m->orgk, &m->orgm, &m->orgm64, &m->cl_first, &m->cl_of, &m->cl_run_off, &m->cl_runs, &m->cl_full_off, &m->cl_full, &m->cl_box, &m->xlo, &m->flag_list, &m->tri32, &m->pl32, &m->tric, &m->orgf, &m->vtx32, &m->edg32, &m->ctr32, &m->rad32, &m->box32, &m->bkt_off, &m->bkt_cells, &m->nbr_off, &m->nbr, &m->dil_off,
                             &m->dil_ids, &m->ref_src, &m->ref_n, &m->ref_off, &m->ref_ids, &m->run_off, &m->runs, &m->xf_dev, &m->run_d, &m->work_off,
-                            &m->work, &m->work_split, &m->proc_order, &m->cell_of, &m->order, &m->unsorted,
+                            &m->work, &m->work_split, &m->proc_order, &m->cell_of, &m->order, &m->unsorted, &m->ucell,
                             &m->cell_off, &m->fill, &m->inv, &m->sph, &m->xloc, &m->xs64, &m->facc,
                             &m->vsorted, &m->acc, &m->flags, &m->params, &m->tmp, &m->scan_state};
     for (auto *b : bufs) b->release();
