@@ -19,8 +19,16 @@
 // skipped.  The counters still report every pair of every scheduled cell pair
 // as "evaluated".
 //
-// FP32 layout.  A persistent grid of 4-warp blocks; warps claim cells from
-// a global counter.  The chunk (up to NI molecules of I: 4 for cells of a
+// Kernels.  With box periodicity and the minimum-distance lists the FP32
+// forces come from the cluster kernel pair_fwd32c (further below: a warp
+// per cluster of cells, candidates culled against the cluster's box), then
+// flag_ill_conditioned and refine_ds recompute in double-single arithmetic
+// the molecules whose FP32 force the error bound cannot certify.  The cell
+// kernel pair_fwd32 described next serves general referring transforms, the
+// vertex criterion and AICA_OPT_FP32_KERNEL = 1; pair_fwd64 is the FP64 path.
+//
+// FP32 cell kernel layout.  A persistent grid of 4-warp blocks; warps claim
+// cells from a global counter.  The chunk (up to NI molecules of I: 4 for cells of a
 // few molecules, 8 otherwise) sits in shared memory.  The FP32 schedule is
 // kept in runs: consecutive partner cells under one image vector and one
 // molecule-frame origin are one contiguous range of binned molecules under
@@ -1620,9 +1628,10 @@ __global__ void __launch_bounds__(kGradSlots * 32) finish_bwd(const double *acc,
 //      candidate farther than rc from the box cannot pair with any molecule
 //      of A (margins above the FP32 cut-off) and is dropped, the rest go to
 //      a per-warp survivor buffer in shared memory;
-//   3. for every i-tile of NI molecules of A, every batch of 32 survivors is
-//      evaluated one survivor per lane against the tile (the tile's
-//      molecules broadcast from shared memory): forces by FMA, the survivor's
+//   3. whenever the buffer cannot take 32 more survivors, and at the end:
+//      for every i-tile of kNI molecules of A, every batch of 32 survivors
+//      is evaluated one survivor per lane against the tile (the tile's
+//      molecules read from shared memory): forces by FMA, the survivor's
 //      reaction summed in registers and added to its slot of the buffer, the
 //      tile's forces summed per lane and over the warp at the end of the tile
 //      (recursive halving), one vector atomic per molecule;
@@ -1631,7 +1640,8 @@ __global__ void __launch_bounds__(kGradSlots * 32) finish_bwd(const double *acc,
 // multiples of 2^-q (xloc) plus a remainder (xlo), run shifts likewise, so
 // (x_k,hi - x_l,hi - shift_hi) is exact and adding the remainders rounds once.
 // Every force accumulator's .w sums |f|^2 over the molecule's pairs: the
-// scale of the FP32 error of its force (see refine64).
+// scale of the FP32 error of its force (see flag_ill_conditioned and
+// refine_ds).
 struct ClKArgs {
     const int *cl_first, *cl_run_off;
     const ClRun *runs;
