@@ -10,21 +10,28 @@
 //                creation) does not if it lies in front of one; other
 //                (star-shaped) cells take the cone from the vertex mean
 //                through each face triangle.  FP32 filter on cell-local
-//                coordinates, FP64 and exact slow paths (predicates.cuh).
+//                coordinates (face planes precomputed at mesh creation,
+//                n / |n|_1 and offset, 16 B per triangle), FP64 and exact
+//                slow paths (predicates.cuh).
 //   bin_locate_hint / bin_locate_miss   when the same molecules were binned
 //                before: test each molecule's previous cell with the FP32
-//                filter alone (and, when it left a convex cell, the cell
-//                across the face it crossed), collect the ones still not
+//                filter alone (and, when it left a convex cell, walk across
+//                the faces it lies in front of, up to kWalk cells; the point
+//                in a cell's frame formed in FP32 from an integer split of
+//                the FP64 position), collect the ones still not
 //                located (or that the filter could not decide), then search
 //                those exactly in the previous cell, its face neighbours and
 //                finally the grid.
 //                The previous cell is only a search order: the test is exact.
 //   scan_lookback  cell offsets from the counts (single pass, scan.cuh)
-//   bin_scatter_down  warp-aggregated slot claims, counting the counts down
+//   bin_scatter_down  warp-aggregated slot claims, counting the counts down;
+//                each claimed slot also gets its cell (read in slot order
+//                by bin_slots)
 //   bin_slots / bin_cells   order each cell's slots by original index (the
 //                stable counting sort by (cell, original index)), gather FP64
-//                positions and float4 cell-local coordinates with the species
-//                in .w (the pair kernels' input layout), the inverse
+//                positions, float4 frame coordinates with the species in .w
+//                and their FP32 remainders with the cell in .w (the pair
+//                kernels' input layout), the inverse
 //                permutation, and the cell's bounding sphere: per slot with
 //                window-owned cells for cells of a few molecules, a warp per
 //                cell otherwise
