@@ -198,9 +198,12 @@ aica_status aica_bin_molecules(aica_mesh *mesh, const double *pos, const int32_t
  * acting on the real molecule only, because its source may live on another
  * processor; on one device each periodic image pair is evaluated once with
  * Newton's third law instead, which gives the same forces.
- *   prec   AICA_FP32: FP32 pair arithmetic on cell-local coordinates, FP64
- *          energy/virial sums, and r^2 < rc^2 decided in FP64 whenever the
- *          FP32 value lies within 1e-5 rc^2 of the cut-off;
+ *   prec   AICA_FP32: FP32 pair arithmetic on frame-local coordinates
+ *          (separations rounded once on the cluster path), FP64
+ *          energy/virial sums, r^2 < rc^2 decided in FP64 whenever the
+ *          FP32 value lies within 1e-5 rc^2 of the cut-off, and molecules
+ *          whose FP32 force may miss AICA_OPT_FP32_REFINE_TOL recomputed
+ *          (see aica_set_option);
  *          AICA_FP64: all FP64.
  *   force_out  device [n*3], float (FP32) or double (FP64), original order;
  *              overwritten (may be NULL when no molecules were binned)
@@ -316,11 +319,13 @@ aica_status aica_take_kernel_times(aica_mesh *mesh, float *ms, int64_t cap, int6
 /* Options of a mesh (no counterpart in the paper: precision policy and
  * measurement switches of this implementation).
  *   AICA_OPT_FP32_REFINE_TOL  (default 1e-5) FP32 forces: the per-component
- *       error bound aica_forces guarantees relative to max(|F_ic|, ||F_i||)
- *       on the box-periodic cluster path.  After the FP32 pass, a molecule
+ *       error relative to max(|F_ic|, ||F_i||) that aica_forces targets on
+ *       the box-periodic cluster path.  After the FP32 pass, a molecule
  *       whose force is too small against the FP32 error scale of its pair
- *       forces (|F_i| < 1e-6 sqrt(sum_l |f_kl|^2) / tol) is recomputed in FP64
- *       with the exact pair set.  <= 0 turns the recomputation off.
+ *       forces (|F_i| < 1.25e-6 sqrt(sum_l |f_kl|^2) / tol) is recomputed in
+ *       double-single arithmetic (about 48 bits; cut-off decisions near rc in
+ *       FP64) over the same pair set.  The factor is calibrated against FP64
+ *       forces, not a proven bound.  <= 0 turns the recomputation off.
  *   AICA_OPT_COUNT_EVALUATED  (default 1) aica_forces fills counts_out[0..2]
  *       (pairs of every listed cell pair, §2.3) with an extra pass over the
  *       cell schedule when the FP32 cluster kernel runs; 0 skips that pass
@@ -343,7 +348,7 @@ aica_status aica_take_kernel_times(aica_mesh *mesh, float *ms, int64_t cap, int6
  *       processor; aica_forces_backward and the cell kernel refuse it
  *       (AICA_ERR_INVALID_ARG).  -1 returns to a single processor.
  *   AICA_OPT_REFINED          (read only) molecules the last FP32
- *       aica_forces call recomputed in FP64 (synchronizes `stream`).
+ *       aica_forces call recomputed (synchronizes `stream`).
  *   AICA_OPT_CLUSTER_PATH     (read only) 1 when the built lists have a
  *       cluster schedule (box periodicity, exact-separation bound met).
  * AICA_ERR_INVALID_ARG for an unknown option or a read-only one set. */

@@ -199,7 +199,7 @@ struct aica_mesh {
     int fp32_kernel = 0;                     // 0: cluster kernel when available, 1: the cell kernel
     int64_t n_owned = -1;                    // portion mode: molecules [0, n_owned) are owned, the rest halo (-1: all)
     bool ghosts = false;                     // the last binning marked halo molecules
-    int64_t n_refined = 0;                   // molecules the last FP32 call recomputed in FP64 (host copy on demand)
+    int64_t n_refined = 0;                   // molecules the last FP32 call recomputed (host copy on demand)
     aica::DevBuf unsorted;                   // [n] binned slots before the in-cell sort (cells of a few molecules)
     aica::DevBuf ucell;                      // [n] the cell of each slot of `unsorted`
     int max_species = -1;                    // from the last checked binning, -1 if unknown

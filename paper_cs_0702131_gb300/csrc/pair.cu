@@ -2400,7 +2400,8 @@ extern "C" aica_status aica_forces(aica_mesh *m, const aica_lj *lj, aica_precisi
         m->launches += 1;
     }
     // FP32 with box periodicity (either kernel): molecules whose FP32 force cannot
-    // be certified to the tolerance are recomputed in FP64 (needs the cluster lists)
+    // be certified to the tolerance are recomputed in double-single arithmetic
+    // (needs the cluster lists)
     const bool refine = clpath && m->refine_tol > 0 && n > 0;
     int *flags = refine ? m->flag_list.as<int>() : nullptr;
     if (refine) AICA_CUDA(cudaMemsetAsync(flags, 0, sizeof(int), st));
