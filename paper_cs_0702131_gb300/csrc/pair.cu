@@ -2399,7 +2399,7 @@ extern "C" aica_status aica_forces(aica_mesh *m, const aica_lj *lj, aica_precisi
             a.cell_off, a.run_off, a.runs, a.C, acc);
         m->launches += 1;
     }
-    // FP32 with box periodicity (either kernel): molecules whose FP32 force cannot
+    // FP32 cluster path: molecules whose FP32 force cannot
     // be certified to the tolerance are recomputed in double-single arithmetic
     // (needs the cluster lists)
     const bool refine = clpath && m->refine_tol > 0 && n > 0;
