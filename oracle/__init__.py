@@ -337,6 +337,8 @@ def cell_lists_full(mesh, box, rc, skin, queries=None, geo=None, criterion="min_
     bkt_off = np.r_[0, np.cumsum(np.bincount(bk, minlength=int(G.prod())))].astype(np.int64)
     m = image_range(thr, box)
     cells = np.arange(C, dtype=np.int64) if queries is None else np.asarray(queries, np.int64)
+    if len(cells) and (not np.all(np.diff(cells) > 0) or cells[0] < 0 or cells[-1] >= C):
+        raise ValueError("queries must be ascending, unique cell ids")
     nq = len(cells)
     cnt = np.zeros(nq, np.int64)
     ties = np.zeros(nq, np.int64)
@@ -358,8 +360,6 @@ def cell_lists_full(mesh, box, rc, skin, queries=None, geo=None, criterion="min_
     dA, dB = A[zero], B[zero]                        # n = 0, B > A
     o = np.lexsort((dB, dA))
     rows = np.searchsorted(cells, dA) if queries is not None else dA      # row of each entry's owner
-    if queries is not None and len(cells) and not np.all(np.diff(cells) > 0):
-        raise ValueError("queries must be ascending and unique")
     dil_off = np.r_[0, np.cumsum(np.bincount(rows, minlength=nq))].astype(np.int64)
     dil_ids = dB[o].astype(np.int32)
     rA, rB, rn = A[~zero], B[~zero], -N[~zero]       # referred cell (source A, image -n)
