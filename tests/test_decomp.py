@@ -40,6 +40,31 @@ def test_partition_is_balanced_and_deterministic():
     assert np.all(part[:25] == 0) and np.all(part[25:] == 1)
 
 
+@pytest.mark.parametrize("P", [2, 3])
+def test_halo_molecules_hold_every_partner_of_the_owned(P):
+    """Each molecule within rc of an owned molecule (minimum image) is owned
+    or in the halo the processor receives, and the halo holds exactly the
+    molecules of the plan's received cells."""
+    c, geo, lists, cell, pos = _setup()
+    part = decomp.partition(geo["ctr"], P)
+    L = np.asarray(c["box"]["L"], float)
+    d = pos[:, None, :] - pos[None, :, :]
+    d -= L * np.rint(d / L)
+    near = (d ** 2).sum(-1) < c["rc"] ** 2
+    np.fill_diagonal(near, False)
+    for r in range(P):
+        plan = decomp.halo_plan(lists, part, r)
+        owned = part[cell] == r
+        halo = decomp.halo_molecules(plan, cell)
+        recv = np.concatenate(list(plan["recv"].values())) if plan["recv"] else np.zeros(0, np.int64)
+        np.testing.assert_array_equal(halo, np.flatnonzero(np.isin(cell, recv)))
+        assert not owned[halo].any()
+        have = owned.copy()
+        have[halo] = True
+        partners = near[owned].any(axis=0)
+        assert np.all(have[partners]), f"rank {r}: {int((partners & ~have).sum())} partners missing"
+
+
 def test_plans_cover_every_interaction_once():
     c, geo, lists, _, _ = _setup()
     P = 3
